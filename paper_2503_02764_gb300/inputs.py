@@ -1,0 +1,269 @@
+"""Seeded synthetic inputs for the FLD radiation substep.
+
+This module is shared by the CPU oracle's tests and by the CUDA path's tests and
+benchmark. It holds input recipes only (shapes, random fields, boundary kinds,
+time steps) and none of the substep's arithmetic (no limiter, no diffusion
+operator, no exchange).
+
+Conventions
+-----------
+* Arrays are float64, C-contiguous, numpy axis order (z, y, x): x is fastest.
+  A 1D problem has shape (nx,), 2D (ny, nx), 3D (nz, ny, nx).
+* ``h`` and ``bc`` are given in physical axis order (x, y, z).
+* Boundary codes: 0 periodic, 1 Neumann (zero flux), 2 Dirichlet (face value).
+* Dirichlet face values are a dict ``{(axis, side): face_array}`` with
+  ``side`` 0 = low, 1 = high and ``face_array`` the field's shape with that
+  axis removed. ``pack_dirichlet`` flattens them in the order x-lo, x-hi,
+  y-lo, y-hi, z-lo, z-hi (Dirichlet sides only), which is the layout the C
+  library takes.
+* Seeds: 250302764 + workload index; member p of the batched workload uses
+  base seed + 1000 * p.
+
+The time steps are stated as multiples of the explicit diffusion limit
+h^2 / (2 d D_ref) with the diffusion-limit bound D_ref = c / (3 min(kappa rho))
+(the limiter never exceeds 1/3), so dt is a plain input number.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+SEED_BASE = 250302764
+PERIODIC, NEUMANN, DIRICHLET = 0, 1, 2
+OPACITY_CONST, OPACITY_POWER = 0, 1
+LIMITER_LP, LIMITER_DIFFUSION = 0, 1
+
+
+@dataclass
+class Problem:
+    name: str
+    shape: tuple            # numpy order (z, y, x) restricted to ndim
+    h: tuple                # (hx, hy, hz)[:ndim]
+    bc: tuple               # ((xlo, xhi), (ylo, yhi), ...)[:ndim]
+    c: float
+    a_r: float
+    gamma: float
+    R_gas: float
+    opacity: tuple          # (kind, kappa0, a_rho, a_T): kappa = kappa0 rho^a_rho T^a_T
+    dt: float
+    rho: np.ndarray
+    T: np.ndarray
+    E: np.ndarray
+    E_bc: dict = field(default_factory=dict)
+    limiter: int = LIMITER_LP
+    tol: float = 1e-10
+    steps: int = 1
+
+    @property
+    def ndim(self):
+        return len(self.shape)
+
+    @property
+    def ncells(self):
+        return int(np.prod(self.shape))
+
+    def n_xyz(self):
+        """(nx, ny, nz) with 1 for absent axes."""
+        n = list(reversed(self.shape)) + [1] * (3 - self.ndim)
+        return tuple(int(v) for v in n)
+
+
+def pack_dirichlet(shape, bc, E_bc):
+    """Flatten Dirichlet face arrays in x-lo, x-hi, y-lo, y-hi, z-lo, z-hi order."""
+    parts = []
+    for d in range(len(shape)):
+        for s in (0, 1):
+            if bc[d][s] == DIRICHLET:
+                parts.append(np.ascontiguousarray(E_bc[(d, s)], dtype=np.float64).ravel())
+    if not parts:
+        return np.zeros(0, dtype=np.float64)
+    return np.concatenate(parts)
+
+
+def correlated_gaussian(rng, shape, ell):
+    """Zero-mean, unit-variance Gaussian field with correlation exp(-r^2/(2 ell^2)).
+
+    White noise is filtered by exp(-|k|^2 ell^2 / 4) in Fourier space (k in
+    radians per cell) and normalised to sample mean 0 and sample std 1.
+    """
+    w = rng.standard_normal(shape)
+    k2 = np.zeros(shape)
+    for a, n in enumerate(shape):
+        k = 2.0 * np.pi * np.fft.fftfreq(n)
+        sh = [1] * len(shape)
+        sh[a] = n
+        k2 = k2 + (k.reshape(sh)) ** 2
+    g = np.real(np.fft.ifftn(np.fft.fftn(w) * np.exp(-k2 * ell * ell / 4.0)))
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def lognormal(rng, shape, sigma, ell):
+    g = correlated_gaussian(rng, shape, ell)
+    return np.exp(sigma * g - 0.5 * sigma * sigma)
+
+
+def _cell_centres(n, L=1.0):
+    return (np.arange(n) + 0.5) * (L / n)
+
+
+def gaussian_pulse_1d(n=256, seed=None):
+    """1D periodic, n cells, unit box: rho = 1, kappa = 1e3, T = 1,
+    E = 1 + 0.1 exp(-(x - 0.5)^2 / 0.01^2); dt = 10 x the explicit limit."""
+    h = 1.0 / n
+    x = _cell_centres(n)
+    c, kappa = 1.0, 1.0e3
+    D_ref = c / (3.0 * kappa * 1.0)
+    dt = 10.0 * h * h / (2.0 * D_ref)
+    return Problem(
+        name="pulse1d_%d" % n, shape=(n,), h=(h,), bc=((PERIODIC, PERIODIC),),
+        c=c, a_r=1.0, gamma=5.0 / 3.0, R_gas=1.0,
+        opacity=(OPACITY_CONST, kappa, 0.0, 0.0), dt=dt,
+        rho=np.ones(n), T=np.ones(n), E=1.0 + 0.1 * np.exp(-((x - 0.5) ** 2) / 0.01 ** 2),
+        tol=1e-12, steps=1)
+
+
+def lognormal_2d(n=1024, seed=None, ny=None, steps=10):
+    """2D periodic n x n (or ny x n), h = 1: log-normal rho (sigma = 1,
+    correlation 32 cells), kappa = 0.4, T = p0/(R_gas rho) with p0 = 1,
+    E = a_r T^4 (1 + 0.05 U(-1, 1)); dt = 10 x the explicit limit."""
+    ny = n if ny is None else ny
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 2 if seed is None else seed))
+    shape = (ny, n)
+    rho = lognormal(rng, shape, 1.0, 32.0)
+    c, a_r, R_gas, kappa = 1.0, 1.0, 1.0, 0.4
+    T = 1.0 / (R_gas * rho)
+    E = a_r * T ** 4 * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, shape))
+    D_ref = c / (3.0 * kappa * rho.min())
+    dt = 10.0 * 1.0 / (2.0 * 2 * D_ref)
+    return Problem(
+        name="lognormal2d_%dx%d" % (n, ny), shape=shape, h=(1.0, 1.0),
+        bc=((PERIODIC, PERIODIC), (PERIODIC, PERIODIC)),
+        c=c, a_r=a_r, gamma=5.0 / 3.0, R_gas=R_gas,
+        opacity=(OPACITY_CONST, kappa, 0.0, 0.0), dt=dt, rho=rho, T=T, E=E,
+        tol=1e-10, steps=steps)
+
+
+def stratified_3d(n=256, seed=None, nz=None, ny=None):
+    """3D stratified box, unit cube, x/y periodic, z Dirichlet.
+
+    rho = exp(-z/0.2), T = 10 - 9 z (10x contrast), both times (1 + 0.01 U(-1,1));
+    Kramers-like kappa = kappa0 rho T^-3.5 with kappa0 set so that the
+    unperturbed kappa rho h = 1 at z = 0.5; E = a_r T^4; the z faces hold E of
+    the adjacent cells (radiation temperature pinned to the gas temperature);
+    dt = 10 x the explicit limit of the unperturbed profile.
+    """
+    nz = n if nz is None else nz
+    ny = n if ny is None else ny
+    nx = n
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 3 if seed is None else seed))
+    h = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    z = _cell_centres(nz)[:, None, None] * np.ones((nz, ny, nx))
+    rho0 = np.exp(-z / 0.2)
+    T0 = 10.0 - 9.0 * z
+    rho = rho0 * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, rho0.shape))
+    T = T0 * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, T0.shape))
+    c, a_r = 1.0, 1.0
+    # kappa rho = kappa0 rho^2 T^-3.5 ; equal to 1/h_z at z = 0.5 (unperturbed)
+    kappa0 = (1.0 / h[2]) / (np.exp(-0.5 / 0.2) ** 2 * (10.0 - 4.5) ** -3.5)
+    zc = _cell_centres(nz)
+    kr_min = np.min(kappa0 * np.exp(-zc / 0.2) ** 2 * (10.0 - 9.0 * zc) ** -3.5)
+    D_ref = c / (3.0 * kr_min)
+    hmin = min(h)
+    dt = 10.0 * hmin * hmin / (2.0 * 3 * D_ref)
+    E = a_r * T ** 4
+    E_bc = {(2, 0): E[0].copy(), (2, 1): E[-1].copy()}
+    return Problem(
+        name="stratified3d_%dx%dx%d" % (nx, ny, nz), shape=(nz, ny, nx), h=h,
+        bc=((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (DIRICHLET, DIRICHLET)),
+        c=c, a_r=a_r, gamma=5.0 / 3.0, R_gas=1.0,
+        opacity=(OPACITY_POWER, kappa0, 1.0, -3.5), dt=dt, rho=rho, T=T, E=E,
+        E_bc=E_bc, tol=1e-10, steps=1)
+
+
+def batch_member(p, seed_base=None, nmin=32, nmax=512):
+    """Member p of the batched 2D workload: sides U{nmin..nmax}, periodic, h = 1,
+    log-normal rho (sigma ~ U[0.5, 2], correlation 8 cells), kappa = 10^U[0,4],
+    T = 1/rho, E = T^4 (1 + 0.05 U(-1,1)), dt = s x the explicit limit with
+    s = 10^U[0, 2]."""
+    base = SEED_BASE + 4 if seed_base is None else seed_base
+    rng = np.random.Generator(np.random.PCG64(base + 1000 * p))
+    nx = int(rng.integers(nmin, nmax + 1))
+    ny = int(rng.integers(nmin, nmax + 1))
+    sigma = float(rng.uniform(0.5, 2.0))
+    kappa = float(10.0 ** rng.uniform(0.0, 4.0))
+    s = float(10.0 ** rng.uniform(0.0, 2.0))
+    shape = (ny, nx)
+    rho = lognormal(rng, shape, sigma, 8.0)
+    T = 1.0 / rho
+    E = T ** 4 * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, shape))
+    c = 1.0
+    D_ref = c / (3.0 * kappa * rho.min())
+    dt = s * 1.0 / (2.0 * 2 * D_ref)
+    return Problem(
+        name="batch2d_p%d_%dx%d" % (p, nx, ny), shape=shape, h=(1.0, 1.0),
+        bc=((PERIODIC, PERIODIC), (PERIODIC, PERIODIC)),
+        c=c, a_r=1.0, gamma=5.0 / 3.0, R_gas=1.0,
+        opacity=(OPACITY_CONST, kappa, 0.0, 0.0), dt=dt, rho=rho, T=T, E=E,
+        tol=1e-10, steps=1)
+
+
+def batch(nprob=512, seed_base=None, nmin=32, nmax=512):
+    return [batch_member(p, seed_base, nmin, nmax) for p in range(nprob)]
+
+
+def linear_mode_3d(n=512, ratio=1.0, amp=1e-4, seed=None, ny=None, nz=None,
+                   steps=100, dt=1e-3):
+    """3D periodic unit box driven by a linear perturbation along x.
+
+    rho = 1, T0 = 1, R_gas = 1, gamma = 5/3, a_r = 3 x ratio (so that the
+    radiation-to-gas pressure ratio a_r T^4/3 / (rho R_gas T) equals ratio),
+    kappa = 1e4, c = 1e4 (D = 1/3 in the diffusion limit, c kappa rho = 1e8).
+    The mode is k = 2 pi x-hat with T1 = amp/2 cos(k x) and
+    E1 = 4 E0 amp cos(k x) (a radiation-temperature excess over the gas, so
+    that both the diffusion and the exchange act on it).
+    """
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    nx = n
+    a_r = 3.0 * ratio
+    x = _cell_centres(nx)
+    cosx = np.cos(2.0 * np.pi * x)[None, None, :] * np.ones((nz, ny, nx))
+    T = 1.0 + 0.5 * amp * cosx
+    E0 = a_r * 1.0
+    E = E0 * (1.0 + 4.0 * amp * cosx)
+    return Problem(
+        name="linmode3d_%d_r%g" % (n, ratio), shape=(nz, ny, nx), h=(1.0 / nx, 1.0 / ny, 1.0 / nz),
+        bc=((PERIODIC, PERIODIC),) * 3, c=1.0e4, a_r=a_r, gamma=5.0 / 3.0, R_gas=1.0,
+        opacity=(OPACITY_CONST, 1.0e4, 0.0, 0.0), dt=dt,
+        rho=np.ones((nz, ny, nx)), T=T, E=E, tol=1e-10, steps=steps)
+
+
+def random_cells(ncell, seed=0):
+    """Random per-cell exchange inputs spanning chi = dt c kappa rho in [1e-6, 1e12]
+    and gas/radiation energy ratios over many decades."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 77 + seed))
+    rho = 10.0 ** rng.uniform(-3, 3, ncell)
+    T = 10.0 ** rng.uniform(-1, 2, ncell)
+    E = 10.0 ** rng.uniform(-4, 8, ncell)
+    kappa = 10.0 ** rng.uniform(-2, 4, ncell)
+    return rho, T, E, kappa
+
+
+def make_config(i, seed=None, small=False):
+    """Workload by index: 1 pulse1d, 2 lognormal2d, 3 stratified3d, 4 batch, 5 linmode3d.
+    ``small`` selects a reduced size the oracle solves in seconds."""
+    if i == 1:
+        return gaussian_pulse_1d(256)
+    if i == 2:
+        return lognormal_2d(96 if small else 1024, seed, ny=80 if small else None,
+                            steps=2 if small else 10)
+    if i == 3:
+        return stratified_3d(32 if small else 256, seed, nz=24 if small else None,
+                             ny=20 if small else None)
+    if i == 4:
+        return batch(6 if small else 512, seed, 32 if small else 32, 64 if small else 512)
+    if i == 5:
+        return linear_mode_3d(16 if small else 512, 1.0, steps=5 if small else 100)
+    raise ValueError("workload index must be 1..5")
