@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""FLD radiation substep benchmark (one JSON line on rank 0).
+
+Workload: the 3D stratified box of 256^3 cells (x, y periodic, z Dirichlet,
+Kramers-like opacity, dt = 10x the explicit limit), the radiative-magnetoconvection
+shaped case whose metric compares mixed precision with FP64. One step is one whole
+substep on the resident fields: limiter -> backward-Euler multigrid solve to a
+relative residual of 1e-10 -> exchange quartic, through the C ABI (fld_step).
+
+value    cell-updates/s = cells x steps x ranks / max-over-ranks device time
+e2e      the same through the C ABI with pinned HOST buffers: every step copies
+         rho, T, E (and the Dirichlet faces) to the device and T, E back
+roofline the dominant kernel's algorithmic bytes per launch / its event-timed
+         launch duration, against the measured copy bandwidth
+cpu_baseline  the CPU oracle on a bounded sample of the same workload (rank 0)
+
+--impl reference times that CPU oracle alone (the comparison arm for this build).
+Multi-GPU: each rank solves its own independent replica (no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FLD cell-updates/s (limiter + multigrid solve to 1e-10 + exchange)"
+UNIT = "cell-updates/s"
+
+# algorithmic bytes per cell of each kernel family (FP64 = 8 B, FP32 = 4 B),
+# counting each array once per launch: reads + writes
+BYTES_PER_CELL = {
+    "limiter": 32.0,          # E, rho, T read; D written (power-law opacity)
+    "prep": 36.0,             # D, E read; K64, K32, b written
+    "sumsq": 8.0,             # b read
+    "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
+    "add_correction": 20.0,   # x, e32 read; x written
+    "smooth32": 16.0,         # xin, b, K read; xout written
+    "smooth64": 32.0,
+    "resid_restrict32": 12.0,
+    "resid_restrict64": 24.0,
+    "prolong32": 8.0,
+    "prolong64": 16.0,
+    "exchange": 48.0,         # rho, T, E read; T, E written; T re-read for kappa counted once
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 ALU peak of the GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA lanes
+# per SM per clock (the rate a dependent-FMA probe sustains) x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+                except ValueError:
+                    pass
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_sample_step(n=40, steps=1):
+    """The oracle on a bounded sample of the workload: the same recipe at n^3."""
+    from oracle import fld as O
+    from paper_2503_02764_gb300 import inputs as I
+    P = I.stratified_3d(n)
+    T, E = P.T.copy(), P.E.copy()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        T, E, _ = O.step(P.rho, T, E, P.h, P.bc, P.E_bc, P.dt, P.c, P.a_r, P.gamma, P.R_gas,
+                         P.opacity, P.limiter, method="pcg")
+    dt = time.perf_counter() - t0
+    return P.ncells * steps / dt, dt, P.ncells
+
+
+def cpu_baseline(n=64):
+    v, secs, cells = cpu_sample_step(n, 1)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one oracle substep (numpy/scipy FP64, PCG solve, long-double exchange) "
+                      "of the stratified recipe at %d^3 = %d cells, %.1f s" % (n, cells, secs)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = 32
+    for _ in range(args.warmup):
+        cpu_sample_step(n, 1)
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        _, _, cells = cpu_sample_step(n, 1)
+        total += cells
+    secs = time.perf_counter() - t0
+    v = total / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "stratified3d (bounded CPU sample %d^3 per step)" % n,
+                       "cells": n ** 3},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d oracle substeps of the stratified recipe at %d^3" %
+                                       (args.steps, n)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2503_02764_gb300 import build, fld
+    from paper_2503_02764_gb300 import inputs as I
+    if rank == 0:
+        build.build()
+    barrier()
+
+    P = I.stratified_3d(args.n)
+    prec = fld.PREC_MIXED if args.precision == "mixed" else fld.PREC_FP64
+    hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50)
+    consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
+    op = fld.make_opacity(P.opacity)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rho, T, E = dev(P.rho), dev(P.T), dev(P.E)
+    ebc = dev(I.pack_dirichlet(P.shape, P.bc, P.E_bc))
+    stream = torch.cuda.current_stream()
+
+    stats = None
+    for _ in range(args.warmup):
+        stats = hd.step(consts, op, P.dt, rho, T, E, ebc)
+
+    # ---------------- timed region (device-resident inputs)
+    hd.prof_enable(True, 65536)
+    n0 = fld.fld_launch_count()
+    clk = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    cycles = []
+    for _ in range(args.steps):
+        st = hd.step(consts, op, P.dt, rho, T, E, ebc)
+        cycles.append(st["cycles"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = fld.fld_launch_count() - n0
+    ms = ev0.elapsed_time(ev1)
+    prof = hd.prof_read()
+    hd.prof_enable(False)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = P.ncells * args.steps * world / (ms_max * 1e-3)
+
+    # ---------------- roofline of the dominant level-0 kernel
+    peak_hbm, peak_kind = load_peaks()
+    lvl0 = [e for e in prof if e["level"] == 0 and e["name"] in BYTES_PER_CELL]
+    dom = max(lvl0, key=lambda e: e["ms"]) if lvl0 else None
+    roof = None
+    if dom:
+        bpc = BYTES_PER_CELL[dom["name"]]
+        if dom["name"] == "resid64" and prec == fld.PREC_FP64:
+            bpc = 24.0
+        achieved = bpc * dom["cells"] / (dom["ms"] * 1e-3) / 1e9
+        roof = {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak_hbm,
+                "unit": "GB/s", "frac": achieved / peak_hbm, "traffic": None,
+                "peak_source": peak_kind, "launches": dom["launches"],
+                "avg_launch_us": 1e3 * dom["ms"] / dom["launches"],
+                "bytes_per_cell": bpc}
+    total_prof = sum(e["ms"] for e in prof)
+    breakdown = sorted(({"kernel": e["name"], "level": e["level"], "launches": e["launches"],
+                         "ms": round(e["ms"], 4), "share": round(e["ms"] / total_prof, 4)}
+                        for e in prof), key=lambda d: -d["ms"])[:12]
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_rho = torch.from_numpy(P.rho.copy()).pin_memory()
+        h_T = torch.from_numpy(P.T.copy()).pin_memory()
+        h_E = torch.from_numpy(P.E.copy()).pin_memory()
+        h_ebc = torch.from_numpy(I.pack_dirichlet(P.shape, P.bc, P.E_bc)).pin_memory()
+        o_T, o_E = torch.empty_like(h_T).pin_memory(), torch.empty_like(h_E).pin_memory()
+        d_rho, d_T, d_E, d_ebc = (torch.empty_like(x, device="cuda") for x in (h_rho, h_T, h_E, h_ebc))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            d_rho.copy_(h_rho, non_blocking=True)
+            d_T.copy_(h_T, non_blocking=True)
+            d_E.copy_(h_E, non_blocking=True)
+            d_ebc.copy_(h_ebc, non_blocking=True)
+            hd.step(consts, op, P.dt, d_rho, d_T, d_E, d_ebc)
+            o_T.copy_(d_T, non_blocking=True)
+            o_E.copy_(d_E, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms_e2e = ev0.elapsed_time(ev1)
+        barrier()
+        h2d = sum(x.numel() * 8 for x in (h_rho, h_T, h_E, h_ebc))
+        d2h = 2 * P.ncells * 8
+        e2e = {"value": P.ncells * args.steps * world / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": ms_e2e / args.steps, "wall_ms_per_step": 1e3 * wall / args.steps}
+
+    # ---------------- mixed vs FP64 time to 1e-10 on the same GPU (diffusion solve alone)
+    ttt = {}
+    if rank == 0:
+        D = torch.empty_like(E)
+        hd.limiter(consts, op, E, rho, T, ebc, D)
+        for name, pr in (("mixed", fld.PREC_MIXED), ("fp64", fld.PREC_FP64)):
+            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50)
+            times, cyc = [], 0
+            for rep in range(4):
+                X = E.clone()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st = hd.diffuse(P.dt, D, ebc, X)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if rep:
+                    times.append(a.elapsed_time(b))
+                cyc = st["cycles"]
+            ttt[name] = {"ms": float(np.median(times)), "cycles": cyc}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 smoothing/transfers + f64 residual/correction/limiter/exchange"
+            if prec == fld.PREC_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": "stratified3d_%d^3 (x,y periodic, z Dirichlet, Kramers opacity, "
+                                   "dt = 10x explicit limit)" % args.n,
+                       "cells": P.ncells, "precision": args.precision, "tol": 1e-10,
+                       "l2": "inputs larger than L2 (fields %.0f MB + workspace)" %
+                             (3 * P.ncells * 8 / 1e6),
+                       "parallelism": "replicas x%d" % world},
+            "gpu_launches": launches, "cycles_per_step": cycles,
+            "roofline": roof, "kernel_breakdown": breakdown,
+            "time_to_1e-10_ms": ttt, "clocks": clocks, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * fld.h - C ABI of the GB300 flux-limited-diffusion (FLD) radiation substep.
+ *
+ * The substep (paper: arXiv 2503.02764, Sect. 2 and Sect. 3) advances the
+ * radiation energy density E and the gas temperature T of a Cartesian block by
+ * one time step dt:
+ *
+ *   1. limiter  (Eqs. fld_R, fld_lambda, fld_F; gradient stencil of Sect. 3)
+ *        R = |grad E| / (kappa rho E),  lambda = (2 + R)/(6 + 3R + R^2),
+ *        D = c lambda / (kappa rho), cell-centred, grad E by the 4th-order
+ *        5-point central difference per axis;
+ *   2. diffuse  (the div F term of Eq. mhd_r_e with F = -D grad E, treated
+ *        implicitly as Sect. 3 describes): backward Euler
+ *        (I - dt div D grad) E^{n+1} = E^n on cell-centred finite volumes,
+ *        face D = mean of the two cell values, solved by geometric multigrid
+ *        V-cycles to a relative residual ||b - A x||_2 / ||b||_2 <= tol;
+ *   3. exchange (Eqs. heating, qdot; implicit quartic of Sect. 3): backward
+ *        Euler on de/dt = +qdot, dE/dt = -qdot, qdot = c kappa rho (E - a_r T^4),
+ *        e = rho R_gas T / (gamma - 1) (Eqs. energy_density, ideal_gas_law).
+ *
+ * Layout: every field is a contiguous float64 array of n[0]*n[1]*n[2] cells,
+ * x fastest: index = (k * n[1] + j) * n[0] + i. Absent axes have n = 1.
+ *
+ * Memory: field pointers are DEVICE pointers owned by the caller. The handle
+ * owns its workspace (the multigrid level pyramid, scratch and reduction
+ * buffers), allocated once in fld_create and freed in fld_destroy; no entry
+ * point other than those two allocates device memory.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream). Work is enqueued on it. fld_diffuse and fld_step read the residual
+ * norm back once per V-cycle, so they return only after the solve on `stream`
+ * has finished; fld_limiter and fld_exchange return at once (asynchronous).
+ *
+ * Errors: every call returns an fld_status and never throws. Argument errors
+ * are detected on the host before any work is enqueued. Device-side errors
+ * (a cell with non-positive or non-finite E, rho, T or kappa) set a flag in the
+ * handle; calls that synchronise (fld_diffuse, fld_step) report it, and
+ * fld_get_status synchronises `stream` and reports/clears it for the others.
+ * A cell that fails the domain check is left unchanged.
+ */
+#ifndef FLD_H
+#define FLD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLD_OK = 0,
+    FLD_ERR_ARG = 1,            /* invalid argument: null pointer, size, enum or option */
+    FLD_ERR_DOMAIN = 2,         /* a cell had E, rho, T or kappa <= 0 or non-finite     */
+    FLD_ERR_NOT_CONVERGED = 3,  /* max_cycles V-cycles did not reach tol; E holds the
+                                   last iterate                                        */
+    FLD_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired                  */
+    FLD_ERR_CUDA = 5,           /* a CUDA runtime call failed                          */
+    FLD_ERR_NOMEM = 6           /* device allocation failed in a create call           */
+} fld_status;
+
+/* boundary kinds, per axis side */
+enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2 };
+/* opacity laws: kappa = kappa0 (CONST) or kappa0 rho^a_rho T^a_T (POWER) */
+enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_POWER = 1 };
+/* limiter: Levermore-Pomraning (Eq. fld_lambda) or the diffusion limit lambda = 1/3 */
+enum { FLD_LIMITER_LP = 0, FLD_LIMITER_DIFFUSION = 1 };
+/* solve precision: plain FP64 V-cycles, or FP32 V-cycles inside FP64 iterative
+   refinement (FP64 residual, correction and coarsest-level solve) */
+enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 };
+
+/* Physical constants in the caller's units: speed of light c, radiation
+   constant a_r, adiabatic index gamma and R_gas = k_B / (mu m_p). */
+typedef struct { double c, a_r, gamma, R_gas; } fld_consts;
+
+/* Uniform Cartesian block. ndim in {1,2,3}; n[d] >= 2 for d < ndim and n[d] = 1
+   otherwise; h[d] > 0 the cell size along axis d; bc_lo/bc_hi the boundary kind
+   of each side (periodic must be set on both sides of an axis). A Dirichlet
+   side takes face values from the E_bc array (see fld_limiter). */
+typedef struct {
+    int ndim;
+    int n[3];
+    double h[3];
+    int bc_lo[3], bc_hi[3];
+} fld_grid;
+
+typedef struct { int kind; double kappa0, a_rho, a_T; } fld_opacity;
+
+/* Solver options; fld_default_opts fills sensible values. */
+typedef struct {
+    int precision;      /* FLD_PREC_FP64 or FLD_PREC_MIXED                          */
+    double tol;         /* stop when ||b - A x||_2 <= tol ||b||_2                    */
+    int max_cycles;     /* V-cycle limit (outer refinement steps in MIXED)          */
+    int nu1, nu2;       /* red-black Gauss-Seidel sweeps before / after coarse corr. */
+    int coarse_sweeps;  /* red-black sweeps of the coarsest-level solve             */
+    int limiter;        /* FLD_LIMITER_LP or FLD_LIMITER_DIFFUSION                  */
+    int block;          /* threads per block of the stencil kernels (0 = default)   */
+    int reserved[4];
+} fld_opts;
+
+/* Per-solve statistics (optional output). resid_hist[i] is the relative
+   residual after i cycles (resid_hist[0] before the first), for i < 64. */
+typedef struct {
+    int cycles;
+    double rel_resid;
+    double resid_hist[64];
+    int levels;
+} fld_stats;
+
+typedef struct fld_handle fld_handle;
+
+/* Fill *o with defaults: FP64, tol 1e-10, 50 cycles, V(2,2), 32 coarse sweeps,
+   Levermore-Pomraning limiter. */
+void fld_default_opts(fld_opts* o);
+
+/* Create a handle bound to grid *g with options *o; allocates the workspace on
+   the current CUDA device. Returns FLD_ERR_ARG for an invalid grid or options,
+   FLD_ERR_NOMEM if an allocation fails (nothing is leaked). */
+fld_status fld_create(fld_handle** h, const fld_grid* g, const fld_opts* o);
+
+/* Free the handle and its workspace (NULL is accepted). */
+fld_status fld_destroy(fld_handle* h);
+
+/* Replace the handle's options (the grid and workspace are kept). */
+fld_status fld_set_opts(fld_handle* h, const fld_opts* o);
+
+/* Limiter (Eqs. fld_R, fld_lambda, fld_F; Sect. 3 gradient).
+   In:  E, rho, T (device, ncell float64 each; T is only read by a POWER opacity),
+        E_bc (device float64, may be NULL when no side is Dirichlet): the
+        Dirichlet face values packed side after side in the order x-lo, x-hi,
+        y-lo, y-hi, z-lo, z-hi (Dirichlet sides only), each face row-major over
+        the two other axes (the lower axis fastest).
+   Out: D (device, ncell float64) the cell diffusion coefficient c lambda/(kappa rho);
+        lambda (device, ncell float64, may be NULL) the limiter value.
+   Ghost values for the gradient: periodic wrap; Neumann even mirror
+   (E_-1 = E_0, E_-2 = E_1); Dirichlet odd reflection (E_-k = 2 E_b - E_{k-1}).
+   |grad E| = 0 gives lambda = 1/3. Asynchronous. */
+fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op,
+                       const double* E, const double* rho, const double* T,
+                       const double* E_bc, double* D, double* lambda, void* stream);
+
+/* Backward-Euler diffusion step: solves A E^{n+1} = E^n + g in place,
+     (A x)_i = x_i + sum_faces (dt/h_d^2) w_f (x_i - x_j),  w_f = (D_i + D_j)/2,
+   a Dirichlet face adding (dt/h_d^2) 2 D_i (x_i - E_b) (g holds the E_b part),
+   a Neumann face nothing.
+   In:  dt > 0; D (device, ncell float64, > 0); E_bc as for fld_limiter.
+   In/out: E (device, ncell float64): E^n on entry, E^{n+1} on return (the last
+   iterate on FLD_ERR_NOT_CONVERGED).
+   stats may be NULL. Returns after the solve has finished on `stream`. */
+fld_status fld_diffuse(fld_handle* h, double dt, const double* D, const double* E_bc,
+                       double* E, fld_stats* stats, void* stream);
+
+/* Gas-radiation exchange, cell by cell (Eqs. heating, qdot): with
+   chi = dt c kappa rho, c_v = R_gas/(gamma - 1), e = rho c_v T, solves
+   rho c_v T' + (chi/(1+chi)) a_r T'^4 = e + chi E/(1+chi) for the unique positive
+   T' and sets E' = (E + chi a_r T'^4)/(1 + chi). kappa = kappa(rho, T) on entry.
+   In: rho (device float64). In/out: T, E (device float64). Asynchronous. */
+fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
+                        const double* rho, double* T, double* E, void* stream);
+
+/* The whole substep: limiter -> diffuse -> exchange, the opacity frozen at
+   (rho, T^n) for all three. The handle's scratch holds D. Returns after the
+   step has finished on `stream`. */
+fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
+                    const double* rho, double* T, double* E, const double* E_bc,
+                    fld_stats* stats, void* stream);
+
+/* Synchronise `stream` and return (and clear) any device-side error flag. */
+fld_status fld_get_status(fld_handle* h, void* stream);
+
+/* Number of multigrid levels of the handle's pyramid. */
+int fld_num_levels(const fld_handle* h);
+
+/* ---------------------------------------------------------------- profiling
+   While profiling is on, every kernel the handle launches is bracketed by a pair of
+   CUDA events on its stream (up to `capacity` launches; later ones are counted but
+   not timed). fld_prof_read synchronises the device, fills up to `cap` entries, one
+   per (kernel, level), and returns the number of entries; enabling again resets
+   the record. The events are created in fld_prof_enable, never in the timed path. */
+typedef struct {
+    char name[24];          /* kernel family, e.g. "smooth32", "resid64", "exchange" */
+    int level;              /* multigrid level (0 = the caller's grid)              */
+    long long launches;     /* launches timed                                       */
+    long long cells;        /* cells processed over those launches                  */
+    double ms;              /* summed event time                                    */
+} fld_prof_entry;
+
+fld_status fld_prof_enable(fld_handle* h, int on, int capacity);
+int fld_prof_read(fld_handle* h, fld_prof_entry* out, int cap);
+
+/* Number of kernels launched by this library in this process so far. */
+long long fld_launch_count(void);
+
+/* Static string for a status code. */
+const char* fld_strerror(fld_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLD_H */

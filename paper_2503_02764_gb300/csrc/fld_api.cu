@@ -1,0 +1,556 @@
+// Host side of the C ABI declared in include/fld.h: handle and workspace, the
+// multigrid level pyramid, the V-cycle driver (FP64, or FP32 cycles inside FP64
+// iterative refinement) and the substep composition limiter -> diffuse -> exchange.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fld_internal.cuh"
+
+using namespace fld;
+
+namespace {
+
+constexpr int MAX_LEVELS = 24;
+constexpr long long COARSE_TARGET = 64;   // stop coarsening at or below this many cells
+constexpr int NORM_BLOCKS = 152 * 8;      // fixed grid of the residual-norm kernels
+constexpr int NORM_THREADS = 256;
+
+template <typename T>
+struct LevelBufs {
+    T* x = nullptr;
+    T* b = nullptr;
+    T* K = nullptr;
+    T* tmp = nullptr;
+};
+
+struct DevScalars {       // read back together after each cycle
+    double sum;
+    unsigned err;
+    unsigned pad;
+};
+
+std::atomic<long long> g_launches{0};
+
+// Event-bracketed launch record (profiling on).
+struct ProfRec {
+    const char* name;
+    int level;
+    long long cells;
+};
+
+struct Prof {
+    bool on = false;
+    int cap = 0;
+    int used = 0;
+    std::vector<cudaEvent_t> ev;     // 2 per record
+    std::vector<ProfRec> rec;
+};
+
+}  // namespace
+
+struct fld_handle {
+    fld_grid g;
+    fld_opts o;
+    int nlev = 0;
+    Lvl lv[MAX_LEVELS];
+    double kscale_down[MAX_LEVELS];   // K_{l+1} = mean(K_l) * kscale_down[l]
+    long long bc_off[6];
+    long long ncell = 0;
+    LevelBufs<double> d64[MAX_LEVELS];
+    LevelBufs<float> d32[MAX_LEVELS];
+    double* Dscratch = nullptr;
+    double* partials = nullptr;
+    DevScalars* scal = nullptr;       // device
+    DevScalars* hscal = nullptr;      // pinned host
+    std::vector<void*> allocs;
+    Prof prof;
+};
+
+namespace {
+
+fld_status cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return FLD_OK;
+    fprintf(stderr, "fld: CUDA error: %s\n", cudaGetErrorString(e));
+    return FLD_ERR_CUDA;
+}
+
+#define FLD_CK(call)                                          \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_);          \
+    } while (0)
+
+bool grid_ok(const fld_grid* g) {
+    if (!g || g->ndim < 1 || g->ndim > 3) return false;
+    long long n = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < g->ndim) {
+            if (g->n[d] < 2 || !(g->h[d] > 0) || !std::isfinite(g->h[d])) return false;
+            for (int s = 0; s < 2; ++s) {
+                int k = s ? g->bc_hi[d] : g->bc_lo[d];
+                if (k < FLD_BC_PERIODIC || k > FLD_BC_DIRICHLET) return false;
+            }
+            if ((g->bc_lo[d] == FLD_BC_PERIODIC) != (g->bc_hi[d] == FLD_BC_PERIODIC)) return false;
+        } else if (g->n[d] != 1) {
+            return false;
+        }
+        n *= g->n[d];
+    }
+    return n < (1LL << 31);
+}
+
+bool opts_ok(const fld_opts* o) {
+    return o && (o->precision == FLD_PREC_FP64 || o->precision == FLD_PREC_MIXED) && o->tol > 0 &&
+           o->max_cycles >= 1 && o->nu1 >= 0 && o->nu2 >= 0 && (o->nu1 + o->nu2) >= 1 &&
+           o->coarse_sweeps >= 1 &&
+           (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION) &&
+           (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0));
+}
+
+Opacity to_op(const fld_opacity* op) {
+    Opacity o;
+    o.kind = op->kind;
+    o.kappa0 = op->kappa0;
+    o.a_rho = op->a_rho;
+    o.a_T = op->a_T;
+    return o;
+}
+
+bool op_ok(const fld_opacity* op) {
+    return op && (op->kind == FLD_OPACITY_CONST || op->kind == FLD_OPACITY_POWER) &&
+           op->kappa0 > 0 && std::isfinite(op->kappa0) && std::isfinite(op->a_rho) &&
+           std::isfinite(op->a_T);
+}
+
+bool consts_ok(const fld_consts* k) {
+    return k && k->c > 0 && k->a_r > 0 && k->gamma > 1 && k->R_gas > 0 && std::isfinite(k->c) &&
+           std::isfinite(k->a_r) && std::isfinite(k->gamma) && std::isfinite(k->R_gas);
+}
+
+bool has_dirichlet(const fld_grid& g) {
+    for (int d = 0; d < g.ndim; ++d)
+        if (g.bc_lo[d] == FLD_BC_DIRICHLET || g.bc_hi[d] == FLD_BC_DIRICHLET) return true;
+    return false;
+}
+
+void build_levels(fld_handle* h) {
+    const fld_grid& g = h->g;
+    Lvl L{};
+    double H[3], len[3];
+    for (int d = 0; d < 3; ++d) {
+        L.n[d] = g.n[d];
+        L.bclo[d] = d < g.ndim ? g.bc_lo[d] : FLD_BC_PERIODIC;
+        L.bchi[d] = d < g.ndim ? g.bc_hi[d] : FLD_BC_PERIODIC;
+        H[d] = d < g.ndim ? g.h[d] : 1.0;
+        len[d] = H[d] * g.n[d];
+    }
+    L.ndim = g.ndim;
+    int nl = 0;
+    for (;;) {
+        L.ncell = (long long)L.n[0] * L.n[1] * L.n[2];
+        for (int d = 0; d < 3; ++d) L.w[d] = d < g.ndim ? (H[0] / H[d]) * (H[0] / H[d]) : 0.0;
+        h->lv[nl++] = L;
+        bool can = false;
+        for (int d = 0; d < g.ndim; ++d) can |= L.n[d] >= 4;
+        if (!can || L.ncell <= COARSE_TARGET || nl == MAX_LEVELS) break;
+        const double Hx_old = H[0];
+        for (int d = 0; d < g.ndim; ++d) {
+            if (L.n[d] >= 4) {
+                L.n[d] = (L.n[d] + 1) / 2;
+                H[d] = len[d] / L.n[d];
+            }
+        }
+        h->kscale_down[nl - 1] = (Hx_old / H[0]) * (Hx_old / H[0]);
+    }
+    h->nlev = nl;
+}
+
+template <typename T>
+fld_status dalloc(fld_handle* h, T** p, long long n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (size_t)std::max<long long>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FLD_ERR_NOMEM;
+    }
+    h->allocs.push_back(q);
+    *p = (T*)q;
+    return FLD_OK;
+}
+
+void free_all(fld_handle* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->hscal) cudaFreeHost(h->hscal);
+    h->hscal = nullptr;
+}
+
+int blk(const fld_handle* h) { return h->o.block ? h->o.block : 256; }
+
+// Launch `f` (which enqueues exactly one kernel on s), counting it and, when
+// profiling is on, bracketing it with events.
+template <typename F>
+void run(fld_handle* h, const char* name, int level, long long cells, cudaStream_t s, F&& f) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    Prof& P = h->prof;
+    const bool timed = P.on && P.used < P.cap;
+    if (timed) cudaEventRecord(P.ev[2 * P.used], s);
+    f();
+    if (timed) {
+        cudaEventRecord(P.ev[2 * P.used + 1], s);
+        P.rec[P.used] = ProfRec{name, level, cells};
+        ++P.used;
+    }
+}
+
+void prof_free(fld_handle* h) {
+    for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+    h->prof.ev.clear();
+    h->prof.rec.clear();
+    h->prof.cap = h->prof.used = 0;
+    h->prof.on = false;
+}
+
+// -------------------------------------------------- V-cycle on level l (x_l in/out)
+template <typename T>
+void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
+    const Lvl& L = h->lv[l];
+    LevelBufs<T>& B = P[l];
+    const bool f32 = sizeof(T) == 4;
+    if (l == h->nlev - 1) {
+        run(h, f32 ? "coarse32" : "coarse64", l, L.ncell, s,
+            [&] { launch_coarse_solve<T>(L, B.x, B.b, B.K, h->o.coarse_sweeps, s); });
+        return;
+    }
+    const int bs = blk(h);
+    const char* sm = f32 ? "smooth32" : "smooth64";
+    for (int it = 0; it < h->o.nu1; ++it) {
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, B.x, B.tmp, B.b, B.K, bs, s); });
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, B.tmp, B.x, B.b, B.K, bs, s); });
+    }
+    const Lvl& C = h->lv[l + 1];
+    run(h, f32 ? "resid_restrict32" : "resid_restrict64", l, L.ncell, s,
+        [&] { launch_resid_restrict<T>(L, C, B.x, B.b, B.K, P[l + 1].b, bs, s); });
+    if (l + 1 < h->nlev - 1) cudaMemsetAsync(P[l + 1].x, 0, sizeof(T) * C.ncell, s);
+    vcycle<T>(h, P, l + 1, s);
+    run(h, f32 ? "prolong32" : "prolong64", l, L.ncell, s,
+        [&] { launch_prolong<T>(L, C, B.x, P[l + 1].x, bs, s); });
+    for (int it = 0; it < h->o.nu2; ++it) {
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, B.x, B.tmp, B.b, B.K, bs, s); });
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, B.tmp, B.x, B.b, B.K, bs, s); });
+    }
+}
+
+template <typename T>
+void restrict_pyramid(fld_handle* h, LevelBufs<T>* P, cudaStream_t s) {
+    for (int l = 0; l + 1 < h->nlev; ++l)
+        run(h, "restrict_K", l, h->lv[l + 1].ncell, s, [&] {
+            launch_restrict_K<T>(h->lv[l], h->lv[l + 1], h->kscale_down[l], P[l].K, P[l + 1].K, s);
+        });
+}
+
+fld_status read_scalars(fld_handle* h, cudaStream_t s, double* sum, unsigned* err) {
+    FLD_CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    FLD_CK(cudaStreamSynchronize(s));
+    *sum = h->hscal->sum;
+    *err = h->hscal->err;
+    return FLD_OK;
+}
+
+// relative residual of x at level 0 (FP64), optional FP32 copy of the residual
+fld_status residual(fld_handle* h, double* x, float* r32, cudaStream_t s, double* rr,
+                    unsigned* err) {
+    const Lvl& L = h->lv[0];
+    run(h, "resid64", 0, L.ncell, s, [&] {
+        launch_resid64(L, x, h->d64[0].b, h->d64[0].K, r32, h->partials, NORM_BLOCKS, NORM_THREADS, s);
+    });
+    run(h, "finish_sum", 0, NORM_BLOCKS, s,
+        [&] { launch_finish_sum(h->partials, NORM_BLOCKS, &h->scal->sum, s); });
+    FLD_CK(cudaGetLastError());
+    return read_scalars(h, s, rr, err);
+}
+
+fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double* E_bc, double* E,
+                        fld_stats* st, cudaStream_t s) {
+    const Lvl& L0 = h->lv[0];
+    const bool mixed = h->o.precision == FLD_PREC_MIXED;
+    const double kscale = dt / (h->g.h[0] * h->g.h[0]);
+    run(h, "prep", 0, L0.ncell, s, [&] {
+        launch_prep_level0(L0, kscale, D, E, E_bc, h->bc_off, h->d64[0].K,
+                           mixed ? h->d32[0].K : nullptr, h->d64[0].b, &h->scal->err, s);
+    });
+    if (mixed) restrict_pyramid<float>(h, h->d32, s);
+    else restrict_pyramid<double>(h, h->d64, s);
+    run(h, "sumsq", 0, L0.ncell, s,
+        [&] { launch_sumsq(L0.ncell, h->d64[0].b, h->partials, NORM_BLOCKS, s); });
+    run(h, "finish_sum", 0, NORM_BLOCKS, s,
+        [&] { launch_finish_sum(h->partials, NORM_BLOCKS, &h->scal->sum, s); });
+    FLD_CK(cudaGetLastError());
+    double bsum;
+    unsigned err;
+    fld_status rc = read_scalars(h, s, &bsum, &err);
+    if (rc != FLD_OK) return rc;
+    if (err) {
+        cudaMemsetAsync(&h->scal->err, 0, sizeof(unsigned), s);
+        return FLD_ERR_DOMAIN;
+    }
+    const double bnorm = std::sqrt(bsum);
+    h->d64[0].x = E;
+    double r2;
+    rc = residual(h, E, mixed ? h->d32[0].b : nullptr, s, &r2, &err);
+    if (rc != FLD_OK) return rc;
+    double rel = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->resid_hist[0] = rel;
+        st->levels = h->nlev;
+    }
+    int cyc = 0;
+    while (rel > h->o.tol && cyc < h->o.max_cycles && std::isfinite(rel)) {
+        if (mixed) {
+            FLD_CK(cudaMemsetAsync(h->d32[0].x, 0, sizeof(float) * L0.ncell, s));
+            vcycle<float>(h, h->d32, 0, s);
+            run(h, "add_correction", 0, L0.ncell, s,
+                [&] { launch_add_correction(L0.ncell, E, h->d32[0].x, s); });
+            rc = residual(h, E, h->d32[0].b, s, &r2, &err);
+        } else {
+            vcycle<double>(h, h->d64, 0, s);
+            rc = residual(h, E, nullptr, s, &r2, &err);
+        }
+        if (rc != FLD_OK) return rc;
+        rel = std::sqrt(r2) / bnorm;
+        ++cyc;
+        if (st && cyc < 64) st->resid_hist[cyc] = rel;
+    }
+    if (st) {
+        st->cycles = cyc;
+        st->rel_resid = rel;
+    }
+    if (!std::isfinite(rel)) return FLD_ERR_DOMAIN;
+    return rel <= h->o.tol ? FLD_OK : FLD_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fld_default_opts(fld_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = FLD_PREC_FP64;
+    o->tol = 1e-10;
+    o->max_cycles = 50;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->coarse_sweeps = 32;
+    o->limiter = FLD_LIMITER_LP;
+    o->block = 0;
+}
+
+fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
+    if (!out) return FLD_ERR_ARG;
+    *out = nullptr;
+    if (!grid_ok(g)) return FLD_ERR_ARG;
+    fld_opts def;
+    fld_default_opts(&def);
+    if (!o) o = &def;
+    if (!opts_ok(o)) return FLD_ERR_ARG;
+    fld_handle* h = new (std::nothrow) fld_handle();
+    if (!h) return FLD_ERR_NOMEM;
+    h->g = *g;
+    h->o = *o;
+    build_levels(h);
+    h->ncell = h->lv[0].ncell;
+    // Dirichlet face offsets (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi)
+    long long off = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+            const int kind = s ? g->bc_hi[d] : g->bc_lo[d];
+            if (d < g->ndim && kind == FLD_BC_DIRICHLET) {
+                h->bc_off[2 * d + s] = off;
+                off += h->ncell / g->n[d];
+            } else {
+                h->bc_off[2 * d + s] = -1;
+            }
+        }
+    fld_status rc = FLD_OK;
+    const long long n0 = h->ncell;
+    rc = rc ? rc : dalloc(h, &h->d64[0].b, n0);
+    rc = rc ? rc : dalloc(h, &h->d64[0].K, n0);
+    rc = rc ? rc : dalloc(h, &h->d64[0].tmp, n0);
+    for (int l = 1; l < h->nlev && !rc; ++l) {
+        const long long n = h->lv[l].ncell;
+        rc = rc ? rc : dalloc(h, &h->d64[l].x, n);
+        rc = rc ? rc : dalloc(h, &h->d64[l].b, n);
+        rc = rc ? rc : dalloc(h, &h->d64[l].K, n);
+        rc = rc ? rc : dalloc(h, &h->d64[l].tmp, n);
+    }
+    for (int l = 0; l < h->nlev && !rc; ++l) {
+        const long long n = h->lv[l].ncell;
+        rc = rc ? rc : dalloc(h, &h->d32[l].x, n);
+        rc = rc ? rc : dalloc(h, &h->d32[l].b, n);
+        rc = rc ? rc : dalloc(h, &h->d32[l].K, n);
+        rc = rc ? rc : dalloc(h, &h->d32[l].tmp, n);
+    }
+    rc = rc ? rc : dalloc(h, &h->Dscratch, n0);
+    rc = rc ? rc : dalloc(h, &h->partials, NORM_BLOCKS);
+    rc = rc ? rc : dalloc(h, &h->scal, 1);
+    if (!rc && cudaMallocHost(&h->hscal, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = FLD_ERR_NOMEM;
+    }
+    if (!rc && cudaMemset(h->scal, 0, sizeof(DevScalars)) != cudaSuccess) rc = FLD_ERR_CUDA;
+    if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = FLD_ERR_CUDA;
+    if (rc) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return FLD_OK;
+}
+
+fld_status fld_destroy(fld_handle* h) {
+    if (!h) return FLD_OK;
+    cudaDeviceSynchronize();
+    prof_free(h);
+    free_all(h);
+    delete h;
+    return FLD_OK;
+}
+
+fld_status fld_set_opts(fld_handle* h, const fld_opts* o) {
+    if (!h || !opts_ok(o)) return FLD_ERR_ARG;
+    h->o = *o;
+    return FLD_OK;
+}
+
+int fld_num_levels(const fld_handle* h) { return h ? h->nlev : 0; }
+
+fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op, const double* E,
+                       const double* rho, const double* T, const double* E_bc, double* D,
+                       double* lambda, void* stream) {
+    if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho || !D) return FLD_ERR_ARG;
+    if (op->kind == FLD_OPACITY_POWER && !T) return FLD_ERR_ARG;
+    if (has_dirichlet(h->g) && !E_bc && h->o.limiter == FLD_LIMITER_LP) return FLD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    run(h, "limiter", 0, h->ncell, s, [&] {
+        launch_limiter(h->lv[0], h->g.h, E, rho, T, E_bc, h->bc_off, to_op(op), k->c, h->o.limiter,
+                       D, lambda, &h->scal->err, s);
+    });
+    FLD_CK(cudaGetLastError());
+    return FLD_OK;
+}
+
+fld_status fld_diffuse(fld_handle* h, double dt, const double* D, const double* E_bc, double* E,
+                       fld_stats* stats, void* stream) {
+    if (!h || !D || !E || !(dt > 0) || !std::isfinite(dt)) return FLD_ERR_ARG;
+    if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
+    return diffuse_impl(h, dt, D, E_bc, E, stats, (cudaStream_t)stream);
+}
+
+fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
+                        const double* rho, double* T, double* E, void* stream) {
+    if (!h || !consts_ok(k) || !op_ok(op) || !rho || !T || !E || !(dt >= 0) || !std::isfinite(dt))
+        return FLD_ERR_ARG;
+    run(h, "exchange", 0, h->ncell, (cudaStream_t)stream, [&] {
+        launch_exchange(h->ncell, rho, T, E, to_op(op), dt * k->c, k->a_r,
+                        k->R_gas / (k->gamma - 1.0), &h->scal->err, (cudaStream_t)stream);
+    });
+    FLD_CK(cudaGetLastError());
+    return FLD_OK;
+}
+
+fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
+                    const double* rho, double* T, double* E, const double* E_bc, fld_stats* stats,
+                    void* stream) {
+    if (!h || !consts_ok(k) || !op_ok(op) || !rho || !T || !E || !(dt > 0) || !std::isfinite(dt))
+        return FLD_ERR_ARG;
+    if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    fld_status rc = fld_limiter(h, k, op, E, rho, T, E_bc, h->Dscratch, nullptr, stream);
+    if (rc) return rc;
+    rc = diffuse_impl(h, dt, h->Dscratch, E_bc, E, stats, s);
+    if (rc) return rc;
+    rc = fld_exchange(h, k, op, dt, rho, T, E, stream);
+    if (rc) return rc;
+    return fld_get_status(h, stream);
+}
+
+fld_status fld_get_status(fld_handle* h, void* stream) {
+    if (!h) return FLD_ERR_ARG;
+    double sum;
+    unsigned err;
+    fld_status rc = read_scalars(h, (cudaStream_t)stream, &sum, &err);
+    if (rc) return rc;
+    if (err) {
+        FLD_CK(cudaMemsetAsync(&h->scal->err, 0, sizeof(unsigned), (cudaStream_t)stream));
+        FLD_CK(cudaStreamSynchronize((cudaStream_t)stream));
+        if (err & ERRBIT_TIMEOUT) return FLD_ERR_TIMEOUT;
+        return FLD_ERR_DOMAIN;
+    }
+    return FLD_OK;
+}
+
+fld_status fld_prof_enable(fld_handle* h, int on, int capacity) {
+    if (!h || capacity < 0) return FLD_ERR_ARG;
+    FLD_CK(cudaDeviceSynchronize());
+    prof_free(h);
+    if (!on) return FLD_OK;
+    Prof& P = h->prof;
+    P.ev.resize(2 * (size_t)capacity);
+    for (auto& e : P.ev) FLD_CK(cudaEventCreate(&e));
+    P.rec.resize(capacity);
+    P.cap = capacity;
+    P.used = 0;
+    P.on = true;
+    return FLD_OK;
+}
+
+int fld_prof_read(fld_handle* h, fld_prof_entry* out, int cap) {
+    if (!h || !out || cap <= 0) return 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return 0;
+    Prof& P = h->prof;
+    int nout = 0;
+    for (int r = 0; r < P.used; ++r) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, P.ev[2 * r], P.ev[2 * r + 1]);
+        int slot = -1;
+        for (int q = 0; q < nout; ++q)
+            if (out[q].level == P.rec[r].level && strcmp(out[q].name, P.rec[r].name) == 0) slot = q;
+        if (slot < 0) {
+            if (nout == cap) continue;
+            slot = nout++;
+            memset(&out[slot], 0, sizeof(out[slot]));
+            strncpy(out[slot].name, P.rec[r].name, sizeof(out[slot].name) - 1);
+            out[slot].level = P.rec[r].level;
+        }
+        out[slot].launches += 1;
+        out[slot].cells += P.rec[r].cells;
+        out[slot].ms += ms;
+    }
+    return nout;
+}
+
+long long fld_launch_count(void) { return g_launches.load(); }
+
+const char* fld_strerror(fld_status s) {
+    switch (s) {
+        case FLD_OK: return "ok";
+        case FLD_ERR_ARG: return "invalid argument";
+        case FLD_ERR_DOMAIN: return "non-positive or non-finite field value";
+        case FLD_ERR_NOT_CONVERGED: return "multigrid did not reach the tolerance";
+        case FLD_ERR_TIMEOUT: return "bounded device wait expired";
+        case FLD_ERR_CUDA: return "CUDA runtime error";
+        case FLD_ERR_NOMEM: return "device allocation failed";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

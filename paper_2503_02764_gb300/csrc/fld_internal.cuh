@@ -1,0 +1,74 @@
+// Internal declarations shared by the FLD CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fld.h"
+
+namespace fld {
+
+// Device error bits (OR-ed into the handle's status word).
+enum : unsigned { ERRBIT_DOMAIN = 1u, ERRBIT_TIMEOUT = 2u };
+
+// One multigrid level of a uniform block. The operator at this level is
+//   (A x)_p = x_p + sum_faces 0.5 (K_p + K_q) w_d (x_p - x_q) + sum_dirichlet 2 K_p w_d x_p
+// with K = dt D / H_x^2 (stored per cell) and w_d = (H_x / H_d)^2.
+struct Lvl {
+    int n[3];       // nx, ny, nz (1 for absent axes)
+    int ndim;
+    int bclo[3];
+    int bchi[3];
+    double w[3];    // axis weights (H_x / H_d)^2
+    long long ncell;
+};
+
+// Opacity law evaluated in FP64: kappa0 (kind 0) or kappa0 rho^a T^b (kind 1).
+struct Opacity {
+    int kind;
+    double kappa0, a_rho, a_T;
+};
+
+__device__ __forceinline__ double opacity_eval(const Opacity& op, double rho, double T) {
+    if (op.kind == FLD_OPACITY_CONST) return op.kappa0;
+    double fr = (op.a_rho == 1.0) ? rho : pow(rho, op.a_rho);
+    double ft;
+    if (op.a_T == 0.0) ft = 1.0;
+    else if (op.a_T == -3.5) ft = 1.0 / (T * T * T * sqrt(T));   // Kramers-like law
+    else ft = pow(T, op.a_T);
+    return op.kappa0 * fr * ft;
+}
+
+__device__ __forceinline__ bool pos_finite(double v) { return v > 0.0 && v < INFINITY; }
+
+// ----------------------------------------------------------------- launchers
+// pointwise / limiter (k_pointwise.cu)
+void launch_exchange(long long n, const double* rho, double* T, double* E, Opacity op,
+                     double dtc, double a_r, double cv, unsigned* err, cudaStream_t s);
+void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
+                    const double* T, const double* E_bc, const long long* bc_off, Opacity op,
+                    double c, int mode, double* D, double* lam, unsigned* err, cudaStream_t s);
+
+// multigrid (k_mg.cu)
+void launch_prep_level0(const Lvl& L, double kscale, const double* D, const double* E,
+                        const double* E_bc, const long long* bc_off, double* K64, float* K32,
+                        double* b, unsigned* err, cudaStream_t s);
+template <typename T>
+void launch_restrict_K(const Lvl& F, const Lvl& C, double scale, const T* Kf, T* Kc,
+                       cudaStream_t s);
+template <typename T>
+void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, const T* K,
+                   int block, cudaStream_t s);
+template <typename T>
+void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K,
+                           T* bc, int block, cudaStream_t s);
+template <typename T>
+void launch_prolong(const Lvl& F, const Lvl& C, T* xf, const T* xc, int block, cudaStream_t s);
+template <typename T>
+void launch_coarse_solve(const Lvl& L, T* x, const T* b, const T* K, int sweeps, cudaStream_t s);
+void launch_resid64(const Lvl& L, const double* x, const double* b, const double* K,
+                    float* r32, double* partials, int nblocks, int block, cudaStream_t s);
+void launch_add_correction(long long n, double* x, const float* e, cudaStream_t s);
+void launch_sumsq(long long n, const double* v, double* partials, int nblocks, cudaStream_t s);
+void launch_finish_sum(const double* partials, int nparts, double* out, cudaStream_t s);
+
+}  // namespace fld

@@ -1,0 +1,364 @@
+// Geometric multigrid kernels for the backward-Euler diffusion solve
+//   A x = x - dt div(D grad x) = b
+// on cell-centred finite volumes (face D = mean of the two cell values).
+// Per level the operator is stored as K = dt D / H_x^2 per cell with axis weights
+// w_d = (H_x/H_d)^2:
+//   (A x)_p = x_p + sum_{faces p|q} 0.5 (K_p + K_q) w_d (x_p - x_q) + sum_{Dirichlet} 2 K_p w_d x_p.
+// Coarse levels average K over the (up to 2^d) children and rescale it to the coarse
+// spacing; restriction averages residuals; prolongation is piecewise constant.
+// Every kernel here is templated on the storage/arithmetic type (double or float).
+#include "fld_internal.cuh"
+
+namespace fld {
+
+static inline int grid_for(long long n, int block, int cap = 152 * 32) {
+    long long nb = (n + block - 1) / block;
+    if (nb > cap) nb = cap;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+__device__ __forceinline__ void decode(const Lvl& L, long long p, int& i, int& j, int& k) {
+    i = (int)(p % L.n[0]);
+    const long long q = p / L.n[0];
+    j = (int)(q % L.n[1]);
+    k = (int)(q / L.n[1]);
+}
+
+// Off-diagonal sum and diagonal excess of the level operator at cell p:
+//   sw  = sum of face weights (+ 2 K_p w_d per Dirichlet face),  acc = sum w_f x_q,
+// so (A x)_p = (1 + sw) x_p - acc.
+template <typename T>
+__device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
+                                        const T* __restrict__ x, int i, int j, int k, long long p,
+                                        T& sw, T& acc) {
+    const T Kc = K[p];
+    const int c[3] = {i, j, k};
+    long long stride = 1;
+    sw = T(0);
+    acc = T(0);
+    for (int d = 0; d < L.ndim; ++d) {
+        const int n = L.n[d];
+        const T wd = (T)L.w[d];
+        // low face
+        long long q = -1;
+        if (c[d] > 0) q = p - stride;
+        else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (long long)(n - 1) * stride;
+        if (q >= 0) {
+            const T w = T(0.5) * (Kc + K[q]) * wd;
+            sw += w;
+            acc += w * x[q];
+        } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
+            sw += T(2) * Kc * wd;
+        }
+        // high face
+        q = -1;
+        if (c[d] < n - 1) q = p + stride;
+        else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (long long)(n - 1) * stride;
+        if (q >= 0) {
+            const T w = T(0.5) * (Kc + K[q]) * wd;
+            sw += w;
+            acc += w * x[q];
+        } else if (L.bchi[d] == FLD_BC_DIRICHLET) {
+            sw += T(2) * Kc * wd;
+        }
+        stride *= n;
+    }
+}
+
+// ----------------------------------------------------------------- level-0 set-up
+// K = kscale D (kscale = dt / h_x^2), its FP32 copy, and b = E + Dirichlet face terms
+// 2 K w_d E_b.
+struct BcOffM {
+    long long off[6];
+};
+
+__global__ void k_prep_level0(Lvl L, double kscale, const double* __restrict__ D,
+                              const double* __restrict__ E, const double* __restrict__ Ebc,
+                              BcOffM bo, double* __restrict__ K64, float* __restrict__ K32,
+                              double* __restrict__ b, unsigned* err) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
+         p += (long long)gridDim.x * blockDim.x) {
+        const double Dp = D[p];
+        if (!pos_finite(Dp)) atomicOr(err, ERRBIT_DOMAIN);
+        const double Kp = kscale * Dp;
+        K64[p] = Kp;
+        if (K32) K32[p] = (float)Kp;
+        double bp = E[p];
+        if (Ebc) {
+            int c[3];
+            decode(L, p, c[0], c[1], c[2]);
+            for (int d = 0; d < L.ndim; ++d) {
+                long long fi;
+                if (d == 0) fi = (long long)c[2] * L.n[1] + c[1];
+                else if (d == 1) fi = (long long)c[2] * L.n[0] + c[0];
+                else fi = (long long)c[1] * L.n[0] + c[0];
+                if (c[d] == 0 && L.bclo[d] == FLD_BC_DIRICHLET)
+                    bp += 2.0 * Kp * L.w[d] * Ebc[bo.off[2 * d] + fi];
+                if (c[d] == L.n[d] - 1 && L.bchi[d] == FLD_BC_DIRICHLET)
+                    bp += 2.0 * Kp * L.w[d] * Ebc[bo.off[2 * d + 1] + fi];
+            }
+        }
+        b[p] = bp;
+    }
+}
+
+void launch_prep_level0(const Lvl& L, double kscale, const double* D, const double* E,
+                        const double* E_bc, const long long* bc_off, double* K64, float* K32,
+                        double* b, unsigned* err, cudaStream_t s) {
+    BcOffM bo;
+    for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
+    k_prep_level0<<<grid_for(L.ncell, 256), 256, 0, s>>>(L, kscale, D, E, E_bc, bo, K64, K32, b,
+                                                         err);
+}
+
+// ----------------------------------------------------------------- transfers
+// Children of coarse index I along axis d: {2I, 2I+1} (clipped) if the axis was
+// coarsened, else {I}.
+template <typename T>
+__global__ void k_restrict_K(Lvl F, Lvl C, double scale, const T* __restrict__ Kf,
+                             T* __restrict__ Kc) {
+    for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < C.ncell;
+         P += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        decode(C, P, c[0], c[1], c[2]);
+        int lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            if (C.n[d] < F.n[d]) {
+                lo[d] = 2 * c[d];
+                hi[d] = min(2 * c[d] + 1, F.n[d] - 1);
+            } else {
+                lo[d] = hi[d] = c[d];
+            }
+        }
+        double s = 0.0;
+        int cnt = 0;
+        for (int k = lo[2]; k <= hi[2]; ++k)
+            for (int j = lo[1]; j <= hi[1]; ++j)
+                for (int i = lo[0]; i <= hi[0]; ++i) {
+                    s += (double)Kf[((long long)k * F.n[1] + j) * F.n[0] + i];
+                    ++cnt;
+                }
+        Kc[P] = (T)(scale * s / cnt);
+    }
+}
+
+template <typename T>
+void launch_restrict_K(const Lvl& F, const Lvl& C, double scale, const T* Kf, T* Kc,
+                       cudaStream_t s) {
+    k_restrict_K<T><<<grid_for(C.ncell, 256), 256, 0, s>>>(F, C, scale, Kf, Kc);
+}
+
+// Red-black Gauss-Seidel half sweep, out of place: cells of `color` ((i+j+k) mod 2)
+// get (b + acc)/(1 + sw) from xin; the other colour is copied. Reading xin only makes
+// the result independent of thread order; on an odd periodic extent two same-colour
+// neighbours across the wrap then couple Jacobi-style.
+template <typename T>
+__global__ void k_smooth(Lvl L, int color, const T* __restrict__ xin, T* __restrict__ xout,
+                         const T* __restrict__ b, const T* __restrict__ K) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
+         p += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(L, p, i, j, k);
+        if (((i + j + k) & 1) != color) {
+            xout[p] = xin[p];
+            continue;
+        }
+        T sw, acc;
+        stencil<T>(L, K, xin, i, j, k, p, sw, acc);
+        xout[p] = (b[p] + acc) / (T(1) + sw);
+    }
+}
+
+template <typename T>
+void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, const T* K,
+                   int block, cudaStream_t s) {
+    k_smooth<T><<<grid_for(L.ncell, block), block, 0, s>>>(L, color, xin, xout, b, K);
+}
+
+// Coarse right-hand side = average of the fine residuals b - A x over the children.
+template <typename T>
+__global__ void k_resid_restrict(Lvl F, Lvl C, const T* __restrict__ x, const T* __restrict__ b,
+                                 const T* __restrict__ K, T* __restrict__ bc) {
+    for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < C.ncell;
+         P += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        decode(C, P, c[0], c[1], c[2]);
+        int lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            if (C.n[d] < F.n[d]) {
+                lo[d] = 2 * c[d];
+                hi[d] = min(2 * c[d] + 1, F.n[d] - 1);
+            } else {
+                lo[d] = hi[d] = c[d];
+            }
+        }
+        T s = T(0);
+        int cnt = 0;
+        for (int k = lo[2]; k <= hi[2]; ++k)
+            for (int j = lo[1]; j <= hi[1]; ++j)
+                for (int i = lo[0]; i <= hi[0]; ++i) {
+                    const long long p = ((long long)k * F.n[1] + j) * F.n[0] + i;
+                    T sw, acc;
+                    stencil<T>(F, K, x, i, j, k, p, sw, acc);
+                    s += b[p] - (T(1) + sw) * x[p] + acc;
+                    ++cnt;
+                }
+        bc[P] = s / T(cnt);
+    }
+}
+
+template <typename T>
+void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
+                           int block, cudaStream_t s) {
+    k_resid_restrict<T><<<grid_for(C.ncell, block), block, 0, s>>>(F, C, x, b, K, bc);
+}
+
+// x_fine += x_coarse[parent], parent index = i/2 along coarsened axes.
+template <typename T>
+__global__ void k_prolong(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict__ xc) {
+    const int sx = C.n[0] < F.n[0], sy = C.n[1] < F.n[1], sz = C.n[2] < F.n[2];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < F.ncell;
+         p += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(F, p, i, j, k);
+        const long long P = ((long long)(k >> sz) * C.n[1] + (j >> sy)) * C.n[0] + (i >> sx);
+        xf[p] += xc[P];
+    }
+}
+
+template <typename T>
+void launch_prolong(const Lvl& F, const Lvl& C, T* xf, const T* xc, int block, cudaStream_t s) {
+    k_prolong<T><<<grid_for(F.ncell, block), block, 0, s>>>(F, C, xf, xc);
+}
+
+// Coarsest level: `sweeps` red-black sweeps from x = 0 by one block, in FP64 whatever
+// the storage type, the level held in shared memory (ncell <= MAX_COARSE, 32 KB).
+constexpr int MAX_COARSE = 1024;
+
+template <typename T>
+__global__ void k_coarse_solve(Lvl L, T* __restrict__ x, const T* __restrict__ b,
+                               const T* __restrict__ K, int sweeps) {
+    __shared__ double xs[MAX_COARSE], bs[MAX_COARSE], Ks[MAX_COARSE], nx[MAX_COARSE];
+    const int n = (int)L.ncell;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        xs[p] = 0.0;
+        bs[p] = (double)b[p];
+        Ks[p] = (double)K[p];
+    }
+    __syncthreads();
+    for (int it = 0; it < sweeps; ++it) {
+        for (int color = 0; color < 2; ++color) {
+            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                int i, j, k;
+                decode(L, p, i, j, k);
+                if (((i + j + k) & 1) != color) continue;
+                double sw, acc;
+                stencil<double>(L, Ks, xs, i, j, k, p, sw, acc);
+                nx[p] = (bs[p] + acc) / (1.0 + sw);
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                int i, j, k;
+                decode(L, p, i, j, k);
+                if (((i + j + k) & 1) == color) xs[p] = nx[p];
+            }
+            __syncthreads();
+        }
+    }
+    for (int p = threadIdx.x; p < n; p += blockDim.x) x[p] = (T)xs[p];
+}
+
+template <typename T>
+void launch_coarse_solve(const Lvl& L, T* x, const T* b, const T* K, int sweeps, cudaStream_t s) {
+    k_coarse_solve<T><<<1, 256, 0, s>>>(L, x, b, K, sweeps);
+}
+
+// ----------------------------------------------------------------- FP64 residual + norms
+// r = b - A x in FP64; optional FP32 copy; per-block partial sums of r^2 (fixed
+// grid and fixed tree, so the sum is deterministic).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void k_resid64(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
+                          const double* __restrict__ K, float* __restrict__ r32,
+                          double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double acc2 = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
+         p += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(L, p, i, j, k);
+        double sw, acc;
+        stencil<double>(L, K, x, i, j, k, p, sw, acc);
+        const double r = b[p] - (1.0 + sw) * x[p] + acc;
+        if (r32) r32[p] = (float)r;
+        acc2 = fma(r, r, acc2);
+    }
+    acc2 = block_sum(acc2, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc2;
+}
+
+void launch_resid64(const Lvl& L, const double* x, const double* b, const double* K, float* r32,
+                    double* partials, int nblocks, int block, cudaStream_t s) {
+    k_resid64<<<nblocks, block, 0, s>>>(L, x, b, K, r32, partials);
+}
+
+__global__ void k_add_correction(long long n, double* __restrict__ x, const float* __restrict__ e) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        x[p] += (double)e[p];
+}
+
+void launch_add_correction(long long n, double* x, const float* e, cudaStream_t s) {
+    k_add_correction<<<grid_for(n, 256), 256, 0, s>>>(n, x, e);
+}
+
+__global__ void k_sumsq(long long n, const double* __restrict__ v, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        a = fma(v[p], v[p], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+}
+
+void launch_sumsq(long long n, const double* v, double* partials, int nblocks, cudaStream_t s) {
+    k_sumsq<<<nblocks, 256, 0, s>>>(n, v, partials);
+}
+
+__global__ void k_finish_sum(const double* __restrict__ partials, int nparts, double* out) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += blockDim.x) a += partials[q];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) *out = a;
+}
+
+void launch_finish_sum(const double* partials, int nparts, double* out, cudaStream_t s) {
+    k_finish_sum<<<1, 1024, 0, s>>>(partials, nparts, out);
+}
+
+// explicit instantiations
+#define FLD_INST(T)                                                                              \
+    template void launch_restrict_K<T>(const Lvl&, const Lvl&, double, const T*, T*, cudaStream_t); \
+    template void launch_smooth<T>(const Lvl&, int, const T*, T*, const T*, const T*, int,         \
+                                   cudaStream_t);                                                \
+    template void launch_resid_restrict<T>(const Lvl&, const Lvl&, const T*, const T*, const T*,  \
+                                           T*, int, cudaStream_t);                               \
+    template void launch_prolong<T>(const Lvl&, const Lvl&, T*, const T*, int, cudaStream_t);     \
+    template void launch_coarse_solve<T>(const Lvl&, T*, const T*, const T*, int, cudaStream_t);
+FLD_INST(double)
+FLD_INST(float)
+
+}  // namespace fld

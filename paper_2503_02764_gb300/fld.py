@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the C ABI in include/fld.h (argument marshalling only).
+
+Every step of the substep runs in the CUDA library libfld_gb300.so; this module
+only converts torch tensors to device pointers and Python numbers to the C
+structs. Loading fails loudly if the library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libfld_gb300.so")
+
+FLD_OK, FLD_ERR_ARG, FLD_ERR_DOMAIN, FLD_ERR_NOT_CONVERGED, FLD_ERR_TIMEOUT, FLD_ERR_CUDA, \
+    FLD_ERR_NOMEM = range(7)
+PREC_FP64, PREC_MIXED = 0, 1
+LIMITER_LP, LIMITER_DIFFUSION = 0, 1
+
+
+class FldError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (where, strerror(code), code))
+
+
+class fld_consts(C.Structure):
+    _fields_ = [("c", C.c_double), ("a_r", C.c_double), ("gamma", C.c_double), ("R_gas", C.c_double)]
+
+
+class fld_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3),
+                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3)]
+
+
+class fld_opacity(C.Structure):
+    _fields_ = [("kind", C.c_int), ("kappa0", C.c_double), ("a_rho", C.c_double), ("a_T", C.c_double)]
+
+
+class fld_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
+                ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
+                ("limiter", C.c_int), ("block", C.c_int), ("reserved", C.c_int * 4)]
+
+
+class fld_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("rel_resid", C.c_double), ("resid_hist", C.c_double * 64),
+                ("levels", C.c_int)]
+
+
+class fld_prof_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("level", C.c_int), ("launches", C.c_longlong),
+                ("cells", C.c_longlong), ("ms", C.c_double)]
+
+
+_lib = None
+P = C.c_void_p
+H = C.c_void_p
+
+
+def lib():
+    """Load libfld_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise ImportError("libfld_gb300.so not built: run paper_2503_02764_gb300/build.py")
+    L = C.CDLL(LIBPATH)
+    sig = {
+        "fld_default_opts": (None, [C.POINTER(fld_opts)]),
+        "fld_create": (C.c_int, [C.POINTER(H), C.POINTER(fld_grid), C.POINTER(fld_opts)]),
+        "fld_destroy": (C.c_int, [H]),
+        "fld_set_opts": (C.c_int, [H, C.POINTER(fld_opts)]),
+        "fld_num_levels": (C.c_int, [H]),
+        "fld_limiter": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), P, P, P, P, P,
+                                  P, P]),
+        "fld_diffuse": (C.c_int, [H, C.c_double, P, P, P, C.POINTER(fld_stats), P]),
+        "fld_exchange": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), C.c_double,
+                                   P, P, P, P]),
+        "fld_step": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), C.c_double, P, P,
+                               P, P, C.POINTER(fld_stats), P]),
+        "fld_get_status": (C.c_int, [H, P]),
+        "fld_strerror": (C.c_char_p, [C.c_int]),
+        "fld_prof_enable": (C.c_int, [H, C.c_int, C.c_int]),
+        "fld_prof_read": (C.c_int, [H, C.POINTER(fld_prof_entry), C.c_int]),
+        "fld_launch_count": (C.c_longlong, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(code):
+    return lib().fld_strerror(int(code)).decode()
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        return int(t)
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("fields must be contiguous float64 CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(rc, where):
+    if rc != FLD_OK:
+        raise FldError(rc, where)
+
+
+def make_grid(shape, h, bc):
+    """fld_grid from a numpy-order shape, (x, y, z) spacings and ((lo, hi), ...) kinds."""
+    g = fld_grid()
+    nd = len(shape)
+    g.ndim = nd
+    n = list(reversed(shape)) + [1] * (3 - nd)
+    for d in range(3):
+        g.n[d] = int(n[d])
+        g.h[d] = float(h[d]) if d < nd else 1.0
+        g.bc_lo[d] = int(bc[d][0]) if d < nd else 0
+        g.bc_hi[d] = int(bc[d][1]) if d < nd else 0
+    return g
+
+
+def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
+              limiter=LIMITER_LP, block=0):
+    o = fld_opts()
+    lib().fld_default_opts(C.byref(o))
+    o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
+    o.nu1, o.nu2, o.coarse_sweeps, o.limiter, o.block = nu1, nu2, coarse_sweeps, limiter, block
+    return o
+
+
+def make_consts(c, a_r, gamma, R_gas):
+    return fld_consts(c, a_r, gamma, R_gas)
+
+
+def make_opacity(op):
+    kind, k0, ar, at = op
+    return fld_opacity(int(kind), float(k0), float(ar), float(at))
+
+
+def stats_dict(st):
+    n = min(st.cycles, 63)
+    return {"cycles": st.cycles, "rel_resid": st.rel_resid, "levels": st.levels,
+            "resid_hist": [st.resid_hist[i] for i in range(n + 1)]}
+
+
+# ------------------------------------------------ C entry points, same names
+def fld_create(grid, opts):
+    h = H()
+    _check(lib().fld_create(C.byref(h), C.byref(grid), C.byref(opts)), "fld_create")
+    return h
+
+
+def fld_destroy(h):
+    _check(lib().fld_destroy(h), "fld_destroy")
+
+
+def fld_set_opts(h, opts):
+    _check(lib().fld_set_opts(h, C.byref(opts)), "fld_set_opts")
+
+
+def fld_num_levels(h):
+    return lib().fld_num_levels(h)
+
+
+def fld_limiter(h, consts, opacity, E, rho, T, E_bc, D, lam=None, stream=None):
+    _check(lib().fld_limiter(h, C.byref(consts), C.byref(opacity), _ptr(E), _ptr(rho), _ptr(T),
+                             _ptr(E_bc), _ptr(D), _ptr(lam), _stream(stream)), "fld_limiter")
+
+
+def fld_diffuse(h, dt, D, E_bc, E, stream=None, raise_on_error=True):
+    st = fld_stats()
+    rc = lib().fld_diffuse(h, float(dt), _ptr(D), _ptr(E_bc), _ptr(E), C.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(rc, "fld_diffuse")
+    return stats_dict(st) | {"status": rc}
+
+
+def fld_exchange(h, consts, opacity, dt, rho, T, E, stream=None):
+    _check(lib().fld_exchange(h, C.byref(consts), C.byref(opacity), float(dt), _ptr(rho), _ptr(T),
+                              _ptr(E), _stream(stream)), "fld_exchange")
+
+
+def fld_step(h, consts, opacity, dt, rho, T, E, E_bc, stream=None, raise_on_error=True):
+    st = fld_stats()
+    rc = lib().fld_step(h, C.byref(consts), C.byref(opacity), float(dt), _ptr(rho), _ptr(T),
+                        _ptr(E), _ptr(E_bc), C.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(rc, "fld_step")
+    return stats_dict(st) | {"status": rc}
+
+
+def fld_get_status(h, stream=None):
+    return lib().fld_get_status(h, _stream(stream))
+
+
+def fld_prof_enable(h, on=True, capacity=65536):
+    _check(lib().fld_prof_enable(h, int(on), int(capacity)), "fld_prof_enable")
+
+
+def fld_prof_read(h, cap=256):
+    buf = (fld_prof_entry * cap)()
+    n = lib().fld_prof_read(h, buf, cap)
+    return [{"name": e.name.decode(), "level": e.level, "launches": e.launches, "cells": e.cells,
+             "ms": e.ms} for e in buf[:n]]
+
+
+def fld_launch_count():
+    return lib().fld_launch_count()
+
+
+class Handle:
+    """Owns an fld_handle for one grid; the methods are the C entry points."""
+
+    def __init__(self, shape, h, bc, **opts):
+        self.grid = make_grid(shape, h, bc)
+        self.opts = make_opts(**opts)
+        self.h = fld_create(self.grid, self.opts)
+        self.shape = tuple(shape)
+
+    def set_opts(self, **opts):
+        self.opts = make_opts(**opts)
+        fld_set_opts(self.h, self.opts)
+
+    @property
+    def levels(self):
+        return fld_num_levels(self.h)
+
+    def close(self):
+        if self.h:
+            fld_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def limiter(self, consts, opacity, E, rho, T, E_bc, D, lam=None, stream=None):
+        fld_limiter(self.h, consts, opacity, E, rho, T, E_bc, D, lam, stream)
+
+    def diffuse(self, dt, D, E_bc, E, stream=None, raise_on_error=True):
+        return fld_diffuse(self.h, dt, D, E_bc, E, stream, raise_on_error)
+
+    def exchange(self, consts, opacity, dt, rho, T, E, stream=None):
+        fld_exchange(self.h, consts, opacity, dt, rho, T, E, stream)
+
+    def step(self, consts, opacity, dt, rho, T, E, E_bc, stream=None, raise_on_error=True):
+        return fld_step(self.h, consts, opacity, dt, rho, T, E, E_bc, stream, raise_on_error)
+
+    def status(self, stream=None):
+        return fld_get_status(self.h, stream)
+
+    def prof_enable(self, on=True, capacity=65536):
+        fld_prof_enable(self.h, on, capacity)
+
+    def prof_read(self, cap=256):
+        return fld_prof_read(self.h, cap)

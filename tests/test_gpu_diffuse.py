@@ -1,0 +1,92 @@
+"""GPU multigrid diffusion solve (fld_diffuse) against the oracle's direct solve."""
+import numpy as np
+import pytest
+
+from oracle import fld as O
+from paper_2503_02764_gb300 import inputs as I
+from gpu_util import torch_cuda, library, dev, host, maxrel
+
+pytestmark = pytest.mark.gpu
+
+# (shape, h, bc, dt, sigma)
+CASES = [
+    ((256,), (1 / 256,), ((0, 0),), 0.2, 1.0),
+    ((2,), (0.5,), ((1, 2),), 0.3, 0.5),
+    ((31,), (0.1,), ((2, 2),), 0.5, 1.0),
+    ((5, 3), (0.2, 0.3), ((0, 0), (1, 2)), 0.1, 1.0),
+    ((29, 37), (1.0, 1.0), ((0, 0), (0, 0)), 2.0, 1.5),
+    ((80, 96), (1.0, 1.0), ((0, 0), (0, 0)), 5.0, 1.0),
+    ((9, 11, 13), (0.1, 0.1, 0.1), ((1, 2), (0, 0), (2, 1)), 0.004, 1.0),
+    ((24, 20, 32), (1 / 32, 1 / 20, 1 / 24), ((0, 0), (0, 0), (2, 2)), 2e-4, 1.0),
+]
+
+
+def _problem(shape, bc, sigma, seed):
+    rng = np.random.default_rng(seed)
+    D = np.exp(sigma * rng.standard_normal(shape))
+    E = 1.0 + rng.uniform(0, 1, shape)
+    Eb = {}
+    nd = len(shape)
+    for d in range(nd):
+        for s in (0, 1):
+            if bc[d][s] == 2:
+                fs = tuple(n for a, n in enumerate(shape) if a != nd - 1 - d)
+                Eb[(d, s)] = 1.0 + rng.uniform(0, 1, fs)
+    return D, E, Eb
+
+
+def _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, tol=1e-14):
+    hd = fld.Handle(shape, h, bc, precision=precision, tol=tol, max_cycles=100)
+    Ed = dev(torch, E)
+    packed = I.pack_dirichlet(shape, bc, Eb)
+    st = hd.diffuse(dt, dev(torch, D), dev(torch, packed) if packed.size else None, Ed,
+                    raise_on_error=False)
+    assert st["status"] in (0, 3), st
+    assert st["rel_resid"] < 1e-13, st       # reached the FP64 residual floor
+    return host(Ed).reshape(shape), st
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
+@pytest.mark.parametrize("shape,h,bc,dt,sigma", CASES)
+def test_diffuse_matches_direct_solve(shape, h, bc, dt, sigma, precision, tol):
+    torch = torch_cuda()
+    fld = library()
+    D, E, Eb = _problem(shape, bc, sigma, 17 + len(shape) + shape[0])
+    x, st = _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision)
+    xo = O.diffuse(E, D, h, bc, Eb, dt, method="lu" if E.size <= 4096 else "splu")
+    assert maxrel(x, xo) < tol, (maxrel(x, xo), st)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_convergence_rate_and_determinism(precision):
+    torch = torch_cuda()
+    fld = library()
+    P = I.make_config(2, small=True)
+    D, _, _ = O.limiter(P.E, P.rho, P.T, P.h, P.bc, P.E_bc, P.c, P.opacity)
+    x1, st = _solve_gpu(fld, torch, P.shape, P.h, P.bc, P.dt, D, P.E, {}, precision, tol=1e-10)
+    x2, _ = _solve_gpu(fld, torch, P.shape, P.h, P.bc, P.dt, D, P.E, {}, precision, tol=1e-10)
+    assert np.array_equal(x1, x2)                 # bitwise reproducible (fixed reductions)
+    hist = st["resid_hist"]
+    rates = [hist[i + 1] / hist[i] for i in range(len(hist) - 1)]
+    assert max(rates) < 0.5, hist                 # each V-cycle removes most of the residual
+
+
+def test_not_converged_status_keeps_iterate():
+    torch = torch_cuda()
+    fld = library()
+    D, E, _ = _problem((64, 64), ((0, 0), (0, 0)), 1.0, 3)
+    hd = fld.Handle((64, 64), (1, 1), ((0, 0), (0, 0)), tol=1e-14, max_cycles=1)
+    Ed = dev(torch, E)
+    st = hd.diffuse(5.0, dev(torch, D), None, Ed, raise_on_error=False)
+    assert st["status"] == fld.FLD_ERR_NOT_CONVERGED and st["cycles"] == 1
+    assert st["rel_resid"] < st["resid_hist"][0]
+    assert np.all(np.isfinite(host(Ed)))
+
+
+def test_conservation_periodic():
+    torch = torch_cuda()
+    fld = library()
+    for precision in (0, 1):
+        D, E, _ = _problem((33, 47), ((0, 0), (0, 0)), 2.0, 8)
+        x, _ = _solve_gpu(fld, torch, (33, 47), (1, 1), ((0, 0), (0, 0)), 3.0, D, E, {}, precision)
+        assert abs(x.sum() - E.sum()) / E.sum() < 1e-13

@@ -1,0 +1,43 @@
+"""Whole FLD substep (fld_step) on the seeded workloads at reduced size, against the
+oracle's substep."""
+import numpy as np
+import pytest
+
+from oracle import fld as O
+from paper_2503_02764_gb300 import inputs as I
+from gpu_util import torch_cuda, library, dev, host, handle_for, consts_of, ebc_dev, maxrel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 5])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
+def test_step_matches_oracle(cfg, precision, tol):
+    torch = torch_cuda()
+    fld = library()
+    P = I.make_config(cfg, small=True)
+    hd = handle_for(fld, P, precision=precision, tol=1e-14, max_cycles=100)
+    Td, Ed, rd = dev(torch, P.T), dev(torch, P.E), dev(torch, P.rho)
+    ebc = ebc_dev(torch, P)
+    T, E = P.T.copy(), P.E.copy()
+    for _ in range(2):
+        st = hd.step(consts_of(fld, P), fld.make_opacity(P.opacity), P.dt, rd, Td, Ed, ebc,
+                     raise_on_error=False)
+        assert st["status"] in (0, 3) and st["rel_resid"] < 1e-13, st
+        T, E, _ = O.step(P.rho, T, E, P.h, P.bc, P.E_bc, P.dt, P.c, P.a_r, P.gamma, P.R_gas,
+                         P.opacity, P.limiter, method="lu" if P.ncells <= 4096 else "splu")
+    assert maxrel(host(Ed).reshape(P.shape), E) < tol
+    assert maxrel(host(Td).reshape(P.shape), T) < tol
+
+
+def test_total_energy_conserved_on_periodic_step():
+    torch = torch_cuda()
+    fld = library()
+    P = I.make_config(2, small=True)
+    hd = handle_for(fld, P, precision=1, tol=1e-12)
+    Td, Ed, rd = dev(torch, P.T), dev(torch, P.E), dev(torch, P.rho)
+    e0 = (O.internal_energy(P.rho, P.T, P.gamma, P.R_gas) + P.E).sum()
+    hd.step(consts_of(fld, P), fld.make_opacity(P.opacity), P.dt, rd, Td, Ed, None)
+    e1 = (O.internal_energy(P.rho, host(Td).reshape(P.shape), P.gamma, P.R_gas)
+          + host(Ed).reshape(P.shape)).sum()
+    assert abs(e1 - e0) / e0 < 1e-12
