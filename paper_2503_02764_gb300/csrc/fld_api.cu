@@ -17,7 +17,7 @@ using namespace fld;
 namespace {
 
 constexpr int MAX_LEVELS = 24;
-constexpr long long COARSE_TARGET = 64;   // stop coarsening at or below this many cells
+constexpr long long COARSE_TARGET = 8;    // stop coarsening at or below this many cells
 constexpr int NORM_BLOCKS = 152 * 8;      // fixed grid of the residual-norm kernels
 constexpr int NORM_THREADS = 256;
 

@@ -7,6 +7,8 @@
 // Coarse levels average K over the (up to 2^d) children and rescale it to the coarse
 // spacing; restriction averages residuals; prolongation is piecewise constant.
 // Every kernel here is templated on the storage/arithmetic type (double or float).
+#include <algorithm>
+
 #include "fld_internal.cuh"
 
 namespace fld {
@@ -18,11 +20,19 @@ static inline int grid_for(long long n, int block, int cap = 152 * 32) {
     return (int)nb;
 }
 
+// Row mapping: a block walks rows r = (j, k) (grid-stride over ny*nz rows) and its
+// threads walk i along the row, so no per-cell integer division is needed.
+static inline int rows_grid(const Lvl& L, int cap = 152 * 64) {
+    long long nr = (long long)L.n[1] * L.n[2];
+    return (int)std::min<long long>(std::max<long long>(nr, 1), cap);
+}
+
 __device__ __forceinline__ void decode(const Lvl& L, long long p, int& i, int& j, int& k) {
-    i = (int)(p % L.n[0]);
-    const long long q = p / L.n[0];
-    j = (int)(q % L.n[1]);
-    k = (int)(q / L.n[1]);
+    const int pp = (int)p;
+    i = pp % L.n[0];
+    const int q = pp / L.n[0];
+    j = q % L.n[1];
+    k = q / L.n[1];
 }
 
 // Off-diagonal sum and diagonal excess of the level operator at cell p:
@@ -156,24 +166,27 @@ void launch_restrict_K(const Lvl& F, const Lvl& C, double scale, const T* Kf, T*
 template <typename T>
 __global__ void k_smooth(Lvl L, int color, const T* __restrict__ xin, T* __restrict__ xout,
                          const T* __restrict__ b, const T* __restrict__ K) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
-         p += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        decode(L, p, i, j, k);
-        if (((i + j + k) & 1) != color) {
-            xout[p] = xin[p];
-            continue;
+    const int nrows = L.n[1] * L.n[2];
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int j = r % L.n[1], k = r / L.n[1];
+        const long long base = (long long)r * L.n[0];
+        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+            const long long p = base + i;
+            if (((i + j + k) & 1) != color) {
+                xout[p] = xin[p];
+                continue;
+            }
+            T sw, acc;
+            stencil<T>(L, K, xin, i, j, k, p, sw, acc);
+            xout[p] = (b[p] + acc) / (T(1) + sw);
         }
-        T sw, acc;
-        stencil<T>(L, K, xin, i, j, k, p, sw, acc);
-        xout[p] = (b[p] + acc) / (T(1) + sw);
     }
 }
 
 template <typename T>
 void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, const T* K,
                    int block, cudaStream_t s) {
-    k_smooth<T><<<grid_for(L.ncell, block), block, 0, s>>>(L, color, xin, xout, b, K);
+    k_smooth<T><<<rows_grid(L), block, 0, s>>>(L, color, xin, xout, b, K);
 }
 
 // Coarse right-hand side = average of the fine residuals b - A x over the children.
@@ -214,22 +227,70 @@ void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, c
     k_resid_restrict<T><<<grid_for(C.ncell, block), block, 0, s>>>(F, C, x, b, K, bc);
 }
 
-// x_fine += x_coarse[parent], parent index = i/2 along coarsened axes.
+// Cell-centred linear prolongation: along a coarsened axis a fine cell takes 3/4 of
+// its parent I = i/2 and 1/4 of the coarse neighbour on its side (I-1 for an even i,
+// I+1 for an odd one); tensor product over the axes. A missing neighbour at a wall is
+// the mirror value: +e_I (Neumann, zero flux) or -e_I (Dirichlet, zero correction).
+struct Interp {
+    int idx[2];
+    float wt[2];
+};
+
+__device__ __forceinline__ Interp interp1(int i, int nf, int nc, int lo_bc, int hi_bc) {
+    Interp r;
+    if (nc == nf) {           // axis not coarsened
+        r.idx[0] = r.idx[1] = i;
+        r.wt[0] = 1.f;
+        r.wt[1] = 0.f;
+        return r;
+    }
+    const int I = i >> 1;
+    int J = (i & 1) ? I + 1 : I - 1;
+    float sgn = 1.f;
+    if (J < 0 || J >= nc) {
+        const int kind = (J < 0) ? lo_bc : hi_bc;
+        if (kind == FLD_BC_PERIODIC) J = (J + nc) % nc;
+        else {
+            sgn = (kind == FLD_BC_DIRICHLET) ? -1.f : 1.f;
+            J = I;
+        }
+    }
+    r.idx[0] = I;
+    r.idx[1] = J;
+    r.wt[0] = 0.75f;
+    r.wt[1] = 0.25f * sgn;
+    return r;
+}
+
 template <typename T>
 __global__ void k_prolong(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict__ xc) {
-    const int sx = C.n[0] < F.n[0], sy = C.n[1] < F.n[1], sz = C.n[2] < F.n[2];
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < F.ncell;
-         p += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        decode(F, p, i, j, k);
-        const long long P = ((long long)(k >> sz) * C.n[1] + (j >> sy)) * C.n[0] + (i >> sx);
-        xf[p] += xc[P];
+    const int nrows = F.n[1] * F.n[2];
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int j = r % F.n[1], k = r / F.n[1];
+        const long long base = (long long)r * F.n[0];
+        const Interp iy = interp1(j, F.n[1], C.n[1], F.bclo[1], F.bchi[1]);
+        const Interp iz = interp1(k, F.n[2], C.n[2], F.bclo[2], F.bchi[2]);
+        for (int i = threadIdx.x; i < F.n[0]; i += blockDim.x) {
+            const Interp ix = interp1(i, F.n[0], C.n[0], F.bclo[0], F.bchi[0]);
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const T wzy = (T)(iz.wt[c] * iy.wt[b]);
+                    if (wzy == T(0)) continue;
+                    const long long rowc = ((long long)iz.idx[c] * C.n[1] + iy.idx[b]) * C.n[0];
+                    acc += wzy * ((T)ix.wt[0] * xc[rowc + ix.idx[0]] +
+                                  (T)ix.wt[1] * xc[rowc + ix.idx[1]]);
+                }
+            xf[base + i] += acc;
+        }
     }
 }
 
 template <typename T>
 void launch_prolong(const Lvl& F, const Lvl& C, T* xf, const T* xc, int block, cudaStream_t s) {
-    k_prolong<T><<<grid_for(F.ncell, block), block, 0, s>>>(F, C, xf, xc);
+    k_prolong<T><<<rows_grid(F), block, 0, s>>>(F, C, xf, xc);
 }
 
 // Coarsest level: `sweeps` red-black sweeps from x = 0 by one block, in FP64 whatever
@@ -294,15 +355,18 @@ __global__ void k_resid64(Lvl L, const double* __restrict__ x, const double* __r
                           double* __restrict__ partials) {
     __shared__ double sh[32];
     double acc2 = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
-         p += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        decode(L, p, i, j, k);
-        double sw, acc;
-        stencil<double>(L, K, x, i, j, k, p, sw, acc);
-        const double r = b[p] - (1.0 + sw) * x[p] + acc;
-        if (r32) r32[p] = (float)r;
-        acc2 = fma(r, r, acc2);
+    const int nrows = L.n[1] * L.n[2];
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int j = r % L.n[1], k = r / L.n[1];
+        const long long base = (long long)r * L.n[0];
+        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+            const long long p = base + i;
+            double sw, acc;
+            stencil<double>(L, K, x, i, j, k, p, sw, acc);
+            const double r = b[p] - (1.0 + sw) * x[p] + acc;
+            if (r32) r32[p] = (float)r;
+            acc2 = fma(r, r, acc2);
+        }
     }
     acc2 = block_sum(acc2, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc2;

@@ -1,5 +1,7 @@
 // Pointwise kernels of the FLD substep: the gas-radiation exchange quartic and the
 // flux limiter (Levermore-Pomraning, 4th-order 5-point gradient).
+#include <algorithm>
+
 #include "fld_internal.cuh"
 
 namespace fld {
@@ -10,8 +12,73 @@ namespace fld {
 //   f(T) = alpha T + beta T^4 - q = 0,  alpha = rho c_v, beta = a_r chi/(1+chi),
 //   q = e + chi E/(1+chi),  chi = dt c kappa rho,
 // increasing and convex for T > 0 with f(0) < 0: one positive root, bounded above by
-// min(q/alpha, (q/beta)^(1/4)). Newton from that bound decreases monotonically to the
-// root, so a fixed iteration cap with a relative-step stop is safe.
+// min(q/alpha, (q/beta)^(1/4)), from where Newton decreases monotonically to it.
+//
+// FP64 arithmetic is the scarce resource on this GPU, so the root is found in two
+// stages: Newton in FP32 on a scaled form of the quartic (all quantities O(1)), then
+// one FP64 Newton step, whose residual f(T) is evaluated in FP64 and whose derivative
+// only needs FP32 accuracy (the step is ~1e-7 T, so a 1e-7 relative error in it leaves
+// ~1e-14 T). Cells whose coefficients fall outside the FP32 range take a plain FP64
+// Newton iteration instead.
+
+// 1/a for 1 <= a < 1e30 by Newton-Raphson on y -> y + y (1 - a y), seeded with the
+// FP32 reciprocal; each step squares the relative error (2^-23 -> 2^-46 -> rounding).
+__device__ __forceinline__ double rcp_nr(double a) {
+    double y = (double)__frcp_rn((float)a);
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    return fma(y, e, y);
+}
+
+__device__ __forceinline__ bool f32_ok(double v) { return v > 1e-30 && v < 1e30; }
+
+__device__ double exchange_root(double alpha, double beta, double q) {
+    const float af = (float)alpha, bf = (float)beta, qf = (float)q;
+    const float T1 = qf / af;                       // root if beta were 0
+    const float T1sq = T1 * T1;
+    const float g = (bf * T1sq) * (T1sq / qf);      // beta T1^4 / q
+    const bool fast = f32_ok(alpha) && f32_ok(q) && (beta == 0.0 || f32_ok(beta)) &&
+                      T1 > 1e-9f && T1 < 1e9f && g < 1e30f;
+    if (fast) {
+        float x = 1.f, scale = T1;
+        if (g <= 1.f) {
+            // phi(x) = g x^4 + x - 1, root in (0.72, 1]
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const float x2 = x * x;
+                x -= (fmaf(g * x2, x2, x) - 1.f) / fmaf(4.f * g * x2, x, 1.f);
+            }
+        } else {
+            // psi(y) = y^4 + h y - 1 with h = g^(-1/4), T = y T1 h, root in (0.8, 1]
+            const float hh = rsqrtf(sqrtf(g));
+            scale = T1 * hh;
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const float x2 = x * x;
+                x -= (fmaf(x2, x2, hh * x) - 1.f) / fmaf(4.f * x2, x, hh);
+            }
+        }
+        const double T = (double)x * (double)scale;
+        // one FP64 Newton step: FP64 residual, FP32 derivative
+        const double T2 = T * T;
+        const double f = fma(beta * T2, T2, fma(alpha, T, -q));
+        const float fpf = fmaf(4.f * bf * (float)T2, (float)T, af);
+        return fma(-f, (double)__frcp_rn(fpf), T);
+    }
+    // outside the FP32 range: plain FP64 Newton from the upper bound
+    double x = q / alpha;
+    if (beta > 0.0) x = fmin(x, sqrt(sqrt(q / beta)));
+    for (int it = 0; it < 60; ++it) {
+        const double x2 = x * x;
+        const double f = fma(beta * x2, x2, fma(alpha, x, -q));
+        const double dx = f / fma(4.0 * beta * x2, x, alpha);
+        x -= dx;
+        if (fabs(dx) <= 4e-16 * x) break;
+    }
+    return x;
+}
+
 __global__ void k_exchange(long long n, const double* __restrict__ rho, double* __restrict__ T,
                            double* __restrict__ E, Opacity op, double dtc, double a_r, double cv,
                            unsigned* err) {
@@ -29,23 +96,15 @@ __global__ void k_exchange(long long n, const double* __restrict__ rho, double* 
         }
         const double chi = dtc * kap * r;
         const double alpha = r * cv;
-        const double e = alpha * t;
-        const double w = chi / (1.0 + chi);
+        const double d1 = 1.0 + chi;
+        const double inv1 = (d1 < 1e30) ? rcp_nr(d1) : 1.0 / d1;
+        const double w = chi * inv1;
         const double beta = w * a_r;
-        const double q = fma(w, er, e);
-        double x = q / alpha;
-        if (beta > 0.0) x = fmin(x, sqrt(sqrt(q / beta)));
-        for (int it = 0; it < 100; ++it) {
-            const double x2 = x * x;
-            const double f = fma(beta * x2, x2, fma(alpha, x, -q));
-            const double fp = fma(4.0 * beta * x2, x, alpha);
-            const double dx = f / fp;
-            x -= dx;
-            if (fabs(dx) <= 1e-16 * x) break;
-        }
+        const double q = fma(w, er, alpha * t);
+        const double x = exchange_root(alpha, beta, q);
         const double x2 = x * x;
         T[i] = x;
-        E[i] = fma(chi * a_r, x2 * x2, er) / (1.0 + chi);
+        E[i] = fma(chi * a_r, x2 * x2, er) * inv1;
     }
 }
 
@@ -110,12 +169,11 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           int mode, double* __restrict__ D, double* __restrict__ lam,
                           unsigned* err) {
     const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(p % L.n[0]);
-        const long long q = p / L.n[0];
-        const int j = (int)(q % L.n[1]);
-        const int k = (int)(q / L.n[1]);
+    const int nrows = L.n[1] * L.n[2];
+    for (int rw = blockIdx.x; rw < nrows; rw += gridDim.x)
+    for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+        const int j = rw % L.n[1], k = rw / L.n[1];
+        const long long p = (long long)rw * L.n[0] + i;
         const double Ec = E[p], r = rho[p];
         const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
         const double kap = opacity_eval(op, r, t);
@@ -150,9 +208,8 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
                               L.ndim > 2 ? 1.0 / (12.0 * h[2]) : 0.0);
     const int block = 256;
-    long long nb = (L.ncell + block - 1) / block;
-    if (nb > 152 * 32) nb = 152 * 32;
-    k_limiter<<<(int)nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, D, lam, err);
+    const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
+    k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, D, lam, err);
 }
 
 }  // namespace fld

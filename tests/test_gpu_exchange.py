@@ -63,7 +63,8 @@ def test_exchange_fixed_point_table1():
         E = Disp.A_RAD * T ** 4
         Tg, Eg = _run(fld, torch, rho, T, E, 10.0, (Disp.C_LIGHT, Disp.A_RAD, s["gamma"], R_gas),
                       (0, 0.4, 0, 0))
-        assert np.max(np.abs(Tg / T - 1)) < 4e-16 * 4 and np.max(np.abs(Eg / E - 1)) < 1e-15
+        # one FP64 Newton step from an FP32 seed leaves ~1e-15 relative in T (4x in T^4)
+        assert np.max(np.abs(Tg / T - 1)) < 1e-14 and np.max(np.abs(Eg / E - 1)) < 4e-14
 
 
 def test_exchange_domain_error_leaves_cell():
