@@ -91,8 +91,10 @@ typedef struct {
     int nu1, nu2;       /* red-black Gauss-Seidel sweeps before / after coarse corr. */
     int coarse_sweeps;  /* red-black sweeps of the coarsest-level solve             */
     int limiter;        /* FLD_LIMITER_LP or FLD_LIMITER_DIFFUSION                  */
-    int block;          /* threads per block of the stencil kernels (0 = default)   */
-    int reserved[4];
+    int block;          /* threads per block of the row-mapped kernels (0 = default) */
+    int smoother;       /* 0: fused single-pass red-black sweep kernel where the level
+                           allows it (2D/3D, nx >= 8); 1: two half-sweep launches     */
+    int reserved[3];
 } fld_opts;
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative

@@ -110,7 +110,8 @@ bool opts_ok(const fld_opts* o) {
            o->max_cycles >= 1 && o->nu1 >= 0 && o->nu2 >= 0 && (o->nu1 + o->nu2) >= 1 &&
            o->coarse_sweeps >= 1 &&
            (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION) &&
-           (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0));
+           (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0)) &&
+           (o->smoother == 0 || o->smoother == 1);
 }
 
 Opacity to_op(const fld_opacity* op) {
@@ -217,6 +218,30 @@ void prof_free(fld_handle* h) {
     h->prof.on = false;
 }
 
+// -------------------------------------------------- smoothing: `n` red-black sweeps,
+// the iterate in B.x before and after. Pairs of sweeps use the fused single-pass
+// kernel (x -> tmp -> x); an odd last sweep (or a level the fused kernel does not
+// cover) uses two half-sweep launches (x -> tmp -> x).
+template <typename T>
+void smooth(fld_handle* h, LevelBufs<T>& B, int l, int n, cudaStream_t s) {
+    const Lvl& L = h->lv[l];
+    const bool f32 = sizeof(T) == 4;
+    const int bs = blk(h);
+    int left = n;
+    if (h->o.smoother == 0 && rb_sweep_supported<T>(L)) {
+        const char* nm = f32 ? "rbsweep32" : "rbsweep64";
+        for (; left >= 2; left -= 2) {
+            run(h, nm, l, L.ncell, s, [&] { launch_rb_sweep<T>(L, B.x, B.tmp, B.b, B.K, s); });
+            run(h, nm, l, L.ncell, s, [&] { launch_rb_sweep<T>(L, B.tmp, B.x, B.b, B.K, s); });
+        }
+    }
+    const char* sm = f32 ? "smooth32" : "smooth64";
+    for (; left > 0; --left) {
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, B.x, B.tmp, B.b, B.K, bs, s); });
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, B.tmp, B.x, B.b, B.K, bs, s); });
+    }
+}
+
 // -------------------------------------------------- V-cycle on level l (x_l in/out)
 template <typename T>
 void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
@@ -229,11 +254,7 @@ void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
         return;
     }
     const int bs = blk(h);
-    const char* sm = f32 ? "smooth32" : "smooth64";
-    for (int it = 0; it < h->o.nu1; ++it) {
-        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, B.x, B.tmp, B.b, B.K, bs, s); });
-        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, B.tmp, B.x, B.b, B.K, bs, s); });
-    }
+    smooth<T>(h, B, l, h->o.nu1, s);
     const Lvl& C = h->lv[l + 1];
     run(h, f32 ? "resid_restrict32" : "resid_restrict64", l, L.ncell, s,
         [&] { launch_resid_restrict<T>(L, C, B.x, B.b, B.K, P[l + 1].b, bs, s); });
@@ -241,10 +262,7 @@ void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
     vcycle<T>(h, P, l + 1, s);
     run(h, f32 ? "prolong32" : "prolong64", l, L.ncell, s,
         [&] { launch_prolong<T>(L, C, B.x, P[l + 1].x, bs, s); });
-    for (int it = 0; it < h->o.nu2; ++it) {
-        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, B.x, B.tmp, B.b, B.K, bs, s); });
-        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, B.tmp, B.x, B.b, B.K, bs, s); });
-    }
+    smooth<T>(h, B, l, h->o.nu2, s);
 }
 
 template <typename T>

@@ -58,6 +58,11 @@ void launch_restrict_K(const Lvl& F, const Lvl& C, double scale, const T* Kf, T*
 template <typename T>
 void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, const T* K,
                    int block, cudaStream_t s);
+// fused red+black sweep, xin -> xout (2D/3D levels with nx >= 8)
+template <typename T>
+bool rb_sweep_supported(const Lvl& L);
+template <typename T>
+void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K, cudaStream_t s);
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K,
                            T* bc, int block, cudaStream_t s);

@@ -40,7 +40,8 @@ class fld_opacity(C.Structure):
 class fld_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
-                ("limiter", C.c_int), ("block", C.c_int), ("reserved", C.c_int * 4)]
+                ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
+                ("reserved", C.c_int * 3)]
 
 
 class fld_stats(C.Structure):
@@ -136,11 +137,12 @@ def make_grid(shape, h, bc):
 
 
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
-              limiter=LIMITER_LP, block=0):
+              limiter=LIMITER_LP, block=0, smoother=0):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
     o.nu1, o.nu2, o.coarse_sweeps, o.limiter, o.block = nu1, nu2, coarse_sweeps, limiter, block
+    o.smoother = smoother
     return o
 
 

@@ -18,6 +18,9 @@ CASES = [
     ((80, 96), (1.0, 1.0), ((0, 0), (0, 0)), 5.0, 1.0),
     ((9, 11, 13), (0.1, 0.1, 0.1), ((1, 2), (0, 0), (2, 1)), 0.004, 1.0),
     ((24, 20, 32), (1 / 32, 1 / 20, 1 / 24), ((0, 0), (0, 0), (2, 2)), 2e-4, 1.0),
+    ((11, 13, 17), (1.0, 1.0, 1.0), ((0, 0), (0, 0), (0, 0)), 1.5, 1.0),
+    ((2, 40), (0.5, 0.5), ((1, 2), (0, 0)), 0.2, 1.0),
+    ((70, 9, 131), (1.0, 1.0, 1.0), ((1, 1), (0, 0), (2, 0)), 0.8, 0.7),
 ]
 
 
@@ -38,8 +41,8 @@ def _problem(shape, bc, sigma, seed, ell=4.0):
     return D, E, Eb
 
 
-def _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, tol=1e-14):
-    hd = fld.Handle(shape, h, bc, precision=precision, tol=tol, max_cycles=100)
+def _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, tol=1e-14, smoother=0):
+    hd = fld.Handle(shape, h, bc, precision=precision, tol=tol, max_cycles=100, smoother=smoother)
     Ed = dev(torch, E)
     packed = I.pack_dirichlet(shape, bc, Eb)
     st = hd.diffuse(dt, dev(torch, D), dev(torch, packed) if packed.size else None, Ed,
@@ -49,13 +52,15 @@ def _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, tol=1e-14):
     return host(Ed).reshape(shape), st
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
 @pytest.mark.parametrize("shape,h,bc,dt,sigma", CASES)
-def test_diffuse_matches_direct_solve(shape, h, bc, dt, sigma, precision, tol):
+def test_diffuse_matches_direct_solve(shape, h, bc, dt, sigma, precision, tol, smoother):
+    # smoother 0: fused single-pass red-black kernel; 1: two half-sweep launches
     torch = torch_cuda()
     fld = library()
     D, E, Eb = _problem(shape, bc, sigma, 17 + len(shape) + shape[0])
-    x, st = _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision)
+    x, st = _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, smoother=smoother)
     xo = O.diffuse(E, D, h, bc, Eb, dt, method="lu" if E.size <= 4096 else "splu")
     assert maxrel(x, xo) < tol, (maxrel(x, xo), st)
 
