@@ -172,6 +172,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--smoother", type=int, default=0, help="0 in-place half sweeps, 1 out-of-place half sweeps, 2 fused single-pass sweep")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the mixed-vs-FP64 solve timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -196,7 +198,8 @@ def main():
 
     P = I.stratified_3d(args.n)
     prec = fld.PREC_MIXED if args.precision == "mixed" else fld.PREC_FP64
-    hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50)
+    hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50,
+                    smoother=args.smoother)
     consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
     op = fld.make_opacity(P.opacity)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -289,11 +292,11 @@ def main():
 
     # ---------------- mixed vs FP64 time to 1e-10 on the same GPU (diffusion solve alone)
     ttt = {}
-    if rank == 0:
+    if rank == 0 and not args.no_ttt:
         D = torch.empty_like(E)
         hd.limiter(consts, op, E, rho, T, ebc, D)
         for name, pr in (("mixed", fld.PREC_MIXED), ("fp64", fld.PREC_FP64)):
-            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50)
+            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, smoother=args.smoother)
             times, cyc = [], 0
             for rep in range(4):
                 X = E.clone()

@@ -92,8 +92,10 @@ typedef struct {
     int coarse_sweeps;  /* red-black sweeps of the coarsest-level solve             */
     int limiter;        /* FLD_LIMITER_LP or FLD_LIMITER_DIFFUSION                  */
     int block;          /* threads per block of the row-mapped kernels (0 = default) */
-    int smoother;       /* 0: fused single-pass red-black sweep kernel where the level
-                           allows it (2D/3D, nx >= 8); 1: two half-sweep launches     */
+    int smoother;       /* 0: in-place red and black half sweeps (levels with no odd
+                           periodic extent; others as 1); 1: two out-of-place half
+                           sweeps; 2: the fused single-pass shared-memory sweep
+                           (2D/3D, nx >= 8; others as 1)                               */
     int reserved[3];
 } fld_opts;
 

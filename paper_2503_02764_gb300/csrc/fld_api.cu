@@ -111,7 +111,7 @@ bool opts_ok(const fld_opts* o) {
            o->coarse_sweeps >= 1 &&
            (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION) &&
            (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0)) &&
-           (o->smoother == 0 || o->smoother == 1);
+           (o->smoother >= 0 && o->smoother <= 2);
 }
 
 Opacity to_op(const fld_opacity* op) {
@@ -155,7 +155,10 @@ void build_levels(fld_handle* h) {
     int nl = 0;
     for (;;) {
         L.ncell = (long long)L.n[0] * L.n[1] * L.n[2];
-        for (int d = 0; d < 3; ++d) L.w[d] = d < g.ndim ? (H[0] / H[d]) * (H[0] / H[d]) : 0.0;
+        for (int d = 0; d < 3; ++d) {
+            L.w[d] = d < g.ndim ? (H[0] / H[d]) * (H[0] / H[d]) : 0.0;
+            L.wf[d] = (float)L.w[d];
+        }
         h->lv[nl++] = L;
         bool can = false;
         for (int d = 0; d < g.ndim; ++d) can |= L.n[d] >= 4;
@@ -228,7 +231,14 @@ void smooth(fld_handle* h, LevelBufs<T>& B, int l, int n, cudaStream_t s) {
     const bool f32 = sizeof(T) == 4;
     const int bs = blk(h);
     int left = n;
-    if (h->o.smoother == 0 && rb_sweep_supported<T>(L)) {
+    if (h->o.smoother == 0 && rb_half_supported<T>(L)) {
+        const char* nm = f32 ? "rbhalf32" : "rbhalf64";
+        for (; left > 0; --left) {
+            run(h, nm, l, L.ncell, s, [&] { launch_rb_half<T>(L, 0, B.x, B.b, B.K, s); });
+            run(h, nm, l, L.ncell, s, [&] { launch_rb_half<T>(L, 1, B.x, B.b, B.K, s); });
+        }
+    }
+    if (h->o.smoother == 2 && rb_sweep_supported<T>(L)) {
         const char* nm = f32 ? "rbsweep32" : "rbsweep64";
         for (; left >= 2; left -= 2) {
             run(h, nm, l, L.ncell, s, [&] { launch_rb_sweep<T>(L, B.x, B.tmp, B.b, B.K, s); });

@@ -19,8 +19,17 @@ struct Lvl {
     int bclo[3];
     int bchi[3];
     double w[3];    // axis weights (H_x / H_d)^2
+    float wf[3];    // the same in FP32 (FP32 kernels never touch FP64 values)
     long long ncell;
 };
+
+// Axis weight in the kernel's arithmetic type.
+template <typename T>
+__host__ __device__ __forceinline__ T wgt(const Lvl& L, int d);
+template <>
+__host__ __device__ __forceinline__ double wgt<double>(const Lvl& L, int d) { return L.w[d]; }
+template <>
+__host__ __device__ __forceinline__ float wgt<float>(const Lvl& L, int d) { return L.wf[d]; }
 
 // Opacity law evaluated in FP64: kappa0 (kind 0) or kappa0 rho^a T^b (kind 1).
 struct Opacity {
@@ -58,6 +67,11 @@ void launch_restrict_K(const Lvl& F, const Lvl& C, double scale, const T* Kf, T*
 template <typename T>
 void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, const T* K,
                    int block, cudaStream_t s);
+// in-place half sweep of one colour (no odd periodic extent)
+template <typename T>
+bool rb_half_supported(const Lvl& L);
+template <typename T>
+void launch_rb_half(const Lvl& L, int color, T* x, const T* b, const T* K, cudaStream_t s);
 // fused red+black sweep, xin -> xout (2D/3D levels with nx >= 8)
 template <typename T>
 bool rb_sweep_supported(const Lvl& L);

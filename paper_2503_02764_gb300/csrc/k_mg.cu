@@ -40,39 +40,44 @@ __device__ __forceinline__ void decode(const Lvl& L, long long p, int& i, int& j
 // so (A x)_p = (1 + sw) x_p - acc.
 template <typename T>
 __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
-                                        const T* __restrict__ x, int i, int j, int k, long long p,
+                                        const T* __restrict__ x, int i, int j, int k, long long p64,
                                         T& sw, T& acc) {
+    // cell indices fit in 32 bits (the handle rejects grids of 2^31 cells or more)
+    const int p = (int)p64;
     const T Kc = K[p];
     const int c[3] = {i, j, k};
-    long long stride = 1;
+    int stride = 1;
     sw = T(0);
     acc = T(0);
-    for (int d = 0; d < L.ndim; ++d) {
-        const int n = L.n[d];
-        const T wd = (T)L.w[d];
-        // low face
-        long long q = -1;
-        if (c[d] > 0) q = p - stride;
-        else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (long long)(n - 1) * stride;
-        if (q >= 0) {
-            const T w = T(0.5) * (Kc + K[q]) * wd;
-            sw += w;
-            acc += w * x[q];
-        } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
-            sw += T(2) * Kc * wd;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d < L.ndim) {
+            const int n = L.n[d];
+            const T wd = wgt<T>(L, d);
+            // low face
+            int q = -1;
+            if (c[d] > 0) q = p - stride;
+            else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
+            if (q >= 0) {
+                const T w = T(0.5) * (Kc + K[q]) * wd;
+                sw += w;
+                acc += w * x[q];
+            } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
+                sw += T(2) * Kc * wd;
+            }
+            // high face
+            q = -1;
+            if (c[d] < n - 1) q = p + stride;
+            else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
+            if (q >= 0) {
+                const T w = T(0.5) * (Kc + K[q]) * wd;
+                sw += w;
+                acc += w * x[q];
+            } else if (L.bchi[d] == FLD_BC_DIRICHLET) {
+                sw += T(2) * Kc * wd;
+            }
+            stride *= n;
         }
-        // high face
-        q = -1;
-        if (c[d] < n - 1) q = p + stride;
-        else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (long long)(n - 1) * stride;
-        if (q >= 0) {
-            const T w = T(0.5) * (Kc + K[q]) * wd;
-            sw += w;
-            acc += w * x[q];
-        } else if (L.bchi[d] == FLD_BC_DIRICHLET) {
-            sw += T(2) * Kc * wd;
-        }
-        stride *= n;
     }
 }
 
@@ -187,6 +192,70 @@ template <typename T>
 void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, const T* K,
                    int block, cudaStream_t s) {
     k_smooth<T><<<rows_grid(L), block, 0, s>>>(L, color, xin, xout, b, K);
+}
+
+// In-place red-black half sweep: only cells of `color` are updated, from neighbours
+// of the other colour. One thread per pair of cells along x (the one of `color`),
+// a row (j, k) per block row, so the index arithmetic is a few integer operations.
+// Valid when no periodic axis has an odd extent (otherwise two same-colour cells
+// meet across the wrap and would race); the caller checks.
+template <typename T>
+__device__ __forceinline__ T div_fast(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float div_fast<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename T>
+__global__ void k_rb_half(Lvl L, int color, T* __restrict__ x, const T* __restrict__ b,
+                          const T* __restrict__ K) {
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+    if (i >= nx) return;
+    const int sy = nx, sz = nx * ny;
+    const int p = (k * ny + j) * nx + i;
+    const T kc = K[p];
+    T sw = T(0), acc = T(0);
+    const T wx = wgt<T>(L, 0);
+    int q = i > 0 ? p - 1 : (L.bclo[0] == FLD_BC_PERIODIC ? p + nx - 1 : -1);
+    if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wx; sw += w; acc += w * x[q]; }
+    else if (L.bclo[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
+    q = i < nx - 1 ? p + 1 : (L.bchi[0] == FLD_BC_PERIODIC ? p - nx + 1 : -1);
+    if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wx; sw += w; acc += w * x[q]; }
+    else if (L.bchi[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
+    if (L.ndim >= 2) {
+        const T wy = wgt<T>(L, 1);
+        q = j > 0 ? p - sy : (L.bclo[1] == FLD_BC_PERIODIC ? p + (ny - 1) * sy : -1);
+        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wy; sw += w; acc += w * x[q]; }
+        else if (L.bclo[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
+        q = j < ny - 1 ? p + sy : (L.bchi[1] == FLD_BC_PERIODIC ? p - (ny - 1) * sy : -1);
+        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wy; sw += w; acc += w * x[q]; }
+        else if (L.bchi[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
+    }
+    if (L.ndim >= 3) {
+        const T wz = wgt<T>(L, 2);
+        q = k > 0 ? p - sz : (L.bclo[2] == FLD_BC_PERIODIC ? p + (nz - 1) * sz : -1);
+        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wz; sw += w; acc += w * x[q]; }
+        else if (L.bclo[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
+        q = k < nz - 1 ? p + sz : (L.bchi[2] == FLD_BC_PERIODIC ? p - (nz - 1) * sz : -1);
+        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wz; sw += w; acc += w * x[q]; }
+        else if (L.bchi[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
+    }
+    x[p] = div_fast<T>(b[p] + acc, T(1) + sw);
+}
+
+template <typename T>
+bool rb_half_supported(const Lvl& L) {
+    for (int d = 0; d < L.ndim; ++d)
+        if (L.bclo[d] == FLD_BC_PERIODIC && (L.n[d] & 1)) return false;
+    return L.n[1] <= 65535 && L.n[2] <= 65535;
+}
+
+template <typename T>
+void launch_rb_half(const Lvl& L, int color, T* x, const T* b, const T* K, cudaStream_t s) {
+    const int pairs = (L.n[0] + 1) / 2;
+    const int bs = pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32;
+    dim3 grid((pairs + bs - 1) / bs, L.n[1], L.n[2]);
+    k_rb_half<T><<<grid, bs, 0, s>>>(L, color, x, b, K);
 }
 
 // Coarse right-hand side = average of the fine residuals b - A x over the children.
@@ -350,22 +419,60 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return v;
 }
 
+// FP64 residual with the fewest FP64 operations per cell (FP64 issues at 1/58 of the
+// FP32 rate here): per face one sum of coefficients, one difference and one FMA,
+//   r = b - x - sum_d (w_d/2) sum_faces (K_p + K_q)(x_p - x_q) - sum_Dirichlet 2 w_d K_p x_p.
 __global__ void k_resid64(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
                           const double* __restrict__ K, float* __restrict__ r32,
                           double* __restrict__ partials) {
     __shared__ double sh[32];
     double acc2 = 0.0;
-    const int nrows = L.n[1] * L.n[2];
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int nrows = ny * nz;
+    const int sy = nx, sz = nx * ny;
+    const double hx = 0.5 * L.w[0], hy = 0.5 * L.w[1], hz = 0.5 * L.w[2];
     for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
-        const int j = r % L.n[1], k = r / L.n[1];
-        const long long base = (long long)r * L.n[0];
-        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
-            const long long p = base + i;
-            double sw, acc;
-            stencil<double>(L, K, x, i, j, k, p, sw, acc);
-            const double r = b[p] - (1.0 + sw) * x[p] + acc;
-            if (r32) r32[p] = (float)r;
-            acc2 = fma(r, r, acc2);
+        const int j = r % ny, k = r / ny;
+        const int base = r * nx;
+        // neighbour row offsets (periodic wrap, or -1 for a wall)
+        int oym = -1, oyp = -1, ozm = -1, ozp = -1;
+        if (L.ndim >= 2) {
+            oym = j > 0 ? -sy : (L.bclo[1] == FLD_BC_PERIODIC ? (ny - 1) * sy : -1);
+            oyp = j < ny - 1 ? sy : (L.bchi[1] == FLD_BC_PERIODIC ? -(ny - 1) * sy : -1);
+        }
+        if (L.ndim >= 3) {
+            ozm = k > 0 ? -sz : (L.bclo[2] == FLD_BC_PERIODIC ? (nz - 1) * sz : -1);
+            ozp = k < nz - 1 ? sz : (L.bchi[2] == FLD_BC_PERIODIC ? -(nz - 1) * sz : -1);
+        }
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int p = base + i;
+            const double xc = x[p], kc = K[p];
+            double ax = 0.0, ay = 0.0, az = 0.0, dir = 0.0;
+            // x faces
+            int q = i > 0 ? p - 1 : (L.bclo[0] == FLD_BC_PERIODIC ? p + nx - 1 : -1);
+            if (q >= 0) ax = fma(kc + K[q], xc - x[q], ax);
+            else if (L.bclo[0] == FLD_BC_DIRICHLET) dir += L.w[0];
+            q = i < nx - 1 ? p + 1 : (L.bchi[0] == FLD_BC_PERIODIC ? p - nx + 1 : -1);
+            if (q >= 0) ax = fma(kc + K[q], xc - x[q], ax);
+            else if (L.bchi[0] == FLD_BC_DIRICHLET) dir += L.w[0];
+            if (L.ndim >= 2) {
+                if (oym != -1) ay = fma(kc + K[p + oym], xc - x[p + oym], ay);
+                else if (L.bclo[1] == FLD_BC_DIRICHLET) dir += L.w[1];
+                if (oyp != -1) ay = fma(kc + K[p + oyp], xc - x[p + oyp], ay);
+                else if (L.bchi[1] == FLD_BC_DIRICHLET) dir += L.w[1];
+            }
+            if (L.ndim >= 3) {
+                if (ozm != -1) az = fma(kc + K[p + ozm], xc - x[p + ozm], az);
+                else if (L.bclo[2] == FLD_BC_DIRICHLET) dir += L.w[2];
+                if (ozp != -1) az = fma(kc + K[p + ozp], xc - x[p + ozp], az);
+                else if (L.bchi[2] == FLD_BC_DIRICHLET) dir += L.w[2];
+            }
+            double res = fma(-hx, ax, b[p] - xc);
+            res = fma(-hy, ay, res);
+            res = fma(-hz, az, res);
+            if (dir != 0.0) res = fma(-2.0 * dir * kc, xc, res);
+            if (r32) r32[p] = (float)res;
+            acc2 = fma(res, res, acc2);
         }
     }
     acc2 = block_sum(acc2, sh);
@@ -421,7 +528,9 @@ void launch_finish_sum(const double* partials, int nparts, double* out, cudaStre
     template void launch_resid_restrict<T>(const Lvl&, const Lvl&, const T*, const T*, const T*,  \
                                            T*, int, cudaStream_t);                               \
     template void launch_prolong<T>(const Lvl&, const Lvl&, T*, const T*, int, cudaStream_t);     \
-    template void launch_coarse_solve<T>(const Lvl&, T*, const T*, const T*, int, cudaStream_t);
+    template void launch_coarse_solve<T>(const Lvl&, T*, const T*, const T*, int, cudaStream_t); \
+    template bool rb_half_supported<T>(const Lvl&);                                              \
+    template void launch_rb_half<T>(const Lvl&, int, T*, const T*, const T*, cudaStream_t);
 FLD_INST(double)
 FLD_INST(float)
 

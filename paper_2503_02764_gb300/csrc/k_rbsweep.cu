@@ -33,17 +33,59 @@ __device__ __forceinline__ int wrap_idx(int g, int n, bool periodic) {
 
 }  // namespace
 
+// Asynchronous 4- or 8-byte global -> shared copy (zero-filled when !valid).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int sz = valid ? BYTES : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES),
+                 "r"(sz)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Ring depths: x needs planes m-1..m+1 for red(m) plus the prefetched m+2 (4);
+// K needs m-2..m+1 (black(m-1) and red(m)) plus m+2 (5); b needs m-1, m plus m+1 (3);
+// the red-updated iterate needs m-2..m (3).
+constexpr int NXR = 4, NKR = 5, NBR = 3, NRR = 3;
+
+template <typename T>
+__device__ __forceinline__ T fast_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+
+// Shared-memory plane layout (all four arrays): TY + 4 rows of XWP = TX + 2 XL
+// elements, row r holding global y = ty0 - 2 + r and column c global x = tx0 - XL + c.
+// XL >= 2 is a whole 16-byte chunk, so interior rows are copied with 16-byte
+// cp.async when the row length nx is a multiple of the chunk.
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+struct RbLayout {
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int XL = V > 2 ? V : 2;
+    static constexpr int XWP = TX + 2 * XL;
+    static constexpr int NROW = TY + 4;
+    static constexpr int PL = XWP * NROW;
+    static constexpr int CPR = XWP / V;
+};
+
+template <typename T, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
 k_rb_sweep(Lvl L, const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ b,
-           const T* __restrict__ K, int cz) {
-    constexpr int XW = TX + 4, XH = TY + 4, XP = XW * XH;   // halo-2 plane
-    constexpr int RW = TX + 2, RH = TY + 2, RP = RW * RH;   // halo-1 plane
+           const T* __restrict__ K, int cz, int vec_ok) {
+    using LY = RbLayout<T, TX, TY>;
+    constexpr int V = LY::V, XL = LY::XL, XWP = LY::XWP, NROW = LY::NROW, PL = LY::PL;
+    constexpr int CPR = LY::CPR, NT = TX * TY;
+    constexpr int NXK = NROW * CPR, NB = (NROW - 2) * CPR;   // x/K chunks, b chunks
+    constexpr int RWID = TX + 2, NRED = (TY + 2) * RWID;     // red region (halo 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Xs = reinterpret_cast<T*>(smem_raw);   // 3 planes
-    T* Ks = Xs + 3 * XP;                      // 4 planes
-    T* Bs = Ks + 4 * XP;                      // 2 planes (halo 1)
-    T* Rs = Bs + 2 * RP;                      // 3 planes (halo 1)
+    T* Xs = reinterpret_cast<T*>(smem_raw);
+    T* Ks = Xs + NXR * PL;
+    T* Bs = Ks + NKR * PL;
+    T* Rs = Bs + NBR * PL;
 
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int tiles_x = (nx + TX - 1) / TX, tiles_y = (ny + TY - 1) / TY;
@@ -58,195 +100,173 @@ k_rb_sweep(Lvl L, const T* __restrict__ xin, T* __restrict__ xout, const T* __re
     const bool yper = L.bclo[1] == FLD_BC_PERIODIC;
     const bool three = L.ndim == 3;
     const bool zper = three && L.bclo[2] == FLD_BC_PERIODIC;
-    const T wx = (T)L.w[0], wy = (T)L.w[1], wz = (T)L.w[2];
-    const long long plane = (long long)nx * ny;
+    const T wx = wgt<T>(L, 0), wy = wgt<T>(L, 1), wz = wgt<T>(L, 2);
+    const bool xd_lo = L.bclo[0] == FLD_BC_DIRICHLET, xd_hi = L.bchi[0] == FLD_BC_DIRICHLET;
+    const bool yd_lo = L.bclo[1] == FLD_BC_DIRICHLET, yd_hi = L.bchi[1] == FLD_BC_DIRICHLET;
+    const bool zd_lo = L.bclo[2] == FLD_BC_DIRICHLET, zd_hi = L.bchi[2] == FLD_BC_DIRICHLET;
+    const int plane = nx * ny;
     const int tid = threadIdx.x;
-    constexpr int NT = TX * TY;
 
     auto zmap = [&](int m) { return three ? wrap_idx(m, nz, zper) : (m == 0 ? 0 : -1); };
+    auto ring = [](int m, int n) { return ((m % n) + n) % n; };
 
-    // load plane m (if it exists) of x and K (halo 2), and of b (halo 1)
-    auto load_xk = [&](int m) {
-        const int gz = zmap(m);
-        if (gz < 0) return;
-        T* xd = Xs + ((m + 3) % 3) * XP;
-        T* kd = Ks + ((m + 4) % 4) * XP;
-        const long long zb = (long long)gz * plane;
-        for (int e = tid; e < XP; e += NT) {
-            const int ly = e / XW, lx = e - ly * XW;
-            const int gx = wrap_idx(tx0 - 2 + lx, nx, xper);
-            const int gy = wrap_idx(ty0 - 2 + ly, ny, yper);
-            T xv = T(0), kv = T(0);
-            if (gx >= 0 && gy >= 0) {
-                const long long p = zb + (long long)gy * nx + gx;
-                xv = xin[p];
-                kv = K[p];
+    // copy plane m of x and K (all rows) and plane mb of b (halo-1 rows)
+    auto issue = [&](int m, int mb) {
+        const int gzx = zmap(m), gzb = zmap(mb);
+        T* xd = Xs + ring(m, NXR) * PL;
+        T* kd = Ks + ring(m, NKR) * PL;
+        T* bd = Bs + ring(mb, NBR) * PL;
+        for (int c = tid; c < NXK + NB; c += NT) {
+            const bool isb = c >= NXK;
+            const int cc = isb ? c - NXK + CPR : c;          // b skips the first row
+            const int gz = isb ? gzb : gzx;
+            if (gz < 0) continue;
+            const int row = cc / CPR, ch = cc - row * CPR;
+            const int gy = wrap_idx(ty0 - 2 + row, ny, yper);
+            const int gx0 = tx0 - XL + V * ch;
+            const int so = row * XWP + V * ch;
+            if (isb) {
+                T* dst = bd + so;
+                const T* src = b + (long long)gz * plane;
+                if (gy >= 0 && vec_ok && gx0 >= 0 && gx0 + V <= nx) {
+                    cp_async<16>(dst, src + gy * nx + gx0, true);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int gx = wrap_idx(gx0 + v, nx, xper);
+                        const bool ok = gy >= 0 && gx >= 0;
+                        cp_async<sizeof(T)>(dst + v, src + (ok ? gy * nx + gx : 0), ok);
+                    }
+                }
+            } else {
+                const long long zo = (long long)gz * plane;
+                if (gy >= 0 && vec_ok && gx0 >= 0 && gx0 + V <= nx) {
+                    const int go = gy * nx + gx0;
+                    cp_async<16>(xd + so, xin + zo + go, true);
+                    cp_async<16>(kd + so, K + zo + go, true);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int gx = wrap_idx(gx0 + v, nx, xper);
+                        const bool ok = gy >= 0 && gx >= 0;
+                        const long long go = zo + (ok ? gy * nx + gx : 0);
+                        cp_async<sizeof(T)>(xd + so + v, xin + go, ok);
+                        cp_async<sizeof(T)>(kd + so + v, K + go, ok);
+                    }
+                }
             }
-            xd[e] = xv;
-            kd[e] = kv;
         }
-    };
-    auto load_b = [&](int m) {
-        const int gz = zmap(m);
-        if (gz < 0) return;
-        T* bd = Bs + ((m + 2) % 2) * RP;
-        const long long zb = (long long)gz * plane;
-        for (int e = tid; e < RP; e += NT) {
-            const int ly = e / RW, lx = e - ly * RW;
-            const int gx = wrap_idx(tx0 - 1 + lx, nx, xper);
-            const int gy = wrap_idx(ty0 - 1 + ly, ny, yper);
-            bd[e] = (gx >= 0 && gy >= 0) ? b[zb + (long long)gy * nx + gx] : T(0);
-        }
+        cp_async_commit();
     };
 
-    // Stencil of cell with global (wrapped) coordinates (gx, gy, gz) whose centre sits at
-    // index c of a plane of width W in the arrays V (values) and Kp (coefficients);
-    // Vm/Vp, Km/Kp2 are the planes below/above.
-    auto update = [&](int gx, int gy, int gz, const T* V, const T* Vm, const T* Vp, const T* Kc_,
-                      const T* Km, const T* Kq, int c, int W, T bval) -> T {
-        const T kc = Kc_[c];
+    // (b + acc)/(1 + sw) of the cell at index c of value planes V0 (Vm, Vq below and
+    // above) and coefficient planes K0 (Km, Kq), all in the common layout.
+    auto relax = [&](int gx, int gy, int gz, const T* V0, const T* Vm, const T* Vq,
+                     const T* K0, const T* Km, const T* Kq, int c, T bval) -> T {
+        const T kc = K0[c];
         T sw = T(0), acc = T(0);
-        // x faces
         if (gx > 0 || xper) {
-            const T w = T(0.5) * (kc + Kc_[c - 1]) * wx;
+            const T w = T(0.5) * (kc + K0[c - 1]) * wx;
             sw += w;
-            acc += w * V[c - 1];
-        } else if (L.bclo[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
+            acc += w * V0[c - 1];
+        } else if (xd_lo) sw += T(2) * kc * wx;
         if (gx < nx - 1 || xper) {
-            const T w = T(0.5) * (kc + Kc_[c + 1]) * wx;
+            const T w = T(0.5) * (kc + K0[c + 1]) * wx;
             sw += w;
-            acc += w * V[c + 1];
-        } else if (L.bchi[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
-        // y faces
+            acc += w * V0[c + 1];
+        } else if (xd_hi) sw += T(2) * kc * wx;
         if (gy > 0 || yper) {
-            const T w = T(0.5) * (kc + Kc_[c - W]) * wy;
+            const T w = T(0.5) * (kc + K0[c - XWP]) * wy;
             sw += w;
-            acc += w * V[c - W];
-        } else if (L.bclo[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
+            acc += w * V0[c - XWP];
+        } else if (yd_lo) sw += T(2) * kc * wy;
         if (gy < ny - 1 || yper) {
-            const T w = T(0.5) * (kc + Kc_[c + W]) * wy;
+            const T w = T(0.5) * (kc + K0[c + XWP]) * wy;
             sw += w;
-            acc += w * V[c + W];
-        } else if (L.bchi[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
-        // z faces
+            acc += w * V0[c + XWP];
+        } else if (yd_hi) sw += T(2) * kc * wy;
         if (three) {
             if (gz > 0 || zper) {
                 const T w = T(0.5) * (kc + Km[c]) * wz;
                 sw += w;
                 acc += w * Vm[c];
-            } else if (L.bclo[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
+            } else if (zd_lo) sw += T(2) * kc * wz;
             if (gz < nz - 1 || zper) {
                 const T w = T(0.5) * (kc + Kq[c]) * wz;
                 sw += w;
-                acc += w * Vp[c];
-            } else if (L.bchi[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
+                acc += w * Vq[c];
+            } else if (zd_hi) sw += T(2) * kc * wz;
         }
-        return (bval + acc) / (T(1) + sw);
+        return fast_div<T>(bval + acc, T(1) + sw);
     };
 
-    // red-updated values of plane m on the tile and its 1-cell ring
+    // red half of plane m on the tile and its 1-cell ring
     auto red_plane = [&](int m) {
         const int gz = zmap(m);
         if (gz < 0) return;
-        const T* X0 = Xs + ((m + 3) % 3) * XP;
-        const T* Xm = Xs + ((m + 2) % 3) * XP;
-        const T* Xq = Xs + ((m + 1) % 3) * XP;
-        const T* K0 = Ks + ((m + 4) % 4) * XP;
-        const T* Km = Ks + ((m + 3) % 4) * XP;
-        const T* Kq = Ks + ((m + 5) % 4) * XP;
-        const T* B0 = Bs + ((m + 2) % 2) * RP;
-        T* R0 = Rs + ((m + 3) % 3) * RP;
-        for (int e = tid; e < RP; e += NT) {
-            const int ry = e / RW, rx = e - ry * RW;
+        const T* X0 = Xs + ring(m, NXR) * PL;
+        const T* Xm = Xs + ring(m - 1, NXR) * PL;
+        const T* Xq = Xs + ring(m + 1, NXR) * PL;
+        const T* K0 = Ks + ring(m, NKR) * PL;
+        const T* Km = Ks + ring(m - 1, NKR) * PL;
+        const T* Kq = Ks + ring(m + 1, NKR) * PL;
+        const T* B0 = Bs + ring(m, NBR) * PL;
+        T* R0 = Rs + ring(m, NRR) * PL;
+        for (int e = tid; e < NRED; e += NT) {
+            const int ry = e / RWID, rx = e - ry * RWID;
             const int gx = wrap_idx(tx0 - 1 + rx, nx, xper);
             const int gy = wrap_idx(ty0 - 1 + ry, ny, yper);
-            const int c = (ry + 1) * XW + rx + 1;
+            const int c = (ry + 1) * XWP + rx - 1 + XL;
             T v = X0[c];
             if (gx >= 0 && gy >= 0 && ((gx + gy + gz) & 1) == 0)
-                v = update(gx, gy, gz, X0, Xm, Xq, K0, Km, Kq, c, XW, B0[e]);
-            R0[e] = v;
+                v = relax(gx, gy, gz, X0, Xm, Xq, K0, Km, Kq, c, B0[c]);
+            R0[c] = v;
         }
     };
 
-    // black half-sweep of plane m on the tile, written to xout
+    // black half of plane m on the tile, written to xout
     auto black_plane = [&](int m) {
         const int gz = zmap(m);
-        const T* R0 = Rs + ((m + 3) % 3) * RP;
-        const T* Rm = Rs + ((m + 2) % 3) * RP;
-        const T* Rq = Rs + ((m + 1) % 3) * RP;
-        const T* K0 = Ks + ((m + 4) % 4) * XP;
-        const T* Km = Ks + ((m + 3) % 4) * XP;
-        const T* Kq = Ks + ((m + 5) % 4) * XP;
-        const T* B0 = Bs + ((m + 2) % 2) * RP;
+        const T* R0 = Rs + ring(m, NRR) * PL;
+        const T* Rm = Rs + ring(m - 1, NRR) * PL;
+        const T* Rq = Rs + ring(m + 1, NRR) * PL;
+        const T* K0 = Ks + ring(m, NKR) * PL;
+        const T* Km = Ks + ring(m - 1, NKR) * PL;
+        const T* Kq = Ks + ring(m + 1, NKR) * PL;
+        const T* B0 = Bs + ring(m, NBR) * PL;
         const long long zb = (long long)gz * plane;
         for (int e = tid; e < TX * TY; e += NT) {
             const int ly = e / TX, lx = e - ly * TX;
             const int gx = tx0 + lx, gy = ty0 + ly;
             if (gx >= nx || gy >= ny) continue;
-            const int cr = (ly + 1) * RW + lx + 1;      // index in the halo-1 planes
-            const int ck = (ly + 2) * XW + lx + 2;      // index in the halo-2 planes
-            T v = R0[cr];
-            if (((gx + gy + gz) & 1) == 1) {
-                // neighbours from the red-updated planes, coefficients from K: the two
-                // plane layouts differ, so pass K re-based to the R layout
-                const T kc = K0[ck];
-                T sw = T(0), acc = T(0);
-                if (gx > 0 || xper) {
-                    const T w = T(0.5) * (kc + K0[ck - 1]) * wx;
-                    sw += w;
-                    acc += w * R0[cr - 1];
-                } else if (L.bclo[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
-                if (gx < nx - 1 || xper) {
-                    const T w = T(0.5) * (kc + K0[ck + 1]) * wx;
-                    sw += w;
-                    acc += w * R0[cr + 1];
-                } else if (L.bchi[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
-                if (gy > 0 || yper) {
-                    const T w = T(0.5) * (kc + K0[ck - XW]) * wy;
-                    sw += w;
-                    acc += w * R0[cr - RW];
-                } else if (L.bclo[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
-                if (gy < ny - 1 || yper) {
-                    const T w = T(0.5) * (kc + K0[ck + XW]) * wy;
-                    sw += w;
-                    acc += w * R0[cr + RW];
-                } else if (L.bchi[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
-                if (three) {
-                    if (gz > 0 || zper) {
-                        const T w = T(0.5) * (kc + Km[ck]) * wz;
-                        sw += w;
-                        acc += w * Rm[cr];
-                    } else if (L.bclo[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
-                    if (gz < nz - 1 || zper) {
-                        const T w = T(0.5) * (kc + Kq[ck]) * wz;
-                        sw += w;
-                        acc += w * Rq[cr];
-                    } else if (L.bchi[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
-                }
-                v = (B0[cr] + acc) / (T(1) + sw);
-            }
-            xout[zb + (long long)gy * nx + gx] = v;
+            const int c = (ly + 2) * XWP + lx + XL;
+            T v = R0[c];
+            if (((gx + gy + gz) & 1) == 1) v = relax(gx, gy, gz, R0, Rm, Rq, K0, Km, Kq, c, B0[c]);
+            xout[zb + gy * nx + gx] = v;
         }
     };
 
-    // pipeline: red plane m needs x, K at m-1..m+1 and b at m; black plane m-1 needs
-    // red planes m-2..m, K at m-2..m and b at m-1
-    load_xk(z0 - 2);
-    load_xk(z0 - 1);
+    // Pipeline. Iteration m computes red(m) and black(m-1); it needs x, K at m-1..m+1
+    // (and K at m-2), b at m-1 and m. The copies for the next iteration (x, K at m+2,
+    // b at m+1) are issued first so they overlap this iteration's arithmetic.
+    issue(z0 - 2, z0 - 1);
+    issue(z0 - 1, z0 - 1);     // (b plane reissued: harmless, same slot and data)
+    issue(z0, z0);
     for (int m = z0 - 1; m <= z1; ++m) {
-        load_xk(m + 1);
-        load_b(m);
+        issue(m + 2, m + 1);
+        cp_async_wait<1>();    // all but the group just issued have landed
         __syncthreads();
         red_plane(m);
         __syncthreads();
         if (m - 1 >= z0) black_plane(m - 1);
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
-template <typename T>
-static size_t rb_smem(int tx, int ty) {
-    return sizeof(T) * (size_t)(7 * (tx + 4) * (ty + 4) + 5 * (tx + 2) * (ty + 2));
+template <typename T, int TX, int TY>
+static size_t rb_smem() {
+    return sizeof(T) * (size_t)(NXR + NKR + NBR + NRR) * RbLayout<T, TX, TY>::PL;
 }
 
 template <typename T>
@@ -256,18 +276,25 @@ bool rb_sweep_supported(const Lvl& L) {
 
 template <typename T>
 void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K, cudaStream_t s) {
-    constexpr int TX = 64, TY = 8;
+    constexpr int TX = 32, TY = 8, MINB = sizeof(T) == 4 ? 5 : 3;
     const int tiles = ((L.n[0] + TX - 1) / TX) * ((L.n[1] + TY - 1) / TY);
-    const int cz = (L.ndim == 3) ? std::max(8, std::min(L.n[2], 32)) : 1;
+    int cz = 1;
+    if (L.ndim == 3) {
+        // enough z-chunks for ~3 waves of blocks, each chunk >= 8 planes
+        const int want = (152 * MINB * 3 + tiles - 1) / tiles;
+        cz = std::max(8, (L.n[2] + want - 1) / std::max(want, 1));
+        cz = std::min(cz, L.n[2]);
+    }
     const int zch = (L.n[2] + cz - 1) / cz;
-    const size_t sm = rb_smem<T>(TX, TY);
+    const size_t sm = rb_smem<T, TX, TY>();
+    const int vec_ok = (L.n[0] % RbLayout<T, TX, TY>::V) == 0;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_rb_sweep<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_rb_sweep<T, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm);
         attr_set = true;
     }
-    k_rb_sweep<T, TX, TY><<<tiles * zch, TX * TY, sm, s>>>(L, xin, xout, b, K, cz);
+    k_rb_sweep<T, TX, TY, MINB><<<tiles * zch, TX * TY, sm, s>>>(L, xin, xout, b, K, cz, vec_ok);
 }
 
 template bool rb_sweep_supported<float>(const Lvl&);
