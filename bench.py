@@ -42,6 +42,9 @@ BYTES_PER_CELL = {
     "prep": 36.0,             # D, E read; K64, K32, b written
     "sumsq": 8.0,             # b read
     "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
+    "resid_df": 40.0,         # x (hi, lo), e32, b (hi, lo), K (hi, lo) read; x (hi, lo), r32 written
+    "rbhalf32": 16.0,         # x, K, b read; x written (one colour per launch, whole lines)
+    "rbhalf64": 32.0,
     "add_correction": 20.0,   # x, e32 read; x written
     "smooth32": 16.0,         # xin, b, K read; xout written
     "smooth64": 32.0,
@@ -168,7 +171,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
@@ -197,7 +200,8 @@ def main():
     barrier()
 
     P = I.stratified_3d(args.n)
-    prec = fld.PREC_MIXED if args.precision == "mixed" else fld.PREC_FP64
+    prec = {"mixed_df": fld.PREC_MIXED_DF, "mixed": fld.PREC_MIXED, "fp64": fld.PREC_FP64}[
+        args.precision]
     hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50,
                     smoother=args.smoother)
     consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
@@ -295,7 +299,8 @@ def main():
     if rank == 0 and not args.no_ttt:
         D = torch.empty_like(E)
         hd.limiter(consts, op, E, rho, T, ebc, D)
-        for name, pr in (("mixed", fld.PREC_MIXED), ("fp64", fld.PREC_FP64)):
+        for name, pr in (("mixed_df", fld.PREC_MIXED_DF), ("mixed", fld.PREC_MIXED),
+                         ("fp64", fld.PREC_FP64)):
             hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, smoother=args.smoother)
             times, cyc = [], 0
             for rep in range(4):
@@ -314,8 +319,11 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 smoothing/transfers + f64 residual/correction/limiter/exchange"
-            if prec == fld.PREC_MIXED else "f64",
+            "dtype": {fld.PREC_MIXED_DF: "f32 V-cycles + double-f32 (48-bit) refinement residual/"
+                                         "correction + f64 limiter/exchange/coarse solve",
+                      fld.PREC_MIXED: "f32 V-cycles + f64 refinement residual/correction/"
+                                      "limiter/exchange/coarse solve",
+                      fld.PREC_FP64: "f64"}[prec],
             "data": "synthetic",
             "config": {"workload": "stratified3d_%d^3 (x,y periodic, z Dirichlet, Kramers opacity, "
                                    "dt = 10x explicit limit)" % args.n,

@@ -62,9 +62,18 @@ enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2 };
 enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_POWER = 1 };
 /* limiter: Levermore-Pomraning (Eq. fld_lambda) or the diffusion limit lambda = 1/3 */
 enum { FLD_LIMITER_LP = 0, FLD_LIMITER_DIFFUSION = 1 };
-/* solve precision: plain FP64 V-cycles, or FP32 V-cycles inside FP64 iterative
-   refinement (FP64 residual, correction and coarsest-level solve) */
-enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1 };
+/* solve precision:
+   FP64      plain FP64 V-cycles;
+   MIXED     FP32 V-cycles (smoothing, restriction, prolongation) inside iterative
+             refinement whose residual and correction are FP64 (the coarsest-level solve
+             is FP64 arithmetic in every mode);
+   MIXED_DF  as MIXED, but the refinement's iterate, right-hand side, coefficients,
+             residual and correction are carried as double-FP32 pairs (48-bit significand,
+             error-free transformations) between reading E and writing it back: FP64-grade
+             accuracy at FP32 instruction cost, since FP64 issues at a small fraction of
+             the FP32 rate on this GPU. Values must stay within the FP32 exponent range
+             after the power-of-two scaling the solve applies (|S E| well inside 1e-30..1e30). */
+enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1, FLD_PREC_MIXED_DF = 2 };
 
 /* Physical constants in the caller's units: speed of light c, radiation
    constant a_r, adiabatic index gamma and R_gas = k_B / (mu m_p). */

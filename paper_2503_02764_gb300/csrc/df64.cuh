@@ -1,0 +1,68 @@
+// Double-FP32 ("df") arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers with |lo| <= ulp(hi)/2, giving a 48-bit significand with the FP32 exponent
+// range. Built from error-free transformations:
+//   two_sum       Knuth, TAOCP vol. 2, Sect. 4.2.2 (exact a + b = s + e, any order);
+//   fast_two_sum  Dekker 1971, "A floating-point technique for extending the available
+//                 precision" (exact when |a| >= |b|);
+//   two_prod      a*b = p + e exactly with one fused multiply-add (Ogita, Rump and
+//                 Oishi 2005, "Accurate sum and dot product").
+// The df add/mul below are the usual "sloppy" double-word forms (relative error a few
+// units of 2^-48). FP64 issues at 1/58 of the FP32 rate on this GPU, so these FP32
+// sequences are the cheap way to reach FP64-grade accuracy in the memory-bound kernels.
+#pragma once
+
+namespace fld {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+
+__device__ __forceinline__ df df_add_f(df x, float y) {
+    df s = two_sum(x.hi, y);
+    s.lo = __fadd_rn(s.lo, x.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    df p = two_prod(x.hi, y.hi);
+    p.lo = __fmaf_rn(x.hi, y.lo, p.lo);
+    p.lo = __fmaf_rn(x.lo, y.hi, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+// split an FP64 value into the nearest df (hi = RN(v), lo = RN(v - hi))
+__device__ __forceinline__ df df_from_double(double v) {
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+}  // namespace fld

@@ -64,6 +64,9 @@ struct fld_handle {
     long long ncell = 0;
     LevelBufs<double> d64[MAX_LEVELS];
     LevelBufs<float> d32[MAX_LEVELS];
+    float* dfx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // iterate (hi, lo), ping-pong
+    float* dfb[2] = {nullptr, nullptr};                            // right-hand side (hi, lo)
+    float* dfK[2] = {nullptr, nullptr};                            // coefficient K (hi, lo)
     double* Dscratch = nullptr;
     double* partials = nullptr;
     DevScalars* scal = nullptr;       // device
@@ -106,7 +109,8 @@ bool grid_ok(const fld_grid* g) {
 }
 
 bool opts_ok(const fld_opts* o) {
-    return o && (o->precision == FLD_PREC_FP64 || o->precision == FLD_PREC_MIXED) && o->tol > 0 &&
+    return o && (o->precision == FLD_PREC_FP64 || o->precision == FLD_PREC_MIXED ||
+                 o->precision == FLD_PREC_MIXED_DF) && o->tol > 0 &&
            o->max_cycles >= 1 && o->nu1 >= 0 && o->nu2 >= 0 && (o->nu1 + o->nu2) >= 1 &&
            o->coarse_sweeps >= 1 &&
            (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION) &&
@@ -304,10 +308,79 @@ fld_status residual(fld_handle* h, double* x, float* r32, cudaStream_t s, double
     return read_scalars(h, s, rr, err);
 }
 
+// Mixed refinement with the residual and the correction in double-FP32: the scaled
+// iterate S x, S b and K live as (hi, lo) FP32 pairs for the duration of the solve;
+// E is read at the start and written at the end.
+fld_status diffuse_df(fld_handle* h, double* E, double bsum, fld_stats* st, cudaStream_t s) {
+    const Lvl& L0 = h->lv[0];
+    const long long n = L0.ncell;
+    int ex = 0;
+    const double rms = bsum > 0 ? std::sqrt(bsum / (double)n) : 1.0;
+    std::frexp(rms, &ex);
+    const double S = std::ldexp(1.0, -ex);        // power of two: exact scaling
+    const double bnorm = std::sqrt(bsum) * S;
+    DfW wd;
+    for (int d = 0; d < 3; ++d) {
+        const double wh = 0.5 * L0.w[d];
+        wd.hh[d] = (float)wh;
+        wd.hl[d] = (float)(wh - (double)wd.hh[d]);
+    }
+    run(h, "df_setup", 0, n, s, [&] {
+        launch_df_setup(n, S, E, h->d64[0].b, h->d64[0].K, h->dfx[0][0], h->dfx[0][1], h->dfb[0],
+                        h->dfb[1], h->dfK[0], h->dfK[1], s);
+    });
+    int cur = 0;
+    auto resid = [&](const float* e, double* rr) -> fld_status {
+        float* oh = e ? h->dfx[cur ^ 1][0] : nullptr;
+        float* ol = e ? h->dfx[cur ^ 1][1] : nullptr;
+        run(h, "resid_df", 0, n, s, [&] {
+            launch_df_resid(L0, wd, h->dfx[cur][0], h->dfx[cur][1], e, h->dfb[0], h->dfb[1],
+                            h->dfK[0], h->dfK[1], oh, ol, h->d32[0].b, h->partials, NORM_BLOCKS,
+                            NORM_THREADS, s);
+        });
+        if (e) cur ^= 1;
+        run(h, "finish_sum", 0, NORM_BLOCKS, s,
+            [&] { launch_finish_sum(h->partials, NORM_BLOCKS, &h->scal->sum, s); });
+        FLD_CK(cudaGetLastError());
+        unsigned err;
+        return read_scalars(h, s, rr, &err);
+    };
+    double r2;
+    fld_status rc = resid(nullptr, &r2);
+    if (rc != FLD_OK) return rc;
+    double rel = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->resid_hist[0] = rel;
+        st->levels = h->nlev;
+    }
+    int cyc = 0;
+    while (rel > h->o.tol && cyc < h->o.max_cycles && std::isfinite(rel)) {
+        FLD_CK(cudaMemsetAsync(h->d32[0].x, 0, sizeof(float) * n, s));
+        vcycle<float>(h, h->d32, 0, s);
+        rc = resid(h->d32[0].x, &r2);
+        if (rc != FLD_OK) return rc;
+        rel = std::sqrt(r2) / bnorm;
+        ++cyc;
+        if (st && cyc < 64) st->resid_hist[cyc] = rel;
+    }
+    run(h, "df_finish", 0, n, s, [&] {
+        launch_df_finish(n, 1.0 / S, h->dfx[cur][0], h->dfx[cur][1], E, s);
+    });
+    FLD_CK(cudaGetLastError());
+    if (st) {
+        st->cycles = cyc;
+        st->rel_resid = rel;
+    }
+    if (!std::isfinite(rel)) return FLD_ERR_DOMAIN;
+    return rel <= h->o.tol ? FLD_OK : FLD_ERR_NOT_CONVERGED;
+}
+
 fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double* E_bc, double* E,
                         fld_stats* st, cudaStream_t s) {
     const Lvl& L0 = h->lv[0];
-    const bool mixed = h->o.precision == FLD_PREC_MIXED;
+    const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF;
+    const bool mixed = h->o.precision == FLD_PREC_MIXED || dfmode;
     const double kscale = dt / (h->g.h[0] * h->g.h[0]);
     run(h, "prep", 0, L0.ncell, s, [&] {
         launch_prep_level0(L0, kscale, D, E, E_bc, h->bc_off, h->d64[0].K,
@@ -329,6 +402,7 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         return FLD_ERR_DOMAIN;
     }
     const double bnorm = std::sqrt(bsum);
+    if (dfmode) return diffuse_df(h, E, bsum, st, s);
     h->d64[0].x = E;
     double r2;
     rc = residual(h, E, mixed ? h->d32[0].b : nullptr, s, &r2, &err);
@@ -425,6 +499,12 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
         rc = rc ? rc : dalloc(h, &h->d32[l].b, n);
         rc = rc ? rc : dalloc(h, &h->d32[l].K, n);
         rc = rc ? rc : dalloc(h, &h->d32[l].tmp, n);
+    }
+    for (int q = 0; q < 2 && !rc; ++q) {
+        rc = rc ? rc : dalloc(h, &h->dfx[q][0], n0);
+        rc = rc ? rc : dalloc(h, &h->dfx[q][1], n0);
+        rc = rc ? rc : dalloc(h, &h->dfb[q], n0);
+        rc = rc ? rc : dalloc(h, &h->dfK[q], n0);
     }
     rc = rc ? rc : dalloc(h, &h->Dscratch, n0);
     rc = rc ? rc : dalloc(h, &h->partials, NORM_BLOCKS);

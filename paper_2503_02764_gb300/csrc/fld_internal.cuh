@@ -37,17 +37,59 @@ struct Opacity {
     double kappa0, a_rho, a_T;
 };
 
-__device__ __forceinline__ double opacity_eval(const Opacity& op, double rho, double T) {
-    if (op.kind == FLD_OPACITY_CONST) return op.kappa0;
-    double fr = (op.a_rho == 1.0) ? rho : pow(rho, op.a_rho);
-    double ft;
-    if (op.a_T == 0.0) ft = 1.0;
-    else if (op.a_T == -3.5) ft = 1.0 / (T * T * T * sqrt(T));   // Kramers-like law
-    else ft = pow(T, op.a_T);
-    return op.kappa0 * fr * ft;
+// v > 0 and finite, tested on the bit pattern (integer pipe, not the FP64 one).
+__device__ __forceinline__ bool pos_finite(double v) {
+    const long long b = __double_as_longlong(v);
+    return b > 0 && b < 0x7FF0000000000000LL;
 }
 
-__device__ __forceinline__ bool pos_finite(double v) { return v > 0.0 && v < INFINITY; }
+// 1/sqrt(t) for t within the FP32 normal range: FP32 seed refined by Newton-Raphson on
+// f(y) = 1/y^2 - t, y <- y (3/2 - t y^2 / 2); each step squares the relative error
+// (~2^-22 -> ~2^-44 -> rounding). `steps` = 1 or 2.
+__device__ __forceinline__ double rsqrt_nr(double t, int steps) {
+    double y = (double)rsqrtf((float)t);
+    const double ht = 0.5 * t;
+    y = y * fma(-ht, y * y, 1.5);
+    if (steps > 1) y = y * fma(-ht, y * y, 1.5);
+    return y;
+}
+
+// 1/a for a within the FP32 normal range: FP32 reciprocal seed refined by Newton-Raphson
+// on f(y) = 1/y - a, y <- y + y (1 - a y); each step squares the relative error.
+__device__ __forceinline__ double rcp_nr(double a) {
+    double y = (double)__frcp_rn((float)a);
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    return fma(y, e, y);
+}
+
+// |v| within [2^-99, 2^99] (safely inside the FP32 normal range), tested on the
+// exponent bits with integer operations.
+__device__ __forceinline__ bool in_f32_range(double v) {
+    const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023;
+    return e > -100 && e < 99;
+}
+
+__device__ __forceinline__ double opacity_eval(const Opacity& op, double rho, double T) {
+    if (op.kind == FLD_OPACITY_CONST) return op.kappa0;
+    const double fr = (op.a_rho == 1.0) ? rho : pow(rho, op.a_rho);
+    double ft;
+    if (op.a_T == 0.0) {
+        ft = 1.0;
+    } else if (op.a_T == -3.5) {            // Kramers-like law: T^-3.5 = (T^-1/2)^7
+        if (in_f32_range(T)) {
+            const double y = rsqrt_nr(T, 2);
+            const double y2 = y * y;
+            ft = y2 * y2 * y2 * y;
+        } else {
+            ft = 1.0 / (T * T * T * sqrt(T));
+        }
+    } else {
+        ft = pow(T, op.a_T);
+    }
+    return op.kappa0 * fr * ft;
+}
 
 // ----------------------------------------------------------------- launchers
 // pointwise / limiter (k_pointwise.cu)
@@ -87,6 +129,20 @@ void launch_coarse_solve(const Lvl& L, T* x, const T* b, const T* K, int sweeps,
 void launch_resid64(const Lvl& L, const double* x, const double* b, const double* K,
                     float* r32, double* partials, int nblocks, int block, cudaStream_t s);
 void launch_add_correction(long long n, double* x, const float* e, cudaStream_t s);
+
+// double-FP32 refinement (k_df.cu): half axis weights w_d/2 as (hi, lo) pairs
+struct DfW {
+    float hh[3], hl[3];
+};
+void launch_df_setup(long long n, double S, const double* E, const double* b, const double* K,
+                     float* xh, float* xl, float* bh, float* bl, float* Kh, float* Kl,
+                     cudaStream_t s);
+void launch_df_finish(long long n, double invS, const float* xh, const float* xl, double* E,
+                      cudaStream_t s);
+void launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* xl, const float* e,
+                     const float* bh, const float* bl, const float* Kh, const float* Kl, float* oh,
+                     float* ol, float* r32, double* partials, int nblocks, int block,
+                     cudaStream_t s);
 void launch_sumsq(long long n, const double* v, double* partials, int nblocks, cudaStream_t s);
 void launch_finish_sum(const double* partials, int nparts, double* out, cudaStream_t s);
 

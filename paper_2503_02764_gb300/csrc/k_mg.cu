@@ -399,9 +399,70 @@ __global__ void k_coarse_solve(Lvl L, T* __restrict__ x, const T* __restrict__ b
     for (int p = threadIdx.x; p < n; p += blockDim.x) x[p] = (T)xs[p];
 }
 
+// Coarsest level with at most MAX_DENSE cells: the level matrix is assembled in shared
+// memory and solved exactly by Gauss-Jordan elimination in FP64 (no pivoting: the
+// matrix is symmetric, diagonally dominant with a unit-or-larger excess). One thread
+// per row.
+constexpr int MAX_DENSE = 64;
+
+template <typename T>
+__global__ void k_coarse_dense(Lvl L, T* __restrict__ x, const T* __restrict__ b,
+                               const T* __restrict__ K) {
+    __shared__ double A[MAX_DENSE][MAX_DENSE + 1];
+    const int n = (int)L.ncell;
+    const int r = threadIdx.x;
+    if (r < n) {
+        for (int c = 0; c <= n; ++c) A[r][c] = 0.0;
+        int i, j, k;
+        decode(L, r, i, j, k);
+        const int c3[3] = {i, j, k};
+        const double kc = (double)K[r];
+        double diag = 1.0;
+        int stride = 1;
+        for (int d = 0; d < L.ndim; ++d) {
+            const int nd = L.n[d];
+            const double wd = L.w[d];
+            for (int side = 0; side < 2; ++side) {
+                int q = -1;
+                const int kind = side ? L.bchi[d] : L.bclo[d];
+                if (side == 0) {
+                    if (c3[d] > 0) q = r - stride;
+                    else if (kind == FLD_BC_PERIODIC) q = r + (nd - 1) * stride;
+                } else {
+                    if (c3[d] < nd - 1) q = r + stride;
+                    else if (kind == FLD_BC_PERIODIC) q = r - (nd - 1) * stride;
+                }
+                if (q >= 0) {
+                    const double w = 0.5 * (kc + (double)K[q]) * wd;
+                    diag += w;
+                    A[r][q] -= w;
+                } else if (kind == FLD_BC_DIRICHLET) {
+                    diag += 2.0 * kc * wd;
+                }
+            }
+            stride *= nd;
+        }
+        A[r][r] += diag;
+        A[r][n] = (double)b[r];
+    }
+    for (int p = 0; p < n; ++p) {
+        __syncthreads();
+        double f = 0.0;
+        if (r < n && r != p) f = A[r][p] / A[p][p];
+        __syncthreads();
+        if (r < n && r != p)
+            for (int c = p; c <= n; ++c) A[r][c] = fma(-f, A[p][c], A[r][c]);
+    }
+    __syncthreads();
+    if (r < n) x[r] = (T)(A[r][n] / A[r][r]);
+}
+
 template <typename T>
 void launch_coarse_solve(const Lvl& L, T* x, const T* b, const T* K, int sweeps, cudaStream_t s) {
-    k_coarse_solve<T><<<1, 256, 0, s>>>(L, x, b, K, sweeps);
+    if (L.ncell <= MAX_DENSE)
+        k_coarse_dense<T><<<1, MAX_DENSE, 0, s>>>(L, x, b, K);
+    else
+        k_coarse_solve<T><<<1, 256, 0, s>>>(L, x, b, K, sweeps);
 }
 
 // ----------------------------------------------------------------- FP64 residual + norms

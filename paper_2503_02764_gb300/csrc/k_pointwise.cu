@@ -21,16 +21,6 @@ namespace fld {
 // ~1e-14 T). Cells whose coefficients fall outside the FP32 range take a plain FP64
 // Newton iteration instead.
 
-// 1/a for 1 <= a < 1e30 by Newton-Raphson on y -> y + y (1 - a y), seeded with the
-// FP32 reciprocal; each step squares the relative error (2^-23 -> 2^-46 -> rounding).
-__device__ __forceinline__ double rcp_nr(double a) {
-    double y = (double)__frcp_rn((float)a);
-    double e = fma(-a, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-a, y, 1.0);
-    return fma(y, e, y);
-}
-
 __device__ __forceinline__ bool f32_ok(double v) { return v > 1e-30 && v < 1e30; }
 
 __device__ double exchange_root(double alpha, double beta, double q) {
@@ -181,6 +171,7 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
             atomicOr(err, ERRBIT_DOMAIN);
             continue;
         }
+        const double kr = kap * r;
         double lm = 1.0 / 3.0;
         if (mode == FLD_LIMITER_LP) {
             double g2 = 0.0;
@@ -192,10 +183,25 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                 const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
                 g2 = fma(g, g, g2);
             }
-            const double R = sqrt(g2) / (kap * r * Ec);
+            // R = |grad E| / (kappa rho E), lambda = (2 + R)/(6 + 3R + R^2) and
+            // D = c lambda / (kappa rho) = c lambda E v with v = 1/(kappa rho E): two
+            // reciprocals and one square root, by FP32-seeded Newton-Raphson where the
+            // operands allow it (FP64 issues at a small fraction of the FP32 rate).
+            const double m = kr * Ec;
+            if (in_f32_range(m) && (g2 == 0.0 || in_f32_range(g2))) {
+                const double v = rcp_nr(m);
+                const double R = g2 > 0.0 ? g2 * rsqrt_nr(g2, 2) * v : 0.0;
+                const double P = 2.0 + R, Q = fma(R, R + 3.0, 6.0);
+                const double rQ = in_f32_range(Q) ? rcp_nr(Q) : 1.0 / Q;
+                lm = P * rQ;
+                D[p] = c * lm * (Ec * v);
+                if (lam) lam[p] = lm;
+                continue;
+            }
+            const double R = sqrt(g2) / m;
             lm = (2.0 + R) / (6.0 + 3.0 * R + R * R);
         }
-        D[p] = c * lm / (kap * r);
+        D[p] = in_f32_range(kr) ? c * lm * rcp_nr(kr) : c * lm / kr;
         if (lam) lam[p] = lm;
     }
 }

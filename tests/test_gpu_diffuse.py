@@ -48,12 +48,15 @@ def _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, tol=1e-14, smo
     st = hd.diffuse(dt, dev(torch, D), dev(torch, packed) if packed.size else None, Ed,
                     raise_on_error=False)
     assert st["status"] in (0, 3), st
-    assert st["rel_resid"] < max(tol, 1e-13), st     # tol, or the FP64 residual floor
+    # tol, or the residual floor: ~1e-13 for an FP64 residual; for the double-FP32
+    # residual (48-bit) the floor is cond(A) x 2^-48, ~1e-11 on the stiffest case here
+    floor = 1e-13 if precision != 2 else 1e-10
+    assert st["rel_resid"] < max(tol, floor), st
     return host(Ed).reshape(shape), st
 
 
 @pytest.mark.parametrize("smoother", [0, 1, 2])
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10), (2, 1e-10)])
 @pytest.mark.parametrize("shape,h,bc,dt,sigma", CASES)
 def test_diffuse_matches_direct_solve(shape, h, bc, dt, sigma, precision, tol, smoother):
     # smoother 0: in-place half sweeps, 1: out-of-place half sweeps, 2: fused single pass
@@ -65,7 +68,7 @@ def test_diffuse_matches_direct_solve(shape, h, bc, dt, sigma, precision, tol, s
     assert maxrel(x, xo) < tol, (maxrel(x, xo), st)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_convergence_rate_and_determinism(precision):
     torch = torch_cuda()
     fld = library()
@@ -94,7 +97,7 @@ def test_not_converged_status_keeps_iterate():
 def test_conservation_periodic():
     torch = torch_cuda()
     fld = library()
-    for precision in (0, 1):
+    for precision in (0, 1, 2):
         D, E, _ = _problem((33, 47), ((0, 0), (0, 0)), 1.5, 8)
         x, _ = _solve_gpu(fld, torch, (33, 47), (1, 1), ((0, 0), (0, 0)), 3.0, D, E, {}, precision)
         assert abs(x.sum() - E.sum()) / E.sum() < 1e-13

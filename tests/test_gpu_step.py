@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("cfg", [1, 2, 3, 5])
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10), (2, 1e-10)])
 def test_step_matches_oracle(cfg, precision, tol):
     torch = torch_cuda()
     fld = library()
