@@ -69,6 +69,25 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+def ncu_traffic(kernel, cells_per_launch):
+    """DRAM bytes per launch from the committed ncu capture (profiles/dram_traffic.json),
+    scaled by cells per launch; None when the kernel's source changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    src = os.path.join(ROOT, k["source"])
+    if not os.path.exists(src):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != k["sha256_16"]:
+        return None
+    return k["dram_bytes"] * cells_per_launch / d["cells"]
+
+
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -253,7 +272,8 @@ def main():
             bpc = 24.0
         achieved = bpc * dom["cells"] / (dom["ms"] * 1e-3) / 1e9
         roof = {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak_hbm,
-                "unit": "GB/s", "frac": achieved / peak_hbm, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak_hbm,
+                "traffic": ncu_traffic(dom["name"], dom["cells"] / dom["launches"]),
                 "peak_source": peak_kind, "launches": dom["launches"],
                 "avg_launch_us": 1e3 * dom["ms"] / dom["launches"],
                 "bytes_per_cell": bpc}
