@@ -201,6 +201,29 @@ int fld_prof_read(fld_handle* h, fld_prof_entry* out, int cap);
 /* Number of kernels launched by this library in this process so far. */
 long long fld_launch_count(void);
 
+/* ---------------------------------------------------------------- no-allocation solve
+   fld_diffuse_static: the same backward-Euler multigrid solve as fld_diffuse, for
+   callers that cannot allocate device memory themselves or through a handle: host
+   codes that own every byte of the GPU through their own allocator, solvers called
+   from inside a captured or otherwise allocation-free section, or real-time loops
+   that must never reach the CUDA allocator. The paper has no counterpart; this is a
+   property of the library, not of the method.
+   The workspace lives in one 16 MiB array defined in the library as a file-scope
+   __device__ variable: every GPU on which the library is loaded keeps those 16 MiB
+   until the process exits, and no call allocates or frees anything. Grids of up to
+   131072 cells are accepted in any precision mode; larger grids return FLD_ERR_ARG
+   with a message on stderr.
+   Arguments and results are those of fld_diffuse plus the grid and options a handle
+   would hold (o may be NULL for the defaults); D, E_bc and E are caller-owned device
+   arrays as above. The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) with that device current; make that first call before any
+   stream capture. Every call reuses the same array, which keeps the previous call's
+   contents (the call clears what must start at zero), so calls must not overlap on
+   the GPU: two calls in flight at once on different streams race. Host threads are
+   serialised by a lock inside the call. */
+fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, double dt, const double* D,
+                              const double* E_bc, double* E, fld_stats* stats, void* stream);
+
 /* Static string for a status code. */
 const char* fld_strerror(fld_status s);
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -662,3 +663,111 @@ const char* fld_strerror(fld_status s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free solve
+// fld_diffuse_static: the diffusion solve with its whole workspace (level pyramid,
+// scratch, reduction buffers, status word) carved from one fixed device array that the
+// library defines, so the call itself never allocates device or pinned memory.
+namespace {
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)16 << 20;   // 16 MiB on every GPU using it
+constexpr long long STATIC_MAX_CELLS = 131072;                // fits the worst-case pyramid
+constexpr int STATIC_MAX_DEVICES = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+namespace {
+unsigned char* g_static_base[STATIC_MAX_DEVICES];   // device address of the array, per device
+fld_handle g_static_handle;                         // host bookkeeping, rebuilt per call
+DevScalars g_static_host_scalars;                   // pageable host copy of the device scalars
+std::mutex g_static_mutex;
+}  // namespace
+
+extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, double dt,
+                                         const double* D, const double* E_bc, double* E,
+                                         fld_stats* stats, void* stream) {
+    if (!grid_ok(g) || !D || !E || !(dt > 0) || !std::isfinite(dt)) return FLD_ERR_ARG;
+    fld_opts def;
+    fld_default_opts(&def);
+    if (!o) o = &def;
+    if (!opts_ok(o)) return FLD_ERR_ARG;
+    const long long ncell = (long long)g->n[0] * g->n[1] * g->n[2];
+    if (ncell > STATIC_MAX_CELLS) {
+        fprintf(stderr, "fld_diffuse_static: %lld cells exceed the %lld-cell limit of the "
+                        "static workspace\n", ncell, STATIC_MAX_CELLS);
+        return FLD_ERR_ARG;
+    }
+    if (has_dirichlet(*g) && !E_bc) return FLD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    int dev = 0;
+    FLD_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return FLD_ERR_ARG;
+    if (!g_static_base[dev]) {
+        // once per device, with that device current: the host-side symbol is only a
+        // stand-in, the kernels need the device address
+        void* p = nullptr;
+        FLD_CK(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_base[dev] = (unsigned char*)p;
+    }
+    fld_handle& h = g_static_handle;
+    h.g = *g;
+    h.o = *o;
+    build_levels(&h);
+    h.ncell = h.lv[0].ncell;
+    long long off = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int sd = 0; sd < 2; ++sd) {
+            const int kind = sd ? g->bc_hi[d] : g->bc_lo[d];
+            if (d < g->ndim && kind == FLD_BC_DIRICHLET) {
+                h.bc_off[2 * d + sd] = off;
+                off += h.ncell / g->n[d];
+            } else {
+                h.bc_off[2 * d + sd] = -1;
+            }
+        }
+    size_t used = 0;
+    bool fits = true;
+    auto take = [&](size_t bytes) -> unsigned char* {
+        used = (used + 255) & ~(size_t)255;
+        if (used + bytes > STATIC_SCRATCH_BYTES) {
+            fits = false;
+            return nullptr;
+        }
+        unsigned char* q = g_static_base[dev] + used;
+        used += bytes;
+        return q;
+    };
+    const long long n0 = h.ncell;
+    h.d64[0].b = (double*)take(8 * n0);
+    h.d64[0].K = (double*)take(8 * n0);
+    h.d64[0].tmp = (double*)take(8 * n0);
+    for (int l = 1; l < h.nlev; ++l) {
+        const long long n = h.lv[l].ncell;
+        h.d64[l].x = (double*)take(8 * n);
+        h.d64[l].b = (double*)take(8 * n);
+        h.d64[l].K = (double*)take(8 * n);
+        h.d64[l].tmp = (double*)take(8 * n);
+    }
+    for (int l = 0; l < h.nlev; ++l) {
+        const long long n = h.lv[l].ncell;
+        h.d32[l].x = (float*)take(4 * n);
+        h.d32[l].b = (float*)take(4 * n);
+        h.d32[l].K = (float*)take(4 * n);
+        h.d32[l].tmp = (float*)take(4 * n);
+    }
+    for (int q = 0; q < 2; ++q) {
+        h.dfx[q][0] = (float*)take(4 * n0);
+        h.dfx[q][1] = (float*)take(4 * n0);
+        h.dfb[q] = (float*)take(4 * n0);
+        h.dfK[q] = (float*)take(4 * n0);
+    }
+    h.partials = (double*)take(8 * NORM_BLOCKS);
+    h.scal = (DevScalars*)take(sizeof(DevScalars));
+    if (!fits) return FLD_ERR_ARG;
+    h.Dscratch = nullptr;
+    h.hscal = &g_static_host_scalars;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: clear the status word and sums
+    FLD_CK(cudaMemsetAsync(h.scal, 0, sizeof(DevScalars), s));
+    return diffuse_impl(&h, dt, D, E_bc, E, stats, s);
+}

@@ -85,6 +85,8 @@ def lib():
         "fld_prof_enable": (C.c_int, [H, C.c_int, C.c_int]),
         "fld_prof_read": (C.c_int, [H, C.POINTER(fld_prof_entry), C.c_int]),
         "fld_launch_count": (C.c_longlong, []),
+        "fld_diffuse_static": (C.c_int, [C.POINTER(fld_grid), C.POINTER(fld_opts), C.c_double, P,
+                                         P, P, C.POINTER(fld_stats), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -190,6 +192,17 @@ def fld_diffuse(h, dt, D, E_bc, E, stream=None, raise_on_error=True):
     rc = lib().fld_diffuse(h, float(dt), _ptr(D), _ptr(E_bc), _ptr(E), C.byref(st), _stream(stream))
     if raise_on_error:
         _check(rc, "fld_diffuse")
+    return stats_dict(st) | {"status": rc}
+
+
+def fld_diffuse_static(grid, opts, dt, D, E_bc, E, stream=None, raise_on_error=True):
+    """The no-allocation solve: workspace in the library's fixed device array."""
+    st = fld_stats()
+    rc = lib().fld_diffuse_static(C.byref(grid), C.byref(opts) if opts is not None else None,
+                                  float(dt), _ptr(D), _ptr(E_bc), _ptr(E), C.byref(st),
+                                  _stream(stream))
+    if raise_on_error:
+        _check(rc, "fld_diffuse_static")
     return stats_dict(st) | {"status": rc}
 
 
