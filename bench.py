@@ -184,6 +184,71 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def tuned_opts(kind, problems):
+    """Autotuner cache entry for this GPU and workload, or None."""
+    try:
+        from paper_2503_02764_gb300 import autotune
+        c = autotune.cached(kind, autotune.signature(kind, problems))
+        return c["best"] if c else None
+    except Exception:
+        return None
+
+
+def run_batch(args):
+    """The batched workload: 512 independent 2D problems (sides U{32..512}) advanced in
+    one persistent launch per step (fld_step_batched), replayed from a CUDA graph."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2503_02764_gb300 import build, fld
+    from paper_2503_02764_gb300 import inputs as I
+    if rank == 0:
+        build.build()
+    ps = I.batch(args.nprob, seed_base=I.SEED_BASE + 4 + 100000 * rank)
+    tuned = tuned_opts("batch", ps)
+    kw = dict(block=args.block, cluster=args.cluster, nu1=2, nu2=2)
+    if tuned and not (args.block or args.cluster):
+        kw = {k: tuned[k] for k in ("block", "cluster", "nu1", "nu2")}
+    b = fld.Batch([(p.shape, p.h, p.bc) for p in ps], tol=1e-10, max_cycles=50, graph=1, **kw)
+    cat = lambda xs: torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
+    rho, T, E = cat([p.rho for p in ps]), cat([p.T for p in ps]), cat([p.E for p in ps])
+    consts = fld.make_consts(1.0, 1.0, 5.0 / 3.0, 1.0)
+    ops = [fld.make_opacity(p.opacity) for p in ps]
+    dts = [p.dt for p in ps]
+    for _ in range(args.warmup):
+        b.step(consts, ops, dts, rho, T, E)
+    n0 = fld.fld_launch_count()
+    stream = torch.cuda.current_stream()
+    clk = Clocks(local)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    cyc = []
+    for _ in range(args.steps):
+        rc, st = b.step(consts, ops, dts, rho, T, E)
+        cyc.append(max(x["cycles"] for x in st))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    cells = b.cells
+    line = {"metric": METRIC + " [batched]", "value": cells * args.steps * world / (ms * 1e-3),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 V-cycles + double-f32 refinement + f64 limiter/exchange",
+            "data": "synthetic",
+            "config": {"workload": "batch of %d 2D problems, sides U{32..512}, one persistent "
+                                   "launch per step, CUDA graph" % args.nprob,
+                       "cells": cells, "block": kw["block"] or 512,
+                       "cluster": kw["cluster"] or "auto", "nu1": kw["nu1"], "nu2": kw["nu2"],
+                       "autotuned": bool(tuned and not (args.block or args.cluster))},
+            "max_cycles_per_step": cyc, "clocks": clocks,
+            "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,9 +261,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--smoother", type=int, default=0, help="0 in-place half sweeps, 1 out-of-place half sweeps, 2 fused single-pass sweep")
     ap.add_argument("--no-ttt", action="store_true", help="skip the mixed-vs-FP64 solve timing")
+    ap.add_argument("--workload", default="stratified", choices=["stratified", "batch"],
+                    help="stratified: one 3D box (default); batch: 512 uneven 2D problems")
+    ap.add_argument("--nprob", type=int, default=512)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cluster", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     rank, world, local = dist_env()
     import torch
@@ -221,8 +293,11 @@ def main():
     P = I.stratified_3d(args.n)
     prec = {"mixed_df": fld.PREC_MIXED_DF, "mixed": fld.PREC_MIXED, "fp64": fld.PREC_FP64}[
         args.precision]
-    hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50,
-                    smoother=args.smoother)
+    tuned = tuned_opts("grid", [P]) if args.smoother == 0 else None
+    gkw = dict(nu1=2, nu2=2, smoother=args.smoother)
+    if tuned:
+        gkw = {k: tuned[k] for k in ("nu1", "nu2", "smoother")}
+    hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50, **gkw)
     consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
     op = fld.make_opacity(P.opacity)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -321,7 +396,7 @@ def main():
         hd.limiter(consts, op, E, rho, T, ebc, D)
         for name, pr in (("mixed_df", fld.PREC_MIXED_DF), ("mixed", fld.PREC_MIXED),
                          ("fp64", fld.PREC_FP64)):
-            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, smoother=args.smoother)
+            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, **gkw)
             times, cyc = [], 0
             for rep in range(4):
                 X = E.clone()
@@ -348,6 +423,8 @@ def main():
             "config": {"workload": "stratified3d_%d^3 (x,y periodic, z Dirichlet, Kramers opacity, "
                                    "dt = 10x explicit limit)" % args.n,
                        "cells": P.ncells, "precision": args.precision, "tol": 1e-10,
+                       "nu1": gkw["nu1"], "nu2": gkw["nu2"], "smoother": gkw["smoother"],
+                       "autotuned": bool(tuned),
                        "l2": "inputs larger than L2 (fields %.0f MB + workspace)" %
                              (3 * P.ncells * 8 / 1e6),
                        "parallelism": "replicas x%d" % world},

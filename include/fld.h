@@ -105,7 +105,11 @@ typedef struct {
                            periodic extent; others as 1); 1: two out-of-place half
                            sweeps; 2: the fused single-pass shared-memory sweep
                            (2D/3D, nx >= 8; others as 1)                               */
-    int reserved[3];
+    int graph;          /* batched step: capture the step in a CUDA graph on the first
+                           call with given field pointers and replay it afterwards      */
+    int cluster;        /* batched step: blocks per problem (1, 2, 4 or 8, a thread-block
+                           cluster when > 1); 0 = chosen from the largest problem      */
+    int reserved[1];
 } fld_opts;
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative
@@ -174,6 +178,46 @@ fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* o
 fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
                     const double* rho, double* T, double* E, const double* E_bc,
                     fld_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- batched substep
+   Many independent problems of uneven sizes advanced by one substep each in ONE
+   persistent kernel launch (the batched workload of the spec configuration):
+   every block takes the next problem from a queue ordered by decreasing cell count
+   and runs limiter -> multigrid solve -> exchange on it, so no block ever waits on
+   another. The solve is the MIXED_DF scheme (FP32 V-cycles inside double-FP32
+   iterative refinement) whatever o->precision says; o->block (256, 512 or 1024; 0 =
+   512) is the block size and o->cluster the number of blocks that share one problem
+   (a thread-block cluster synchronised by the hardware cluster barrier);
+   o->nu1/nu2/coarse_sweeps/tol/max_cycles/limiter apply.
+   Layout: the fields of all problems are concatenated in problem order (problem p
+   starts at the sum of the cell counts of problems 0..p-1), each in the layout of
+   fld_limiter; Dirichlet faces likewise concatenated problem after problem. */
+typedef struct fld_batch fld_batch;
+
+typedef struct {
+    int cycles;             /* refinement cycles used                               */
+    double rel_resid;       /* final ||b - A x|| / ||b|| (-1 after a domain error)   */
+    double rel_resid0;      /* the same before the first cycle                      */
+} fld_batch_stat;
+
+/* grids: host array of nprob grids (each as for fld_create, at most 2^27 cells).
+   Allocates the per-problem descriptors and workspace once. */
+fld_status fld_batch_create(fld_batch** b, int nprob, const fld_grid* grids, const fld_opts* o);
+fld_status fld_batch_destroy(fld_batch* b);
+fld_status fld_batch_set_opts(fld_batch* b, const fld_opts* o);
+/* Total number of cells of the batch (length of the concatenated fields). */
+long long fld_batch_cells(const fld_batch* b);
+
+/* One substep of every problem (Sect. 2/3 as for fld_step): k shared; ops[p] and dt[p]
+   (host arrays) per problem; rho, T, E, E_bc device arrays as described above.
+   With o->graph the launch sequence is captured into a CUDA graph on the first call
+   with these field pointers and replayed by later calls. stats (host, nprob entries)
+   may be NULL. Returns after the step has finished on `stream`: FLD_ERR_DOMAIN if a
+   problem held an invalid value (it is left unchanged), FLD_ERR_NOT_CONVERGED if a
+   problem missed tol within max_cycles (its E and T hold the last iterate's step). */
+fld_status fld_step_batched(fld_batch* b, const fld_consts* k, const fld_opacity* ops,
+                            const double* dt, const double* rho, double* T, double* E,
+                            const double* E_bc, fld_batch_stat* stats, void* stream);
 
 /* Synchronise `stream` and return (and clear) any device-side error flag. */
 fld_status fld_get_status(fld_handle* h, void* stream);

@@ -55,6 +55,45 @@ struct Prof {
 
 }  // namespace
 
+namespace fld {
+// Level pyramid of a grid: an axis with n >= 4 halves to ceil(n/2) (cell size reset to
+// L/n), until <= COARSE_TARGET cells remain or no axis can coarsen. Returns the number
+// of levels; kdown[l] rescales the averaged K of level l to level l+1's spacing.
+int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl) {
+    Lvl L{};
+    double H[3], len[3];
+    for (int d = 0; d < 3; ++d) {
+        L.n[d] = g.n[d];
+        L.bclo[d] = d < g.ndim ? g.bc_lo[d] : FLD_BC_PERIODIC;
+        L.bchi[d] = d < g.ndim ? g.bc_hi[d] : FLD_BC_PERIODIC;
+        H[d] = d < g.ndim ? g.h[d] : 1.0;
+        len[d] = H[d] * g.n[d];
+    }
+    L.ndim = g.ndim;
+    int nl = 0;
+    for (;;) {
+        L.ncell = (long long)L.n[0] * L.n[1] * L.n[2];
+        for (int d = 0; d < 3; ++d) {
+            L.w[d] = d < g.ndim ? (H[0] / H[d]) * (H[0] / H[d]) : 0.0;
+            L.wf[d] = (float)L.w[d];
+        }
+        lv[nl++] = L;
+        bool can = false;
+        for (int d = 0; d < g.ndim; ++d) can |= L.n[d] >= 4;
+        if (!can || L.ncell <= COARSE_TARGET || nl == maxl) break;
+        const double Hx_old = H[0];
+        for (int d = 0; d < g.ndim; ++d) {
+            if (L.n[d] >= 4) {
+                L.n[d] = (L.n[d] + 1) / 2;
+                H[d] = len[d] / L.n[d];
+            }
+        }
+        kdown[nl - 1] = (Hx_old / H[0]) * (Hx_old / H[0]);
+    }
+    return nl;
+}
+}  // namespace fld
+
 struct fld_handle {
     fld_grid g;
     fld_opts o;
@@ -90,7 +129,9 @@ fld_status cuda_fail(cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_fail(e_);          \
     } while (0)
 
-bool grid_ok(const fld_grid* g) {
+}  // namespace
+
+bool fld::grid_valid(const fld_grid* g) {
     if (!g || g->ndim < 1 || g->ndim > 3) return false;
     long long n = 1;
     for (int d = 0; d < 3; ++d) {
@@ -109,15 +150,27 @@ bool grid_ok(const fld_grid* g) {
     return n < (1LL << 31);
 }
 
-bool opts_ok(const fld_opts* o) {
+namespace {
+
+bool grid_ok(const fld_grid* g) { return fld::grid_valid(g); }
+
+bool opts_ok(const fld_opts* o) { return fld::opts_valid(o); }
+
+}  // namespace
+
+bool fld::opts_valid(const fld_opts* o) {
     return o && (o->precision == FLD_PREC_FP64 || o->precision == FLD_PREC_MIXED ||
                  o->precision == FLD_PREC_MIXED_DF) && o->tol > 0 &&
            o->max_cycles >= 1 && o->nu1 >= 0 && o->nu2 >= 0 && (o->nu1 + o->nu2) >= 1 &&
            o->coarse_sweeps >= 1 &&
            (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION) &&
            (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0)) &&
-           (o->smoother >= 0 && o->smoother <= 2);
+           (o->smoother >= 0 && o->smoother <= 2) &&
+           (o->cluster == 0 || o->cluster == 1 || o->cluster == 2 || o->cluster == 4 ||
+            o->cluster == 8);
 }
+
+namespace {
 
 Opacity to_op(const fld_opacity* op) {
     Opacity o;
@@ -145,40 +198,7 @@ bool has_dirichlet(const fld_grid& g) {
     return false;
 }
 
-void build_levels(fld_handle* h) {
-    const fld_grid& g = h->g;
-    Lvl L{};
-    double H[3], len[3];
-    for (int d = 0; d < 3; ++d) {
-        L.n[d] = g.n[d];
-        L.bclo[d] = d < g.ndim ? g.bc_lo[d] : FLD_BC_PERIODIC;
-        L.bchi[d] = d < g.ndim ? g.bc_hi[d] : FLD_BC_PERIODIC;
-        H[d] = d < g.ndim ? g.h[d] : 1.0;
-        len[d] = H[d] * g.n[d];
-    }
-    L.ndim = g.ndim;
-    int nl = 0;
-    for (;;) {
-        L.ncell = (long long)L.n[0] * L.n[1] * L.n[2];
-        for (int d = 0; d < 3; ++d) {
-            L.w[d] = d < g.ndim ? (H[0] / H[d]) * (H[0] / H[d]) : 0.0;
-            L.wf[d] = (float)L.w[d];
-        }
-        h->lv[nl++] = L;
-        bool can = false;
-        for (int d = 0; d < g.ndim; ++d) can |= L.n[d] >= 4;
-        if (!can || L.ncell <= COARSE_TARGET || nl == MAX_LEVELS) break;
-        const double Hx_old = H[0];
-        for (int d = 0; d < g.ndim; ++d) {
-            if (L.n[d] >= 4) {
-                L.n[d] = (L.n[d] + 1) / 2;
-                H[d] = len[d] / L.n[d];
-            }
-        }
-        h->kscale_down[nl - 1] = (Hx_old / H[0]) * (Hx_old / H[0]);
-    }
-    h->nlev = nl;
-}
+void build_levels(fld_handle* h) { h->nlev = fld::make_levels(h->g, h->lv, h->kscale_down, MAX_LEVELS); }
 
 template <typename T>
 fld_status dalloc(fld_handle* h, T** p, long long n) {
@@ -454,6 +474,9 @@ void fld_default_opts(fld_opts* o) {
     o->coarse_sweeps = 32;
     o->limiter = FLD_LIMITER_LP;
     o->block = 0;
+    o->smoother = 0;
+    o->graph = 1;
+    o->cluster = 0;
 }
 
 fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {

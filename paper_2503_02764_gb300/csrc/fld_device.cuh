@@ -1,0 +1,279 @@
+// Per-cell device routines shared by the grid kernels and the batched persistent
+// kernel: index decoding, the level operator's stencil, linear prolongation weights,
+// block reductions, limiter ghost values and the exchange root.
+#pragma once
+#include "fld_internal.cuh"
+
+namespace fld {
+
+__device__ __forceinline__ void decode(const Lvl& L, long long p, int& i, int& j, int& k) {
+    const int pp = (int)p;
+    i = pp % L.n[0];
+    const int q = pp / L.n[0];
+    j = q % L.n[1];
+    k = q / L.n[1];
+}
+
+// Off-diagonal sum and diagonal excess of the level operator at cell p:
+//   sw  = sum of face weights (+ 2 K_p w_d per Dirichlet face),  acc = sum w_f x_q,
+// so (A x)_p = (1 + sw) x_p - acc.
+template <typename T>
+__device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
+                                        const T* __restrict__ x, int i, int j, int k, long long p64,
+                                        T& sw, T& acc) {
+    // cell indices fit in 32 bits (the handle rejects grids of 2^31 cells or more)
+    const int p = (int)p64;
+    const T Kc = K[p];
+    const int c[3] = {i, j, k};
+    int stride = 1;
+    sw = T(0);
+    acc = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d < L.ndim) {
+            const int n = L.n[d];
+            const T wd = wgt<T>(L, d);
+            // low face
+            int q = -1;
+            if (c[d] > 0) q = p - stride;
+            else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
+            if (q >= 0) {
+                const T w = T(0.5) * (Kc + K[q]) * wd;
+                sw += w;
+                acc += w * x[q];
+            } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
+                sw += T(2) * Kc * wd;
+            }
+            // high face
+            q = -1;
+            if (c[d] < n - 1) q = p + stride;
+            else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
+            if (q >= 0) {
+                const T w = T(0.5) * (Kc + K[q]) * wd;
+                sw += w;
+                acc += w * x[q];
+            } else if (L.bchi[d] == FLD_BC_DIRICHLET) {
+                sw += T(2) * Kc * wd;
+            }
+            stride *= n;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T div_fast(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float div_fast<float>(float a, float b) { return __fdividef(a, b); }
+
+// Cell-centred linear prolongation: along a coarsened axis a fine cell takes 3/4 of
+// its parent I = i/2 and 1/4 of the coarse neighbour on its side (I-1 for an even i,
+// I+1 for an odd one); tensor product over the axes. A missing neighbour at a wall is
+// the mirror value: +e_I (Neumann, zero flux) or -e_I (Dirichlet, zero correction).
+struct Interp {
+    int idx[2];
+    float wt[2];
+};
+
+__device__ __forceinline__ Interp interp1(int i, int nf, int nc, int lo_bc, int hi_bc) {
+    Interp r;
+    if (nc == nf) {           // axis not coarsened
+        r.idx[0] = r.idx[1] = i;
+        r.wt[0] = 1.f;
+        r.wt[1] = 0.f;
+        return r;
+    }
+    const int I = i >> 1;
+    int J = (i & 1) ? I + 1 : I - 1;
+    float sgn = 1.f;
+    if (J < 0 || J >= nc) {
+        const int kind = (J < 0) ? lo_bc : hi_bc;
+        if (kind == FLD_BC_PERIODIC) J = (J + nc) % nc;
+        else {
+            sgn = (kind == FLD_BC_DIRICHLET) ? -1.f : 1.f;
+            J = I;
+        }
+    }
+    r.idx[0] = I;
+    r.idx[1] = J;
+    r.wt[0] = 0.75f;
+    r.wt[1] = 0.25f * sgn;
+    return r;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+
+struct BcOff {
+    long long off[6];   // offset of each Dirichlet face block in E_bc (-1: not Dirichlet)
+};
+
+__device__ __forceinline__ long long face_index(const Lvl& L, int d, int i, int j, int k) {
+    if (d == 0) return (long long)k * L.n[1] + j;
+    if (d == 1) return (long long)k * L.n[0] + i;
+    return (long long)j * L.n[0] + i;
+}
+
+__device__ __forceinline__ long long lin(const Lvl& L, int i, int j, int k) {
+    return ((long long)k * L.n[1] + j) * L.n[0] + i;
+}
+
+// E at offset o (|o| <= 2) from cell (i,j,k) along axis d, with ghost values:
+// periodic wrap, Neumann even mirror, Dirichlet odd reflection about the face value.
+__device__ __forceinline__ double fetch_E(const Lvl& L, const double* __restrict__ E,
+                                          const double* __restrict__ Ebc, const BcOff& bo,
+                                          int i, int j, int k, int d, int o) {
+    int c[3] = {i, j, k};
+    const int n = L.n[d];
+    int m = c[d] + o;
+    if (m >= 0 && m < n) {
+        c[d] = m;
+        return E[lin(L, c[0], c[1], c[2])];
+    }
+    int kind, side, mirror;
+    if (m < 0) {
+        kind = L.bclo[d];
+        side = 0;
+        mirror = -m - 1;            // E_{-k} pairs with E_{k-1}
+        if (kind == FLD_BC_PERIODIC) mirror = m + n;
+    } else {
+        kind = L.bchi[d];
+        side = 1;
+        mirror = 2 * n - 1 - m;     // E_{n-1+k} pairs with E_{n-k}
+        if (kind == FLD_BC_PERIODIC) mirror = m - n;
+    }
+    const long long fi = face_index(L, d, i, j, k);
+    c[d] = mirror;
+    const double v = E[lin(L, c[0], c[1], c[2])];
+    if (kind == FLD_BC_DIRICHLET) return 2.0 * Ebc[bo.off[2 * d + side] + fi] - v;
+    return v;
+}
+
+__device__ __forceinline__ bool f32_ok(double v) { return v > 1e-30 && v < 1e30; }
+
+__device__ __forceinline__ double exchange_root(double alpha, double beta, double q) {
+    const float af = (float)alpha, bf = (float)beta, qf = (float)q;
+    const float T1 = qf / af;                       // root if beta were 0
+    const float T1sq = T1 * T1;
+    const float g = (bf * T1sq) * (T1sq / qf);      // beta T1^4 / q
+    const bool fast = f32_ok(alpha) && f32_ok(q) && (beta == 0.0 || f32_ok(beta)) &&
+                      T1 > 1e-9f && T1 < 1e9f && g < 1e30f;
+    if (fast) {
+        float x = 1.f, scale = T1;
+        if (g <= 1.f) {
+            // phi(x) = g x^4 + x - 1, root in (0.72, 1]
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const float x2 = x * x;
+                x -= (fmaf(g * x2, x2, x) - 1.f) / fmaf(4.f * g * x2, x, 1.f);
+            }
+        } else {
+            // psi(y) = y^4 + h y - 1 with h = g^(-1/4), T = y T1 h, root in (0.8, 1]
+            const float hh = rsqrtf(sqrtf(g));
+            scale = T1 * hh;
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const float x2 = x * x;
+                x -= (fmaf(x2, x2, hh * x) - 1.f) / fmaf(4.f * x2, x, hh);
+            }
+        }
+        const double T = (double)x * (double)scale;
+        // one FP64 Newton step: FP64 residual, FP32 derivative
+        const double T2 = T * T;
+        const double f = fma(beta * T2, T2, fma(alpha, T, -q));
+        const float fpf = fmaf(4.f * bf * (float)T2, (float)T, af);
+        return fma(-f, (double)__frcp_rn(fpf), T);
+    }
+    // outside the FP32 range: plain FP64 Newton from the upper bound
+    double x = q / alpha;
+    if (beta > 0.0) x = fmin(x, sqrt(sqrt(q / beta)));
+    for (int it = 0; it < 60; ++it) {
+        const double x2 = x * x;
+        const double f = fma(beta * x2, x2, fma(alpha, x, -q));
+        const double dx = f / fma(4.0 * beta * x2, x, alpha);
+        x -= dx;
+        if (fabs(dx) <= 4e-16 * x) break;
+    }
+    return x;
+}
+
+// ----------------------------------------------------------------- limiter, one cell
+// R = |grad E| / (kappa rho E) (Eq. fld_R), lambda = (2 + R)/(6 + 3R + R^2)
+// (Eq. fld_lambda), D = c lambda / (kappa rho) (Eq. fld_F), grad E by the 5-point
+// 4th-order difference. With v = 1/(kappa rho E), D = c lambda E v: two reciprocals and
+// one square root, by FP32-seeded Newton-Raphson where the operands allow it (FP64
+// issues at a small fraction of the FP32 rate). Returns false on a domain error.
+__device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
+                                             const double* __restrict__ E,
+                                             const double* __restrict__ rho,
+                                             const double* __restrict__ T,
+                                             const double* __restrict__ Ebc, const BcOff& bo,
+                                             const Opacity& op, double c, int mode, int i, int j,
+                                             int k, long long p, double& Dout, double& lmout) {
+    const double Ec = E[p], r = rho[p];
+    const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
+    const double kap = opacity_eval(op, r, t);
+    if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t) && pos_finite(kap))) return false;
+    const double kr = kap * r;
+    double lm = 1.0 / 3.0;
+    if (mode == FLD_LIMITER_LP) {
+        double g2 = 0.0;
+        for (int d = 0; d < L.ndim; ++d) {
+            const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
+            const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
+            const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
+            const double ep2 = fetch_E(L, E, Ebc, bo, i, j, k, d, 2);
+            const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
+            g2 = fma(g, g, g2);
+        }
+        const double m = kr * Ec;
+        if (in_f32_range(m) && (g2 == 0.0 || in_f32_range(g2))) {
+            const double v = rcp_nr(m);
+            const double R = g2 > 0.0 ? g2 * rsqrt_nr(g2, 2) * v : 0.0;
+            const double P = 2.0 + R, Q = fma(R, R + 3.0, 6.0);
+            const double rQ = in_f32_range(Q) ? rcp_nr(Q) : 1.0 / Q;
+            lmout = P * rQ;
+            Dout = c * lmout * (Ec * v);
+            return true;
+        }
+        const double R = sqrt(g2) / m;
+        lm = (2.0 + R) / (6.0 + 3.0 * R + R * R);
+    }
+    lmout = lm;
+    Dout = in_f32_range(kr) ? c * lm * rcp_nr(kr) : c * lm / kr;
+    return true;
+}
+
+// ----------------------------------------------------------------- exchange, one cell
+// Backward Euler on de/dt = +qdot, dE/dt = -qdot (Eqs. heating, qdot) with kappa from
+// (rho, T on entry): solves alpha T' + beta T'^4 = q (exchange_root) and sets
+// E' = (E + chi a_r T'^4)/(1 + chi). Returns false (cell unchanged) on a domain error.
+__device__ __forceinline__ bool exchange_cell(double r, double& t, double& er, const Opacity& op,
+                                              double dtc, double a_r, double cv) {
+    if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) return false;
+    const double kap = opacity_eval(op, r, t);
+    if (!pos_finite(kap)) return false;
+    const double chi = dtc * kap * r;
+    const double alpha = r * cv;
+    const double d1 = 1.0 + chi;
+    const double inv1 = (d1 < 1e30) ? rcp_nr(d1) : 1.0 / d1;
+    const double w = chi * inv1;
+    const double beta = w * a_r;
+    const double q = fma(w, er, alpha * t);
+    const double x = exchange_root(alpha, beta, q);
+    const double x2 = x * x;
+    er = fma(chi * a_r, x2 * x2, er) * inv1;
+    t = x;
+    return true;
+}
+
+}  // namespace fld

@@ -8,7 +8,7 @@
 namespace fld {
 
 // Device error bits (OR-ed into the handle's status word).
-enum : unsigned { ERRBIT_DOMAIN = 1u, ERRBIT_TIMEOUT = 2u };
+enum : unsigned { ERRBIT_DOMAIN = 1u, ERRBIT_TIMEOUT = 2u, ERRBIT_NOTCONV = 4u };
 
 // One multigrid level of a uniform block. The operator at this level is
 //   (A x)_p = x_p + sum_faces 0.5 (K_p + K_q) w_d (x_p - x_q) + sum_dirichlet 2 K_p w_d x_p
@@ -90,6 +90,11 @@ __device__ __forceinline__ double opacity_eval(const Opacity& op, double rho, do
     }
     return op.kappa0 * fr * ft;
 }
+
+// ----------------------------------------------------------------- host helpers
+int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl);
+bool grid_valid(const fld_grid* g);
+bool opts_valid(const fld_opts* o);
 
 // ----------------------------------------------------------------- launchers
 // pointwise / limiter (k_pointwise.cu)

@@ -3,7 +3,7 @@
 // held as FP32 (hi, lo) pairs scaled by a power of two S (exact), so that the FP64-grade
 // residual r = b - A x costs FP32 instructions only and the kernel stays memory-bound.
 #include "df64.cuh"
-#include "fld_internal.cuh"
+#include "fld_device.cuh"
 
 namespace fld {
 
@@ -30,18 +30,6 @@ __global__ void k_df_finish(long long n, double invS, const float* __restrict__ 
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x)
         E[p] = ((double)xh[p] + (double)xl[p]) * invS;
-}
-
-__device__ __forceinline__ double block_sum_df(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-    if (wid == 0)
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // x_new = x + e (when e is given), written out of place; r = b - A x_new in df;
@@ -126,7 +114,7 @@ __global__ void k_df_resid(Lvl L, DfW wd, const float* __restrict__ xh, const fl
             acc2 = fma((double)res.hi, (double)res.hi, acc2);
         }
     }
-    acc2 = block_sum_df(acc2, sh);
+    acc2 = block_sum(acc2, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc2;
 }
 

@@ -9,7 +9,7 @@
 // Every kernel here is templated on the storage/arithmetic type (double or float).
 #include <algorithm>
 
-#include "fld_internal.cuh"
+#include "fld_device.cuh"
 
 namespace fld {
 
@@ -25,60 +25,6 @@ static inline int grid_for(long long n, int block, int cap = 152 * 32) {
 static inline int rows_grid(const Lvl& L, int cap = 152 * 64) {
     long long nr = (long long)L.n[1] * L.n[2];
     return (int)std::min<long long>(std::max<long long>(nr, 1), cap);
-}
-
-__device__ __forceinline__ void decode(const Lvl& L, long long p, int& i, int& j, int& k) {
-    const int pp = (int)p;
-    i = pp % L.n[0];
-    const int q = pp / L.n[0];
-    j = q % L.n[1];
-    k = q / L.n[1];
-}
-
-// Off-diagonal sum and diagonal excess of the level operator at cell p:
-//   sw  = sum of face weights (+ 2 K_p w_d per Dirichlet face),  acc = sum w_f x_q,
-// so (A x)_p = (1 + sw) x_p - acc.
-template <typename T>
-__device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
-                                        const T* __restrict__ x, int i, int j, int k, long long p64,
-                                        T& sw, T& acc) {
-    // cell indices fit in 32 bits (the handle rejects grids of 2^31 cells or more)
-    const int p = (int)p64;
-    const T Kc = K[p];
-    const int c[3] = {i, j, k};
-    int stride = 1;
-    sw = T(0);
-    acc = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d < L.ndim) {
-            const int n = L.n[d];
-            const T wd = wgt<T>(L, d);
-            // low face
-            int q = -1;
-            if (c[d] > 0) q = p - stride;
-            else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
-            if (q >= 0) {
-                const T w = T(0.5) * (Kc + K[q]) * wd;
-                sw += w;
-                acc += w * x[q];
-            } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
-                sw += T(2) * Kc * wd;
-            }
-            // high face
-            q = -1;
-            if (c[d] < n - 1) q = p + stride;
-            else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
-            if (q >= 0) {
-                const T w = T(0.5) * (Kc + K[q]) * wd;
-                sw += w;
-                acc += w * x[q];
-            } else if (L.bchi[d] == FLD_BC_DIRICHLET) {
-                sw += T(2) * Kc * wd;
-            }
-            stride *= n;
-        }
-    }
 }
 
 // ----------------------------------------------------------------- level-0 set-up
@@ -200,11 +146,6 @@ void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, c
 // Valid when no periodic axis has an odd extent (otherwise two same-colour cells
 // meet across the wrap and would race); the caller checks.
 template <typename T>
-__device__ __forceinline__ T div_fast(T a, T b) { return a / b; }
-template <>
-__device__ __forceinline__ float div_fast<float>(float a, float b) { return __fdividef(a, b); }
-
-template <typename T>
 __global__ void k_rb_half(Lvl L, int color, T* __restrict__ x, const T* __restrict__ b,
                           const T* __restrict__ K) {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
@@ -294,41 +235,6 @@ template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
                            int block, cudaStream_t s) {
     k_resid_restrict<T><<<grid_for(C.ncell, block), block, 0, s>>>(F, C, x, b, K, bc);
-}
-
-// Cell-centred linear prolongation: along a coarsened axis a fine cell takes 3/4 of
-// its parent I = i/2 and 1/4 of the coarse neighbour on its side (I-1 for an even i,
-// I+1 for an odd one); tensor product over the axes. A missing neighbour at a wall is
-// the mirror value: +e_I (Neumann, zero flux) or -e_I (Dirichlet, zero correction).
-struct Interp {
-    int idx[2];
-    float wt[2];
-};
-
-__device__ __forceinline__ Interp interp1(int i, int nf, int nc, int lo_bc, int hi_bc) {
-    Interp r;
-    if (nc == nf) {           // axis not coarsened
-        r.idx[0] = r.idx[1] = i;
-        r.wt[0] = 1.f;
-        r.wt[1] = 0.f;
-        return r;
-    }
-    const int I = i >> 1;
-    int J = (i & 1) ? I + 1 : I - 1;
-    float sgn = 1.f;
-    if (J < 0 || J >= nc) {
-        const int kind = (J < 0) ? lo_bc : hi_bc;
-        if (kind == FLD_BC_PERIODIC) J = (J + nc) % nc;
-        else {
-            sgn = (kind == FLD_BC_DIRICHLET) ? -1.f : 1.f;
-            J = I;
-        }
-    }
-    r.idx[0] = I;
-    r.idx[1] = J;
-    r.wt[0] = 0.75f;
-    r.wt[1] = 0.25f * sgn;
-    return r;
 }
 
 template <typename T>
@@ -466,20 +372,6 @@ void launch_coarse_solve(const Lvl& L, T* x, const T* b, const T* K, int sweeps,
 }
 
 // ----------------------------------------------------------------- FP64 residual + norms
-// r = b - A x in FP64; optional FP32 copy; per-block partial sums of r^2 (fixed
-// grid and fixed tree, so the sum is deterministic).
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-    if (wid == 0)
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // FP64 residual with the fewest FP64 operations per cell (FP64 issues at 1/58 of the
 // FP32 rate here): per face one sum of coefficients, one difference and one FMA,
 //   r = b - x - sum_d (w_d/2) sum_faces (K_p + K_q)(x_p - x_q) - sum_Dirichlet 2 w_d K_p x_p.

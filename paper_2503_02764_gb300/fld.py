@@ -41,7 +41,7 @@ class fld_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
                 ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("graph", C.c_int), ("cluster", C.c_int), ("reserved", C.c_int * 1)]
 
 
 class fld_stats(C.Structure):
@@ -52,6 +52,10 @@ class fld_stats(C.Structure):
 class fld_prof_entry(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("level", C.c_int), ("launches", C.c_longlong),
                 ("cells", C.c_longlong), ("ms", C.c_double)]
+
+
+class fld_batch_stat(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("rel_resid", C.c_double), ("rel_resid0", C.c_double)]
 
 
 _lib = None
@@ -85,6 +89,14 @@ def lib():
         "fld_prof_enable": (C.c_int, [H, C.c_int, C.c_int]),
         "fld_prof_read": (C.c_int, [H, C.POINTER(fld_prof_entry), C.c_int]),
         "fld_launch_count": (C.c_longlong, []),
+        "fld_batch_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(fld_grid),
+                                       C.POINTER(fld_opts)]),
+        "fld_batch_destroy": (C.c_int, [H]),
+        "fld_batch_set_opts": (C.c_int, [H, C.POINTER(fld_opts)]),
+        "fld_batch_cells": (C.c_longlong, [H]),
+        "fld_step_batched": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity),
+                                       C.POINTER(C.c_double), P, P, P, P, C.POINTER(fld_batch_stat),
+                                       P]),
         "fld_diffuse_static": (C.c_int, [C.POINTER(fld_grid), C.POINTER(fld_opts), C.c_double, P,
                                          P, P, C.POINTER(fld_stats), P]),
     }
@@ -139,12 +151,14 @@ def make_grid(shape, h, bc):
 
 
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
-              limiter=LIMITER_LP, block=0, smoother=0):
+              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
     o.nu1, o.nu2, o.coarse_sweeps, o.limiter, o.block = nu1, nu2, coarse_sweeps, limiter, block
     o.smoother = smoother
+    o.graph = graph
+    o.cluster = cluster
     return o
 
 
@@ -237,6 +251,71 @@ def fld_prof_read(h, cap=256):
 
 def fld_launch_count():
     return lib().fld_launch_count()
+
+
+def fld_batch_create(grids, opts):
+    h = H()
+    arr = (fld_grid * len(grids))(*grids)
+    _check(lib().fld_batch_create(C.byref(h), len(grids), arr, C.byref(opts)), "fld_batch_create")
+    return h
+
+
+def fld_batch_destroy(b):
+    _check(lib().fld_batch_destroy(b), "fld_batch_destroy")
+
+
+def fld_batch_set_opts(b, opts):
+    _check(lib().fld_batch_set_opts(b, C.byref(opts)), "fld_batch_set_opts")
+
+
+def fld_batch_cells(b):
+    return lib().fld_batch_cells(b)
+
+
+def fld_step_batched(b, nprob, consts, opacities, dts, rho, T, E, E_bc, stream=None,
+                     raise_on_error=True):
+    ops = (fld_opacity * nprob)(*opacities)
+    dta = (C.c_double * nprob)(*[float(v) for v in dts])
+    st = (fld_batch_stat * nprob)()
+    rc = lib().fld_step_batched(b, C.byref(consts), ops, dta, _ptr(rho), _ptr(T), _ptr(E),
+                                _ptr(E_bc), st, _stream(stream))
+    if raise_on_error:
+        _check(rc, "fld_step_batched")
+    return rc, [{"cycles": x.cycles, "rel_resid": x.rel_resid, "rel_resid0": x.rel_resid0}
+                for x in st]
+
+
+class Batch:
+    """Owns an fld_batch of independent grids; fields are concatenated in order."""
+
+    def __init__(self, grids, **opts):
+        self.grids = [make_grid(*g) for g in grids]
+        self.nprob = len(grids)
+        self.opts = make_opts(**opts)
+        self.b = fld_batch_create(self.grids, self.opts)
+
+    @property
+    def cells(self):
+        return fld_batch_cells(self.b)
+
+    def set_opts(self, **opts):
+        self.opts = make_opts(**opts)
+        fld_batch_set_opts(self.b, self.opts)
+
+    def step(self, consts, opacities, dts, rho, T, E, E_bc=None, stream=None, raise_on_error=True):
+        return fld_step_batched(self.b, self.nprob, consts, opacities, dts, rho, T, E, E_bc,
+                                stream, raise_on_error)
+
+    def close(self):
+        if self.b:
+            fld_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Handle:
