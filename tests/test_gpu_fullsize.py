@@ -1,0 +1,107 @@
+"""Checks at the workloads' full sizes, in the configuration bench.py times: properties
+that hold at any size, and outputs the oracle computes cell by cell on samples."""
+import numpy as np
+import pytest
+
+from oracle import fld as O
+from oracle import dispersion as Disp
+from paper_2503_02764_gb300 import inputs as I
+from gpu_util import torch_cuda, library, dev, host, handle_for, consts_of, ebc_dev, maxrel
+
+pytestmark = pytest.mark.gpu
+
+
+def test_stratified_256_full_size():
+    """Bench workload (256^3, MIXED_DF, tol 1e-10): limiter against the oracle on every
+    cell; the solve's true FP64 residual by the oracle's matrix-free operator; the exchange
+    on a sample of cells."""
+    torch = torch_cuda()
+    fld = library()
+    P = I.stratified_3d(256)
+    hd = handle_for(fld, P, precision=fld.PREC_MIXED_DF, tol=1e-10, max_cycles=50)
+    consts, op = consts_of(fld, P), fld.make_opacity(P.opacity)
+    rho, T, E, ebc = dev(torch, P.rho), dev(torch, P.T), dev(torch, P.E), ebc_dev(torch, P)
+    D = torch.empty_like(E)
+    hd.limiter(consts, op, E, rho, T, ebc, D)
+    Dg = host(D).reshape(P.shape)
+    Do, _, _ = O.limiter(P.E, P.rho, P.T, P.h, P.bc, P.E_bc, P.c, P.opacity)
+    assert np.max(np.abs(Dg / Do - 1)) < 1e-13
+    st = hd.diffuse(P.dt, D, ebc, E)
+    x = host(E).reshape(P.shape)
+    # b - A x with b = E^n + Dirichlet terms: A applied by the oracle's stencil sums
+    Ax = O.apply_operator(x, Do, P.h, P.bc, P.dt)
+    g = np.zeros(P.shape)
+    s = P.dt / P.h[2] ** 2
+    g[0] += 2 * s * Do[0] * P.E_bc[(2, 0)]
+    g[-1] += 2 * s * Do[-1] * P.E_bc[(2, 1)]
+    b = P.E + g
+    rel = np.linalg.norm((b - Ax).ravel()) / np.linalg.norm(b.ravel())
+    assert rel < 1.05e-10, (rel, st)
+    # exchange on the solved field, 40000 sampled cells against the oracle
+    Tg = T.clone()
+    hd.exchange(consts, op, P.dt, rho, Tg, E)
+    assert hd.status() == 0
+    rng = np.random.default_rng(0)
+    idx = rng.choice(P.ncells, 40000, replace=False)
+    To, Eo = O.exchange(P.rho.ravel()[idx], P.T.ravel()[idx], x.ravel()[idx], P.dt, P.c, P.a_r,
+                        P.gamma, P.R_gas, ("field", O.opacity(P.opacity, P.rho.ravel()[idx],
+                                                               P.T.ravel()[idx])))
+    assert np.max(np.abs(host(Tg).ravel()[idx] / To - 1)) < 1e-12
+    assert np.max(np.abs(host(E).ravel()[idx] / Eo - 1)) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (2, 1e-10)])
+def test_lognormal_1024_full_size_step(precision, tol):
+    """The 2D log-normal workload at its full 1024^2, one whole substep, every cell
+    against the oracle's substep (PCG to 1e-14)."""
+    torch = torch_cuda()
+    fld = library()
+    P = I.lognormal_2d(1024)
+    hd = handle_for(fld, P, precision=precision, tol=1e-13, max_cycles=80)
+    Td, Ed = dev(torch, P.T), dev(torch, P.E)
+    st = hd.step(consts_of(fld, P), fld.make_opacity(P.opacity), P.dt, dev(torch, P.rho), Td, Ed,
+                 None, raise_on_error=False)
+    assert st["status"] in (0, 3) and st["rel_resid"] < 1e-12, st
+    To, Eo, _ = O.step(P.rho, P.T, P.E, P.h, P.bc, P.E_bc, P.dt, P.c, P.a_r, P.gamma, P.R_gas,
+                       P.opacity, P.limiter, method="pcg")
+    assert maxrel(host(Ed).reshape(P.shape), Eo) < tol
+    assert maxrel(host(Td).reshape(P.shape), To) < tol
+
+
+@pytest.mark.parametrize("n,steps,ratio", [(32, 100, 1.0), (32, 100, 0.1), (512, 100, 1.0)])
+def test_linear_mode_decay(n, steps, ratio):
+    """The 3D linear-mode workload: the (e_1, E_1) amplitudes of the cos(2 pi x) mode after
+    `steps` substeps equal G^steps applied to the initial ones, G the exact per-step matrix
+    of the split substep (backward-Euler diffusion then exchange, lambda = 1/3 + O(R^2))."""
+    # amplitude 1e-4 (the workload's): second-order terms do not project on cos(2 pi x),
+    # so the linear prediction holds to O(amp^2) relative. The solve tolerance must be
+    # small against the perturbation (E_1/E_0 = 4e-4), hence tol 1e-12 with the FP64
+    # refinement residual.
+    torch = torch_cuda()
+    fld = library()
+    amp = 1e-4
+    P = I.linear_mode_3d(n, ratio=ratio, amp=amp, ny=4 if n < 512 else None,
+                         nz=4 if n < 512 else None, steps=steps)
+    hd = handle_for(fld, P, precision=fld.PREC_MIXED, tol=1e-12, max_cycles=60)
+    rho, T, E = dev(torch, P.rho), dev(torch, P.T), dev(torch, P.E)
+    x = (np.arange(n) + 0.5) / n
+    cosx = np.cos(2 * np.pi * x)
+
+    def modes(Tf, Ef):
+        # average over y, z, then project on cos(2 pi x)
+        e = (P.rho * P.R_gas * Tf / (P.gamma - 1)).reshape(P.shape).mean(axis=(0, 1))
+        Em = Ef.reshape(P.shape).mean(axis=(0, 1))
+        return np.array([2.0 / n * np.sum((e - e.mean()) * cosx),
+                         2.0 / n * np.sum((Em - Em.mean()) * cosx)])
+
+    v0 = modes(P.T, P.E)
+    consts, op = consts_of(fld, P), fld.make_opacity(P.opacity)
+    for _ in range(steps):
+        st = hd.step(consts, op, P.dt, rho, T, E, None, raise_on_error=False)
+        assert st["status"] == 0 or st["rel_resid"] < 1e-12, st
+    got = modes(host(T), host(E))
+    D = P.c / (3.0 * 1e4)
+    G = Disp.substep_amplification(P.dt, P.c, 1e4, 1.0, P.a_r, 1.0, P.gamma, P.R_gas, D,
+                                   Disp.discrete_k2(2 * np.pi, 1.0 / n))
+    want = np.linalg.matrix_power(G, steps) @ v0
+    assert np.all(np.abs(got - want) <= 1e-6 * np.abs(want).max()), (got, want)

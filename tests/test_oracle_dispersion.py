@@ -90,3 +90,21 @@ def test_hydro_frozen_block_close_to_full_modes():
         g = GOLD[case]
         rad = fr[np.argmin(fr.imag)]
         assert rad.imag == pytest.approx(g["radiative_diffusion"][1], rel=5e-4)
+
+
+@pytest.mark.parametrize("ratio", [0.1, 1.0])
+def test_substep_generator_is_hydro_frozen_block(ratio):
+    # The continuum generator behind the substep's amplification matrix,
+    # c kappa rho [[-beta, 1], [beta, -1]] - diag(0, D k^2), has the eigenvalues of the
+    # (p, E) block of the Appendix-B system (rho_1 = v_1 = B_1 = 0): the gas energy and
+    # pressure differ by the constant factor gamma - 1. Code units of the linear-mode
+    # workload: rho = T0 = R_gas = 1, c = kappa = 1e4, a_r = 3 x ratio.
+    a_r, c, kap, gam = 3.0 * ratio, 1e4, 1e4, 5.0 / 3.0
+    bg = dict(rho0=1.0, p0=1.0, B=np.zeros(3), gamma=gam, mu=1.0, kappa=kap, T0=1.0,
+              E0=a_r, k=2 * np.pi, c=c, a_r=a_r)
+    frozen = np.sort(Disp.hydro_frozen(bg).imag)
+    beta = 4 * a_r / (1.0 / (gam - 1))
+    D = c / (3 * kap)
+    J = c * kap * np.array([[-beta, 1.0], [beta, -1.0]]) - np.diag([0, D * (2 * np.pi) ** 2])
+    # the small rate is a difference of O(1e9) numbers: relative rounding ~1e-8
+    assert np.allclose(np.sort(np.linalg.eigvals(J).real), frozen, rtol=1e-7)
