@@ -150,6 +150,20 @@ def cpu_baseline(n=64):
                       "of the stratified recipe at %d^3 = %d cells, %.1f s" % (n, cells, secs)}
 
 
+def aggregate(ms_local, units_local, steps, dist=None, device="cpu"):
+    """Whole-job throughput over ranks: the slowest rank's time (MAX) and all ranks' units
+    (SUM). Returns (ms_max, units_total, value_per_second)."""
+    ms_max, units = float(ms_local), float(units_local)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        u = torch.tensor([units_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms_max, units = float(t.item()), float(u.item())
+    return ms_max, units, units * steps / (ms_max * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -200,10 +214,17 @@ def run_batch(args):
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2503_02764_gb300 import build, fld
     from paper_2503_02764_gb300 import inputs as I
     if rank == 0:
         build.build()
+    if dist is not None:
+        dist.barrier()
+    # each rank advances its own independent batch (weak scaling, no collective)
     ps = I.batch(args.nprob, seed_base=I.SEED_BASE + 4 + 100000 * rank)
     tuned = tuned_opts("batch", ps)
     kw = dict(block=args.block, cluster=args.cluster, nu1=2, nu2=2)
@@ -220,6 +241,8 @@ def run_batch(args):
     n0 = fld.fld_launch_count()
     stream = torch.cuda.current_stream()
     clk = Clocks(local)
+    if dist is not None:
+        dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -229,10 +252,13 @@ def run_batch(args):
         cyc.append(max(x["cycles"] for x in st))
     ev1.record(stream)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms_local = ev0.elapsed_time(ev1)
+    ms, cells_all, value = aggregate(ms_local, b.cells, args.steps, dist, "cuda")
     cells = b.cells
-    line = {"metric": METRIC + " [batched]", "value": cells * args.steps * world / (ms * 1e-3),
+    line = {"metric": METRIC + " [batched]", "value": value,
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -247,6 +273,8 @@ def run_batch(args):
             "gpu_launches": args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -329,12 +357,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = hd.prof_read()
     hd.prof_enable(False)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = P.ncells * args.steps * world / (ms_max * 1e-3)
+    ms_max, _, value = aggregate(ms, P.ncells, args.steps, dist, "cuda")
 
     # ---------------- roofline of the dominant level-0 kernel
     peak_hbm, peak_kind = load_peaks()
