@@ -57,6 +57,46 @@ __device__ __forceinline__ df df_mul(df x, df y) {
     return fast_two_sum(p.hi, p.lo);
 }
 
+__device__ __forceinline__ df df_mul_f(df x, float y) {
+    df p = two_prod(x.hi, y);
+    p.lo = __fmaf_rn(x.lo, y, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+// x / y: quotient estimate q1 = hi/hi, its df remainder x - q1 y, one correction term
+// (the long-division step of double-word arithmetic).
+__device__ __forceinline__ df df_div(df x, df y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const df r = df_sub(x, df_mul_f(y, q1));
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    return fast_two_sum(q1, q2);
+}
+
+// sqrt(x), x > 0: s = sqrt(hi), corrected by the df remainder (x - s^2)/(2 s) (Karp's
+// one-step refinement).
+__device__ __forceinline__ df df_sqrt(df x) {
+    const float s = __fsqrt_rn(x.hi);
+    const df r = df_sub(x, two_prod(s, s));
+    return fast_two_sum(s, __fdiv_rn(r.hi, 2.f * s));
+}
+
+// 1/sqrt(x), x > 0: FP32 seed, then two Newton-Raphson steps y + y (1 - x y^2)/2 in df
+// (the first leaves O(seed error^2) ~ 1e-13, the second the df rounding).
+__device__ __forceinline__ df df_rsqrt(df x) {
+    const float y0 = rsqrtf(x.hi);
+    const df e0 = df_sub({1.f, 0.f}, df_mul(x, two_prod(y0, y0)));
+    const df y1 = df_add_f(df_mul_f(e0, 0.5f * y0), y0);
+    const df e1 = df_sub({1.f, 0.f}, df_mul(x, df_mul(y1, y1)));
+    return df_add(y1, df_mul(df_mul_f(e1, 0.5f), y1));
+}
+
+// |x.hi| within [2^-80, 2^80]: comfortably inside the FP32 normal range, so the lo word
+// keeps its full precision through products of a few such values.
+__device__ __forceinline__ bool df_safe(float v) {
+    const float a = fabsf(v);
+    return a > 8.3e-25f && a < 1.2e24f;
+}
+
 // split an FP64 value into the nearest df (hi = RN(v), lo = RN(v - hi))
 __device__ __forceinline__ df df_from_double(double v) {
     const float h = __double2float_rn(v);

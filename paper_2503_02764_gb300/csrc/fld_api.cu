@@ -574,7 +574,7 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
     cudaStream_t s = (cudaStream_t)stream;
     run(h, "limiter", 0, h->ncell, s, [&] {
         launch_limiter(h->lv[0], h->g.h, E, rho, T, E_bc, h->bc_off, to_op(op), k->c, h->o.limiter,
-                       D, lambda, &h->scal->err, s);
+                       h->o.precision == FLD_PREC_MIXED_DF, D, lambda, &h->scal->err, s);
     });
     FLD_CK(cudaGetLastError());
     return FLD_OK;
@@ -593,7 +593,8 @@ fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* o
         return FLD_ERR_ARG;
     run(h, "exchange", 0, h->ncell, (cudaStream_t)stream, [&] {
         launch_exchange(h->ncell, rho, T, E, to_op(op), dt * k->c, k->a_r,
-                        k->R_gas / (k->gamma - 1.0), &h->scal->err, (cudaStream_t)stream);
+                        k->R_gas / (k->gamma - 1.0), h->o.precision == FLD_PREC_MIXED_DF,
+                        &h->scal->err, (cudaStream_t)stream);
     });
     FLD_CK(cudaGetLastError());
     return FLD_OK;

@@ -2,6 +2,7 @@
 // kernel: index decoding, the level operator's stencil, linear prolongation weights,
 // block reductions, limiter ghost values and the exchange root.
 #pragma once
+#include "df64.cuh"
 #include "fld_internal.cuh"
 
 namespace fld {
@@ -273,6 +274,131 @@ __device__ __forceinline__ bool exchange_cell(double r, double& t, double& er, c
     const double x2 = x * x;
     er = fma(chi * a_r, x2 * x2, er) * inv1;
     t = x;
+    return true;
+}
+
+// ----------------------------------------------------------------- double-FP32 variants
+// The same limiter and exchange with the FP64 work cut to the gradient and the format
+// conversions: every other operation runs as FP32 double-word arithmetic (df64.cuh).
+// They return false when a value leaves the window where that arithmetic keeps 48 bits
+// (the caller then uses the FP64 routines above).
+
+struct DfConst {        // per-launch constants as (hi, lo) pairs
+    float c_h, c_l, kap_h, kap_l, dtc_h, dtc_l, ar_h, ar_l, cv_h, cv_l;
+};
+
+// kappa as df: constant, or the Kramers-like law kappa0 rho T^-3.5; false otherwise
+__device__ __forceinline__ bool df_opacity(const Opacity& op, const DfConst& K, df rho, df T,
+                                           df& kap) {
+    const df k0 = {K.kap_h, K.kap_l};
+    if (op.kind == FLD_OPACITY_CONST) {
+        kap = k0;
+        return true;
+    }
+    if (op.a_rho != 1.0 || op.a_T != -3.5) return false;
+    const df y = df_rsqrt(T);                 // T^-1/2
+    const df y2 = df_mul(y, y);
+    const df y7 = df_mul(df_mul(df_mul(y2, y2), y2), y);
+    kap = df_mul(df_mul(k0, rho), y7);
+    return df_safe(kap.hi);
+}
+
+__device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
+                                                const double* __restrict__ E,
+                                                const double* __restrict__ rho,
+                                                const double* __restrict__ T,
+                                                const double* __restrict__ Ebc, const BcOff& bo,
+                                                const Opacity& op, const DfConst& K, int mode,
+                                                int i, int j, int k, long long p, double& Dout,
+                                                double& lmout) {
+    const double Ec = E[p], r = rho[p];
+    const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
+    if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t))) return false;
+    const df Ed = df_from_double(Ec), rd = df_from_double(r), td = df_from_double(t);
+    if (!(df_safe(Ed.hi) && df_safe(rd.hi) && df_safe(td.hi))) return false;
+    df kap;
+    if (!df_opacity(op, K, rd, td, kap)) return false;
+    const df kr = df_mul(kap, rd);
+    const df m = df_mul(kr, Ed);
+    if (!df_safe(m.hi)) return false;
+    df lm = {0.33333334f, -9.9341077e-09f};   // 1/3 as a double-FP32 pair
+    if (mode == FLD_LIMITER_LP) {
+        double g2 = 0.0;
+        for (int d = 0; d < L.ndim; ++d) {
+            const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
+            const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
+            const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
+            const double ep2 = fetch_E(L, E, Ebc, bo, i, j, k, d, 2);
+            const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
+            g2 = fma(g, g, g2);
+        }
+        if (g2 > 0.0) {
+            const df g2d = df_from_double(g2);
+            if (!df_safe(g2d.hi)) return false;
+            const df R = df_div(df_sqrt(g2d), m);
+            if (!(R.hi < 1e12f)) return false;
+            const df P = df_add_f(R, 2.f);
+            const df Q = df_add_f(df_mul(R, df_add_f(R, 3.f)), 6.f);
+            lm = df_div(P, Q);
+        }
+    }
+    const df D = df_div(df_mul({K.c_h, K.c_l}, lm), kr);
+    if (!df_safe(D.hi)) return false;
+    Dout = df_to_double(D);
+    lmout = df_to_double(lm);
+    return true;
+}
+
+__device__ __forceinline__ bool exchange_cell_df(double r, double& t, double& er,
+                                                 const Opacity& op, const DfConst& K) {
+    if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) return false;
+    const df rd = df_from_double(r), td = df_from_double(t), Ed = df_from_double(er);
+    if (!(df_safe(rd.hi) && df_safe(td.hi) && df_safe(Ed.hi))) return false;
+    df kap;
+    if (!df_opacity(op, K, rd, td, kap)) return false;
+    const df chi = df_mul(df_mul({K.dtc_h, K.dtc_l}, kap), rd);
+    if (!(chi.hi < 1e20f)) return false;
+    const df d1 = df_add_f(chi, 1.f);
+    const df w = df_div(chi, d1);                         // chi/(1+chi)
+    const df onemw = df_div({1.f, 0.f}, d1);              // 1/(1+chi)
+    const df alpha = df_mul(rd, {K.cv_h, K.cv_l});
+    const df beta = df_mul(w, {K.ar_h, K.ar_l});
+    const df q = df_add(df_mul(alpha, td), df_mul(w, Ed));
+    if (!(df_safe(alpha.hi) && df_safe(q.hi) && (beta.hi == 0.f || df_safe(beta.hi)))) return false;
+    // FP32 Newton on the scaled quartic (all quantities O(1)), as in exchange_root
+    const float T1 = q.hi / alpha.hi;
+    if (!(T1 > 1e-9f && T1 < 1e9f)) return false;
+    const float T1sq = T1 * T1;
+    const float g = (beta.hi * T1sq) * (T1sq / q.hi);
+    if (!(g < 1e30f)) return false;
+    float x = 1.f, scale = T1;
+    if (g <= 1.f) {
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const float x2 = x * x;
+            x -= (fmaf(g * x2, x2, x) - 1.f) / fmaf(4.f * g * x2, x, 1.f);
+        }
+    } else {
+        const float hh = rsqrtf(sqrtf(g));
+        scale = T1 * hh;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const float x2 = x * x;
+            x -= (fmaf(x2, x2, hh * x) - 1.f) / fmaf(4.f * x2, x, hh);
+        }
+    }
+    // one df Newton step on f(T) = beta T^4 + alpha T - q, derivative in FP32
+    df Tn = two_prod(x, scale);
+    const df T2 = df_mul(Tn, Tn);
+    const df f = df_sub(df_add(df_mul(beta, df_mul(T2, T2)), df_mul(alpha, Tn)), q);
+    const float fp = fmaf(4.f * beta.hi * T2.hi, Tn.hi, alpha.hi);
+    Tn = df_add_f(Tn, -__fdiv_rn(f.hi, fp));
+    // E' = E/(1+chi) + beta T'^4  (= (E + chi a_r T'^4)/(1+chi))
+    const df T2n = df_mul(Tn, Tn);
+    const df En = df_add(df_mul(Ed, onemw), df_mul(beta, df_mul(T2n, T2n)));
+    if (!(df_safe(Tn.hi) && df_safe(En.hi))) return false;
+    t = df_to_double(Tn);
+    er = df_to_double(En);
     return true;
 }
 

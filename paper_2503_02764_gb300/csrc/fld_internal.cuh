@@ -91,6 +91,12 @@ __device__ __forceinline__ double opacity_eval(const Opacity& op, double rho, do
     return op.kappa0 * fr * ft;
 }
 
+// (hi, lo) FP32 pair nearest to a double, on the host
+inline void split_host(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
 // ----------------------------------------------------------------- host helpers
 int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl);
 bool grid_valid(const fld_grid* g);
@@ -99,10 +105,11 @@ bool opts_valid(const fld_opts* o);
 // ----------------------------------------------------------------- launchers
 // pointwise / limiter (k_pointwise.cu)
 void launch_exchange(long long n, const double* rho, double* T, double* E, Opacity op,
-                     double dtc, double a_r, double cv, unsigned* err, cudaStream_t s);
+                     double dtc, double a_r, double cv, int use_df, unsigned* err, cudaStream_t s);
 void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
-                    double c, int mode, double* D, double* lam, unsigned* err, cudaStream_t s);
+                    double c, int mode, int use_df, double* D, double* lam, unsigned* err,
+                    cudaStream_t s);
 
 // multigrid (k_mg.cu)
 void launch_prep_level0(const Lvl& L, double kscale, const double* D, const double* E,

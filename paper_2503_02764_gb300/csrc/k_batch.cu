@@ -373,13 +373,23 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
         for (int q = 0; q < 6; ++q) bo.off[q] = P.bc_off[q];
         const double ih[3] = {1.0 / (12.0 * P.h[0]), 1.0 / (12.0 * P.h[1]), 1.0 / (12.0 * P.h[2])};
 
+        // per-problem constants as double-FP32 pairs
+        DfConst KC;
+        {
+            const df c2 = df_from_double(prm.c), k2 = df_from_double(op.kappa0),
+                     t2 = df_from_double(dt * prm.c), a2 = df_from_double(prm.a_r),
+                     v2 = df_from_double(prm.cv);
+            KC = {c2.hi, c2.lo, k2.hi, k2.lo, t2.hi, t2.lo, a2.hi, a2.lo, v2.hi, v2.lo};
+        }
         // ---- limiter -> D; count domain errors
         double bad = 0.0;
         for (int p = g.tid; p < n0; p += g.nthr) {
             int i, j, k;
             decode(L0, p, i, j, k);
             double Dv = 0.0, lm;
-            if (!limiter_cell(L0, ih, E_, r_, T_, eb, bo, op, prm.c, prm.limiter, i, j, k, p, Dv, lm))
+            if (!limiter_cell_df(L0, ih, E_, r_, T_, eb, bo, op, KC, prm.limiter, i, j, k, p, Dv,
+                                 lm) &&
+                !limiter_cell(L0, ih, E_, r_, T_, eb, bo, op, prm.c, prm.limiter, i, j, k, p, Dv, lm))
                 bad += 1.0;
             D[p] = Dv;
         }
@@ -463,9 +473,13 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
             const double invS = 1.0 / S;
             const double dtc = dt * prm.c;
             for (int p = g.tid; p < n0; p += g.nthr) {
-                double t = T_[p];
-                double e_new = ((double)xh[p] + (double)xl[p]) * invS;
-                exchange_cell(r_[p], t, e_new, op, dtc, prm.a_r, prm.cv);
+                const double e_sol = ((double)xh[p] + (double)xl[p]) * invS;
+                double t = T_[p], e_new = e_sol;
+                if (!exchange_cell_df(r_[p], t, e_new, op, KC)) {
+                    t = T_[p];
+                    e_new = e_sol;
+                    exchange_cell(r_[p], t, e_new, op, dtc, prm.a_r, prm.cv);
+                }
                 T_[p] = t;
                 E_[p] = e_new;
             }

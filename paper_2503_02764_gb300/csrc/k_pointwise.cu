@@ -23,10 +23,17 @@ namespace fld {
 
 __global__ void k_exchange(long long n, const double* __restrict__ rho, double* __restrict__ T,
                            double* __restrict__ E, Opacity op, double dtc, double a_r, double cv,
-                           unsigned* err) {
+                           int use_df, DfConst K, unsigned* err) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double t = T[i], er = E[i];
+        if (use_df && exchange_cell_df(rho[i], t, er, op, K)) {
+            T[i] = t;
+            E[i] = er;
+            continue;
+        }
+        t = T[i];
+        er = E[i];
         if (!exchange_cell(rho[i], t, er, op, dtc, a_r, cv)) {
             atomicOr(err, ERRBIT_DOMAIN);
             continue;
@@ -36,21 +43,32 @@ __global__ void k_exchange(long long n, const double* __restrict__ rho, double* 
     }
 }
 
+DfConst make_dfconst(double c, double kappa0, double dtc, double a_r, double cv) {
+    DfConst K;
+    split_host(c, K.c_h, K.c_l);
+    split_host(kappa0, K.kap_h, K.kap_l);
+    split_host(dtc, K.dtc_h, K.dtc_l);
+    split_host(a_r, K.ar_h, K.ar_l);
+    split_host(cv, K.cv_h, K.cv_l);
+    return K;
+}
+
 void launch_exchange(long long n, const double* rho, double* T, double* E, Opacity op,
-                     double dtc, double a_r, double cv, unsigned* err, cudaStream_t s) {
+                     double dtc, double a_r, double cv, int use_df, unsigned* err, cudaStream_t s) {
     if (n <= 0) return;
     const int block = 256;
     long long nb = (n + block - 1) / block;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, op, dtc, a_r, cv, err);
+    const DfConst K = make_dfconst(0.0, op.kappa0, dtc, a_r, cv);
+    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, op, dtc, a_r, cv, use_df, K, err);
 }
 
 // ----------------------------------------------------------------- limiter
 __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           const double* __restrict__ rho, const double* __restrict__ T,
                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
-                          int mode, double* __restrict__ D, double* __restrict__ lam,
-                          unsigned* err) {
+                          int mode, int use_df, DfConst K, double* __restrict__ D,
+                          double* __restrict__ lam, unsigned* err) {
     const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
     const int nrows = L.n[1] * L.n[2];
     for (int rw = blockIdx.x; rw < nrows; rw += gridDim.x)
@@ -58,6 +76,11 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
             const int j = rw % L.n[1], k = rw / L.n[1];
             const long long p = (long long)rw * L.n[0] + i;
             double Dv, lm;
+            if (use_df && limiter_cell_df(L, ih, E, rho, T, Ebc, bo, op, K, mode, i, j, k, p, Dv, lm)) {
+                D[p] = Dv;
+                if (lam) lam[p] = lm;
+                continue;
+            }
             if (!limiter_cell(L, ih, E, rho, T, Ebc, bo, op, c, mode, i, j, k, p, Dv, lm)) {
                 atomicOr(err, ERRBIT_DOMAIN);
                 continue;
@@ -69,14 +92,16 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
 
 void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
-                    double c, int mode, double* D, double* lam, unsigned* err, cudaStream_t s) {
+                    double c, int mode, int use_df, double* D, double* lam, unsigned* err,
+                    cudaStream_t s) {
     BcOff bo;
     for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
     double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
                               L.ndim > 2 ? 1.0 / (12.0 * h[2]) : 0.0);
     const int block = 256;
     const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
-    k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, D, lam, err);
+    const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
+    k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, D, lam, err);
 }
 
 }  // namespace fld

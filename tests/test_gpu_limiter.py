@@ -33,14 +33,16 @@ def _fields(shape, bc, seed):
     return E, rho, T, Eb
 
 
+@pytest.mark.parametrize("precision", [0, 2])
 @pytest.mark.parametrize("shape,h,bc", CASES)
 @pytest.mark.parametrize("op", [(0, 2.0, 0.0, 0.0), (1, 5.0, 1.0, -3.5)])
-def test_limiter_matches_oracle(shape, h, bc, op):
+def test_limiter_matches_oracle(shape, h, bc, op, precision):
+    # precision 2 (MIXED_DF) runs the double-FP32 limiter, the others the FP64 one
     torch = torch_cuda()
     fld = library()
     E, rho, T, Eb = _fields(shape, bc, len(shape) * 100 + shape[-1])
     for mode in (0, 1):
-        hd = fld.Handle(shape, h, bc, limiter=mode)
+        hd = fld.Handle(shape, h, bc, limiter=mode, precision=precision)
         D = torch.empty(E.size, dtype=torch.float64, device="cuda")
         lam = torch.empty_like(D)
         packed = I.pack_dirichlet(shape, bc, Eb)
@@ -48,20 +50,23 @@ def test_limiter_matches_oracle(shape, h, bc, op):
                    dev(torch, rho), dev(torch, T), dev(torch, packed) if packed.size else None, D, lam)
         assert hd.status() == 0
         Do, lo, _ = O.limiter(E, rho, T, h, bc, Eb, 3.0, op, mode)
-        assert np.max(np.abs(host(D).reshape(shape) / Do - 1)) < 1e-13
-        assert np.max(np.abs(host(lam).reshape(shape) / lo - 1)) < 1e-13
+        # FP64: rounding-level; double-FP32 (48-bit): a few units of 2^-48
+        tol = 1e-13 if precision == 0 else 1e-12
+        assert np.max(np.abs(host(D).reshape(shape) / Do - 1)) < tol
+        assert np.max(np.abs(host(lam).reshape(shape) / lo - 1)) < tol
 
 
-def test_limiter_workload_fields():
+@pytest.mark.parametrize("precision", [0, 2])
+def test_limiter_workload_fields(precision):
     torch = torch_cuda()
     fld = library()
     for P in (I.make_config(1), I.make_config(2, small=True), I.make_config(3, small=True)):
-        hd = handle_for(fld, P)
+        hd = handle_for(fld, P, precision=precision)
         D = torch.empty(P.ncells, dtype=torch.float64, device="cuda")
         hd.limiter(consts_of(fld, P), fld.make_opacity(P.opacity), dev(torch, P.E), dev(torch, P.rho),
                    dev(torch, P.T), ebc_dev(torch, P), D)
         Do, _, _ = O.limiter(P.E, P.rho, P.T, P.h, P.bc, P.E_bc, P.c, P.opacity)
-        assert np.max(np.abs(host(D).reshape(P.shape) / Do - 1)) < 1e-13
+        assert np.max(np.abs(host(D).reshape(P.shape) / Do - 1)) < (1e-13 if precision == 0 else 1e-12)
 
 
 def test_limiter_rejects_nonpositive_E():
