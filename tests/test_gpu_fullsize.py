@@ -25,7 +25,7 @@ def test_stratified_256_full_size():
     hd.limiter(consts, op, E, rho, T, ebc, D)
     Dg = host(D).reshape(P.shape)
     Do, _, _ = O.limiter(P.E, P.rho, P.T, P.h, P.bc, P.E_bc, P.c, P.opacity)
-    assert np.max(np.abs(Dg / Do - 1)) < 1e-13
+    assert np.max(np.abs(Dg / Do - 1)) < 1e-12      # double-FP32 limiter (MIXED_DF)
     st = hd.diffuse(P.dt, D, ebc, E)
     x = host(E).reshape(P.shape)
     # b - A x with b = E^n + Dirichlet terms: A applied by the oracle's stencil sums
