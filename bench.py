@@ -230,6 +230,7 @@ def run_batch(args):
     kw = dict(block=args.block, cluster=args.cluster, nu1=2, nu2=2)
     if tuned and not (args.block or args.cluster):
         kw = {k: tuned[k] for k in ("block", "cluster", "nu1", "nu2")}
+        kw["inner"] = tuned.get("inner", 1)
     b = fld.Batch([(p.shape, p.h, p.bc) for p in ps], tol=1e-10, max_cycles=50, graph=1, **kw)
     cat = lambda xs: torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
     rho, T, E = cat([p.rho for p in ps]), cat([p.T for p in ps]), cat([p.E for p in ps])
@@ -268,6 +269,7 @@ def run_batch(args):
                                    "launch per step, CUDA graph" % args.nprob,
                        "cells": cells, "block": kw["block"] or 512,
                        "cluster": kw["cluster"] or "auto", "nu1": kw["nu1"], "nu2": kw["nu2"],
+                       "inner": kw.get("inner", 1),
                        "autotuned": bool(tuned and not (args.block or args.cluster))},
             "max_cycles_per_step": cyc, "clocks": clocks,
             "gpu_launches": args.steps}
@@ -325,6 +327,7 @@ def main():
     gkw = dict(nu1=2, nu2=2, smoother=args.smoother)
     if tuned:
         gkw = {k: tuned[k] for k in ("nu1", "nu2", "smoother")}
+        gkw["inner"] = tuned.get("inner", 1)
     hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50, **gkw)
     consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
     op = fld.make_opacity(P.opacity)
@@ -337,8 +340,7 @@ def main():
     for _ in range(args.warmup):
         stats = hd.step(consts, op, P.dt, rho, T, E, ebc)
 
-    # ---------------- timed region (device-resident inputs)
-    hd.prof_enable(True, 65536)
+    # ---------------- timed region (device-resident inputs, graphs on, no profiling)
     n0 = fld.fld_launch_count()
     clk = Clocks(local)
     barrier()
@@ -355,9 +357,22 @@ def main():
     clocks = clk.stop()
     launches = fld.fld_launch_count() - n0
     ms = ev0.elapsed_time(ev1)
+    ms_max, _, value = aggregate(ms, P.ncells, args.steps, dist, "cuda")
+
+    # ---------------- the same steps again with every launch bracketed by events: the
+    # per-kernel durations for the roofline and the breakdown (graphs are off while
+    # profiling, so this pass is slightly slower than the one above)
+    hd.prof_enable(True, 65536)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        hd.step(consts, op, P.dt, rho, T, E, ebc)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = e2.elapsed_time(e3)
     prof = hd.prof_read()
     hd.prof_enable(False)
-    ms_max, _, value = aggregate(ms, P.ncells, args.steps, dist, "cuda")
 
     # ---------------- roofline of the dominant level-0 kernel
     peak_hbm, peak_kind = load_peaks()
@@ -447,11 +462,13 @@ def main():
                                    "dt = 10x explicit limit)" % args.n,
                        "cells": P.ncells, "precision": args.precision, "tol": 1e-10,
                        "nu1": gkw["nu1"], "nu2": gkw["nu2"], "smoother": gkw["smoother"],
+                       "inner": gkw.get("inner", 1),
                        "autotuned": bool(tuned),
                        "l2": "inputs larger than L2 (fields %.0f MB + workspace)" %
                              (3 * P.ncells * 8 / 1e6),
                        "parallelism": "replicas x%d" % world},
             "gpu_launches": launches, "cycles_per_step": cycles,
+            "profiled_pass_ms_per_step": ms_prof / args.steps,
             "roofline": roof, "kernel_breakdown": breakdown,
             "time_to_1e-10_ms": ttt, "clocks": clocks, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -109,7 +109,8 @@ typedef struct {
                            call with given field pointers and replay it afterwards      */
     int cluster;        /* batched step: blocks per problem (1, 2, 4 or 8, a thread-block
                            cluster when > 1); 0 = chosen from the largest problem      */
-    int reserved[1];
+    int inner;          /* MIXED/MIXED_DF: FP32 V-cycles per refinement step (the later
+                           ones continue from the previous correction); 0 means 1      */
 } fld_opts;
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative

@@ -1,7 +1,8 @@
 """Autotuner for the launch shapes and smoother sweep counts of the FLD solver.
 
 For the batched substep it times (threads per block, blocks per problem cluster,
-pre/post smoothing sweeps); for a single grid (pre/post sweeps, smoother kind). Each
+pre/post smoothing sweeps, FP32 V-cycles per refinement step); for a single grid
+(pre/post sweeps, smoother kind, V-cycles per refinement step). Each
 candidate runs the real substep on a copy of the caller's fields; a candidate counts
 only if every problem reaches the tolerance. The fastest is cached in a JSON file keyed
 by the GPU name and a signature of the workload (shapes, boundary kinds), so later runs
@@ -90,22 +91,23 @@ def _time_batch(fld, torch, problems, opts, reps=3):
 
 
 def tune_batch(problems, blocks=(256, 512, 1024), clusters=(1, 2, 4, 8),
-               sweeps=((2, 2), (1, 1), (2, 1), (3, 3)), tol=1e-10, store=True):
-    """Time every (block, cluster, nu1, nu2) candidate on the batch; return the best."""
+               sweeps=((2, 2), (1, 1), (2, 1), (3, 3)), inners=(1, 2), tol=1e-10, store=True):
+    """Time every (block, cluster, nu1, nu2, inner) candidate on the batch; return the best."""
     import torch
     from . import fld
     results = []
     for nb in blocks:
         for cl in clusters:
             for nu1, nu2 in sweeps:
-                opts = dict(tol=tol, max_cycles=60, block=nb, cluster=cl, nu1=nu1, nu2=nu2,
-                            graph=0)
-                try:
-                    t, ok = _time_batch(fld, torch, problems, opts)
-                except fld.FldError:
-                    continue
-                results.append({"block": nb, "cluster": cl, "nu1": nu1, "nu2": nu2,
-                                "seconds": t, "converged": ok})
+                for inner in inners:
+                    opts = dict(tol=tol, max_cycles=60, block=nb, cluster=cl, nu1=nu1, nu2=nu2,
+                                inner=inner, graph=0)
+                    try:
+                        t, ok = _time_batch(fld, torch, problems, opts)
+                    except fld.FldError:
+                        continue
+                    results.append({"block": nb, "cluster": cl, "nu1": nu1, "nu2": nu2,
+                                    "inner": inner, "seconds": t, "converged": ok})
     good = [r for r in results if r["converged"]]
     best = min(good, key=lambda r: r["seconds"]) if good else None
     if store and best:
@@ -117,8 +119,8 @@ def tune_batch(problems, blocks=(256, 512, 1024), clusters=(1, 2, 4, 8),
 
 
 def tune_grid(problem, precision=2, sweeps=((2, 2), (1, 1), (2, 1), (1, 2), (3, 3)),
-              smoothers=(0, 2), tol=1e-10, store=True, reps=3):
-    """Time (nu1, nu2, smoother) for one grid's full substep; return the best."""
+              smoothers=(0, 2), inners=(1, 2, 3), tol=1e-10, store=True, reps=3):
+    """Time (nu1, nu2, smoother, inner) for one grid's full substep; return the best."""
     import numpy as np
     import torch
     from . import fld
@@ -132,20 +134,21 @@ def tune_grid(problem, precision=2, sweeps=((2, 2), (1, 1), (2, 1), (1, 2), (3, 
     op = fld.make_opacity(P.opacity)
     results = []
     hd = fld.Handle(P.shape, P.h, P.bc, precision=precision, tol=tol)
-    for sm in smoothers:
-        for nu1, nu2 in sweeps:
-            hd.set_opts(precision=precision, tol=tol, max_cycles=60, nu1=nu1, nu2=nu2, smoother=sm)
-            best, ok = float("inf"), True
-            for _ in range(reps + 1):
-                T, E = T0.clone(), E0.clone()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                st = hd.step(consts, op, P.dt, rho, T, E, ebc, raise_on_error=False)
-                torch.cuda.synchronize()
-                best = min(best, time.perf_counter() - t0)
-                ok = ok and st["status"] == 0
-            results.append({"nu1": nu1, "nu2": nu2, "smoother": sm, "seconds": best,
-                            "converged": ok, "cycles": st["cycles"]})
+    candidates = [(sm, inner, nu) for sm in smoothers for inner in inners for nu in sweeps]
+    for sm, inner, (nu1, nu2) in candidates:
+        hd.set_opts(precision=precision, tol=tol, max_cycles=60, nu1=nu1, nu2=nu2, smoother=sm,
+                    inner=inner)
+        best, ok = float("inf"), True
+        for _ in range(reps + 1):
+            T, E = T0.clone(), E0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = hd.step(consts, op, P.dt, rho, T, E, ebc, raise_on_error=False)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+            ok = ok and st["status"] == 0
+        results.append({"nu1": nu1, "nu2": nu2, "smoother": sm, "inner": inner,
+                        "seconds": best, "converged": ok, "cycles": st["cycles"]})
     hd.close()
     good = [r for r in results if r["converged"]]
     best = min(good, key=lambda r: r["seconds"]) if good else None

@@ -113,6 +113,12 @@ struct fld_handle {
     DevScalars* hscal = nullptr;      // pinned host
     std::vector<void*> allocs;
     Prof prof;
+    // CUDA graph of the FP32 V-cycle (handle-owned buffers only), replayed per cycle
+    cudaStream_t gs = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    cudaGraphExec_t vgraph = nullptr;
+    int vgraph_key[6] = {0, 0, 0, 0, 0, 0};
+    long long vgraph_nodes = 0;
 };
 
 namespace {
@@ -167,7 +173,8 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0)) &&
            (o->smoother >= 0 && o->smoother <= 2) &&
            (o->cluster == 0 || o->cluster == 1 || o->cluster == 2 || o->cluster == 4 ||
-            o->cluster == 8);
+            o->cluster == 8) &&
+           (o->inner >= 0 && o->inner <= 8);
 }
 
 namespace {
@@ -329,6 +336,62 @@ fld_status residual(fld_handle* h, double* x, float* r32, cudaStream_t s, double
     return read_scalars(h, s, rr, err);
 }
 
+void graph_free(fld_handle* h) {
+    if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
+    if (h->gev_in) cudaEventDestroy(h->gev_in);
+    if (h->gev_out) cudaEventDestroy(h->gev_out);
+    if (h->gs) cudaStreamDestroy(h->gs);
+    h->vgraph = nullptr;
+    h->gev_in = h->gev_out = nullptr;
+    h->gs = nullptr;
+}
+
+// e32 = 0, then `inner` FP32 V-cycles on level 0 (each later one continues from the
+// correction so far: its restriction sees the FP32 residual r32 - A e32). With graphs on (and profiling off) the
+// sequence is captured once per option set on a handle-owned stream and replayed;
+// the caller's stream and that stream are ordered through events.
+fld_status vcycle32(fld_handle* h, cudaStream_t s) {
+    const long long n0 = h->lv[0].ncell;
+    const int inner = h->o.inner > 0 ? h->o.inner : 1;
+    if (!h->o.graph || h->prof.on) {
+        FLD_CK(cudaMemsetAsync(h->d32[0].x, 0, sizeof(float) * n0, s));
+        for (int c = 0; c < inner; ++c) vcycle<float>(h, h->d32, 0, s);
+        return FLD_OK;
+    }
+    const int key[6] = {h->o.nu1, h->o.nu2, h->o.smoother, h->o.block, h->o.coarse_sweeps, inner};
+    if (!h->gs) {
+        FLD_CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+        FLD_CK(cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+        FLD_CK(cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+    }
+    if (!h->vgraph || memcmp(key, h->vgraph_key, sizeof(key)) != 0) {
+        if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
+        h->vgraph = nullptr;
+        cudaGraph_t g = nullptr;
+        const long long before = g_launches.load();
+        FLD_CK(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(h->d32[0].x, 0, sizeof(float) * n0, h->gs);
+        for (int c = 0; c < inner; ++c) vcycle<float>(h, h->d32, 0, h->gs);
+        FLD_CK(cudaStreamEndCapture(h->gs, &g));
+        h->vgraph_nodes = g_launches.load() - before;
+        g_launches.fetch_sub(h->vgraph_nodes);       // counted per replay below
+        cudaError_t e = cudaGraphInstantiate(&h->vgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->vgraph = nullptr;
+            return cuda_fail(e);
+        }
+        memcpy(h->vgraph_key, key, sizeof(key));
+    }
+    FLD_CK(cudaEventRecord(h->gev_in, s));
+    FLD_CK(cudaStreamWaitEvent(h->gs, h->gev_in, 0));
+    FLD_CK(cudaGraphLaunch(h->vgraph, h->gs));
+    g_launches.fetch_add(h->vgraph_nodes);
+    FLD_CK(cudaEventRecord(h->gev_out, h->gs));
+    FLD_CK(cudaStreamWaitEvent(s, h->gev_out, 0));
+    return FLD_OK;
+}
+
 // Mixed refinement with the residual and the correction in double-FP32: the scaled
 // iterate S x, S b and K live as (hi, lo) FP32 pairs for the duration of the solve;
 // E is read at the start and written at the end.
@@ -377,8 +440,8 @@ fld_status diffuse_df(fld_handle* h, double* E, double bsum, fld_stats* st, cuda
     }
     int cyc = 0;
     while (rel > h->o.tol && cyc < h->o.max_cycles && std::isfinite(rel)) {
-        FLD_CK(cudaMemsetAsync(h->d32[0].x, 0, sizeof(float) * n, s));
-        vcycle<float>(h, h->d32, 0, s);
+        rc = vcycle32(h, s);
+        if (rc != FLD_OK) return rc;
         rc = resid(h->d32[0].x, &r2);
         if (rc != FLD_OK) return rc;
         rel = std::sqrt(r2) / bnorm;
@@ -437,8 +500,8 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     int cyc = 0;
     while (rel > h->o.tol && cyc < h->o.max_cycles && std::isfinite(rel)) {
         if (mixed) {
-            FLD_CK(cudaMemsetAsync(h->d32[0].x, 0, sizeof(float) * L0.ncell, s));
-            vcycle<float>(h, h->d32, 0, s);
+            rc = vcycle32(h, s);
+            if (rc != FLD_OK) return rc;
             run(h, "add_correction", 0, L0.ncell, s,
                 [&] { launch_add_correction(L0.ncell, E, h->d32[0].x, s); });
             rc = residual(h, E, h->d32[0].b, s, &r2, &err);
@@ -477,6 +540,7 @@ void fld_default_opts(fld_opts* o) {
     o->smoother = 0;
     o->graph = 1;
     o->cluster = 0;
+    o->inner = 1;
 }
 
 fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
@@ -552,6 +616,7 @@ fld_status fld_destroy(fld_handle* h) {
     if (!h) return FLD_OK;
     cudaDeviceSynchronize();
     prof_free(h);
+    graph_free(h);
     free_all(h);
     delete h;
     return FLD_OK;
@@ -736,6 +801,7 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
     fld_handle& h = g_static_handle;
     h.g = *g;
     h.o = *o;
+    h.o.graph = 0;        // graph capture and instantiation allocate: launch directly
     build_levels(&h);
     h.ncell = h.lv[0].ncell;
     long long off = 0;

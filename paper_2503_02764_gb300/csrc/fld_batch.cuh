@@ -30,7 +30,7 @@ struct BDyn {
 struct BatchParams {
     double c, a_r, cv;      // speed of light, radiation constant, R_gas/(gamma - 1)
     double tol;
-    int max_cycles, nu1, nu2, coarse_sweeps, limiter;
+    int max_cycles, nu1, nu2, coarse_sweeps, limiter, inner;
 };
 
 struct BatchStat {

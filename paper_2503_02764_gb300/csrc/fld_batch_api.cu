@@ -234,6 +234,7 @@ fld_status fld_step_batched(fld_batch* b, const fld_consts* k, const fld_opacity
     prm.nu2 = b->o.nu2;
     prm.coarse_sweeps = b->o.coarse_sweeps;
     prm.limiter = b->o.limiter;
+    prm.inner = b->o.inner > 0 ? b->o.inner : 1;
     const int nt = block_threads(b->o);
     const int cl = cluster_size(b, nt);
     const int maxg = batch_max_groups(nt, cl);

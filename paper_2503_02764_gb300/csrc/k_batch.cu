@@ -459,7 +459,8 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
             while (rel > prm.tol && cyc < prm.max_cycles && isfinite(rel)) {
                 for (int p = g.tid; p < n0; p += g.nthr) x32[p] = 0.f;
                 g.sync();
-                grp_vcycle(g, P, F, prm.nu1, prm.nu2, prm.coarse_sweeps, sh);
+                for (int ic = 0; ic < prm.inner; ++ic)
+                    grp_vcycle(g, P, F, prm.nu1, prm.nu2, prm.coarse_sweeps, sh);
                 for (int p = g.tid; p < n0; p += g.nthr) {
                     const df v = df_add_f({xh[p], xl[p]}, x32[p]);
                     xh[p] = v.hi;

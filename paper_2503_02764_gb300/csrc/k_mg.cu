@@ -145,13 +145,11 @@ void launch_smooth(const Lvl& L, int color, const T* xin, T* xout, const T* b, c
 // a row (j, k) per block row, so the index arithmetic is a few integer operations.
 // Valid when no periodic axis has an odd extent (otherwise two same-colour cells
 // meet across the wrap and would race); the caller checks.
+// One colour-`color` cell (i, j, k) of an in-place half sweep.
 template <typename T>
-__global__ void k_rb_half(Lvl L, int color, T* __restrict__ x, const T* __restrict__ b,
-                          const T* __restrict__ K) {
+__device__ __forceinline__ void rb_cell(const Lvl& L, int i, int j, int k, T* __restrict__ x,
+                                        const T* __restrict__ b, const T* __restrict__ K) {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int j = blockIdx.y, k = blockIdx.z;
-    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
-    if (i >= nx) return;
     const int sy = nx, sz = nx * ny;
     const int p = (k * ny + j) * nx + i;
     const T kc = K[p];
@@ -184,6 +182,24 @@ __global__ void k_rb_half(Lvl L, int color, T* __restrict__ x, const T* __restri
     x[p] = div_fast<T>(b[p] + acc, T(1) + sw);
 }
 
+// In-place red-black half sweep: only cells of `color` are updated, from neighbours
+// of the other colour. One thread per pair of cells along x (the one of `color`) on
+// ZU planes spaced nz/ZU apart (independent cells in flight per thread), a row (j, k)
+// per block row, so the index arithmetic is a few integer operations. Valid when no
+// periodic axis has an odd extent (two same-colour cells would meet across the wrap and
+// race); the caller checks.
+template <typename T>
+__global__ void k_rb_half(Lvl L, int color, T* __restrict__ x, const T* __restrict__ b,
+                          const T* __restrict__ K) {
+    // block = (pairs along x) x (rows along y): neighbouring rows of a tile share L1
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (j >= L.n[1]) return;
+    const int i = 2 * ip + ((j + k + color) & 1);
+    if (i < L.n[0]) rb_cell<T>(L, i, j, k, x, b, K);
+}
+
 template <typename T>
 bool rb_half_supported(const Lvl& L) {
     for (int d = 0; d < L.ndim; ++d)
@@ -194,9 +210,12 @@ bool rb_half_supported(const Lvl& L) {
 template <typename T>
 void launch_rb_half(const Lvl& L, int color, T* x, const T* b, const T* K, cudaStream_t s) {
     const int pairs = (L.n[0] + 1) / 2;
-    const int bs = pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32;
-    dim3 grid((pairs + bs - 1) / bs, L.n[1], L.n[2]);
-    k_rb_half<T><<<grid, bs, 0, s>>>(L, color, x, b, K);
+    // x-y tiles of 32 pairs x 8 rows on wide levels, one row of up to 128 pairs otherwise
+    const int bx = pairs >= 32 ? 32 : ((pairs + 7) / 8) * 8;
+    const int by = pairs >= 32 ? 8 : 1;
+    dim3 block(pairs >= 32 ? bx : (pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32), by);
+    dim3 grid((pairs + block.x - 1) / block.x, (L.n[1] + by - 1) / by, L.n[2]);
+    k_rb_half<T><<<grid, block, 0, s>>>(L, color, x, b, K);
 }
 
 // Coarse right-hand side = average of the fine residuals b - A x over the children.

@@ -41,7 +41,7 @@ class fld_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
                 ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
-                ("graph", C.c_int), ("cluster", C.c_int), ("reserved", C.c_int * 1)]
+                ("graph", C.c_int), ("cluster", C.c_int), ("inner", C.c_int)]
 
 
 class fld_stats(C.Structure):
@@ -151,7 +151,7 @@ def make_grid(shape, h, bc):
 
 
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
-              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0):
+              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
@@ -159,6 +159,7 @@ def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coars
     o.smoother = smoother
     o.graph = graph
     o.cluster = cluster
+    o.inner = inner
     return o
 
 
