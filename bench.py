@@ -43,8 +43,10 @@ BYTES_PER_CELL = {
     "sumsq": 8.0,             # b read
     "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
     "resid_df": 40.0,         # x (hi, lo), e32, b (hi, lo), K (hi, lo) read; x (hi, lo), r32 written
-    "rbhalf32": 16.0,         # x, K, b read; x written (one colour per launch, whole lines)
-    "rbhalf64": 32.0,
+    "rbhalf32": 10.0,         # one colour: the other colour's x and every K read (faces),
+    "rbhalf64": 20.0,         #   this colour's b read and x written
+    "rbsweep32": 16.0,        # x, K, b read; x written (both colours in one pass)
+    "rbsweep64": 32.0,
     "add_correction": 20.0,   # x, e32 read; x written
     "smooth32": 16.0,         # xin, b, K read; xout written
     "smooth64": 32.0,
@@ -52,7 +54,7 @@ BYTES_PER_CELL = {
     "resid_restrict64": 24.0,
     "prolong32": 8.0,
     "prolong64": 16.0,
-    "exchange": 48.0,         # rho, T, E read; T, E written; T re-read for kappa counted once
+    "exchange": 40.0,         # rho, T, E read; T, E written (kappa evaluated from rho, T)
 }
 
 
@@ -298,7 +300,13 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--smoother", type=int, default=0, help="0 in-place half sweeps, 1 out-of-place half sweeps, 2 fused single-pass sweep")
+    ap.add_argument("--smoother", type=int, default=-1,
+                    help="-1 the tuned choice (else 0); 0 in-place half sweeps, 1 out-of-place "
+                         "half sweeps, 2 single-pass z-marching sweep")
+    ap.add_argument("--nu1", type=int, default=-1, help="pre-smoothing sweeps (-1: tuned)")
+    ap.add_argument("--nu2", type=int, default=-1, help="post-smoothing sweeps (-1: tuned)")
+    ap.add_argument("--inner", type=int, default=-1,
+                    help="FP32 V-cycles per refinement step (-1: tuned)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the mixed-vs-FP64 solve timing")
     ap.add_argument("--workload", default="stratified", choices=["stratified", "batch"],
                     help="stratified: one 3D box (default); batch: 512 uneven 2D problems")
@@ -332,11 +340,15 @@ def main():
     P = I.stratified_3d(args.n)
     prec = {"mixed_df": fld.PREC_MIXED_DF, "mixed": fld.PREC_MIXED, "fp64": fld.PREC_FP64}[
         args.precision]
-    tuned = tuned_opts("grid", [P]) if args.smoother == 0 else None
-    gkw = dict(nu1=2, nu2=2, smoother=args.smoother)
+    tuned = tuned_opts("grid", [P])
+    gkw = dict(nu1=2, nu2=2, smoother=0, inner=1)
     if tuned:
         gkw = {k: tuned[k] for k in ("nu1", "nu2", "smoother")}
         gkw["inner"] = tuned.get("inner", 1)
+    for k in ("smoother", "nu1", "nu2", "inner"):     # explicit choices override the tuner
+        if getattr(args, k) >= 0:
+            gkw[k] = getattr(args, k)
+            tuned = None
     hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50, **gkw)
     consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
     op = fld.make_opacity(P.opacity)

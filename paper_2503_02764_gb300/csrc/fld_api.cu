@@ -253,34 +253,35 @@ void prof_free(fld_handle* h) {
     h->prof.on = false;
 }
 
-// -------------------------------------------------- smoothing: `n` red-black sweeps,
-// the iterate in B.x before and after. Pairs of sweeps use the fused single-pass
-// kernel (x -> tmp -> x); an odd last sweep (or a level the fused kernel does not
-// cover) uses two half-sweep launches (x -> tmp -> x).
+// -------------------------------------------------- smoothing: `n` red-black sweeps of
+// the iterate in `cur` (B.x or B.tmp; `oth` is the other buffer). The first `fused` of
+// them use the single-pass out-of-place kernel, each moving the iterate to the other
+// buffer (the two pointers swap). The rest run in place: two half-sweep launches, or,
+// where those do not apply (odd periodic extents) or smoother 1 asks for it, the
+// out-of-place half-sweep pair cur -> oth -> cur.
 template <typename T>
-void smooth(fld_handle* h, LevelBufs<T>& B, int l, int n, cudaStream_t s) {
+void smooth(fld_handle* h, LevelBufs<T>& B, int l, int n, int fused, T*& cur, T*& oth,
+            cudaStream_t s) {
     const Lvl& L = h->lv[l];
     const bool f32 = sizeof(T) == 4;
     const int bs = blk(h);
-    int left = n;
-    if (h->o.smoother == 0 && rb_half_supported<T>(L)) {
+    for (int i = 0; i < fused; ++i) {
+        run(h, f32 ? "rbsweep32" : "rbsweep64", l, L.ncell, s,
+            [&] { launch_rb_sweep<T>(L, cur, oth, B.b, B.K, s); });
+        std::swap(cur, oth);
+    }
+    int left = n - fused;
+    if (h->o.smoother != 1 && rb_half_supported<T>(L)) {
         const char* nm = f32 ? "rbhalf32" : "rbhalf64";
         for (; left > 0; --left) {
-            run(h, nm, l, L.ncell, s, [&] { launch_rb_half<T>(L, 0, B.x, B.b, B.K, s); });
-            run(h, nm, l, L.ncell, s, [&] { launch_rb_half<T>(L, 1, B.x, B.b, B.K, s); });
-        }
-    }
-    if (h->o.smoother == 2 && rb_sweep_supported<T>(L)) {
-        const char* nm = f32 ? "rbsweep32" : "rbsweep64";
-        for (; left >= 2; left -= 2) {
-            run(h, nm, l, L.ncell, s, [&] { launch_rb_sweep<T>(L, B.x, B.tmp, B.b, B.K, s); });
-            run(h, nm, l, L.ncell, s, [&] { launch_rb_sweep<T>(L, B.tmp, B.x, B.b, B.K, s); });
+            run(h, nm, l, L.ncell, s, [&] { launch_rb_half<T>(L, 0, cur, B.b, B.K, s); });
+            run(h, nm, l, L.ncell, s, [&] { launch_rb_half<T>(L, 1, cur, B.b, B.K, s); });
         }
     }
     const char* sm = f32 ? "smooth32" : "smooth64";
     for (; left > 0; --left) {
-        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, B.x, B.tmp, B.b, B.K, bs, s); });
-        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, B.tmp, B.x, B.b, B.K, bs, s); });
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 0, cur, oth, B.b, B.K, bs, s); });
+        run(h, sm, l, L.ncell, s, [&] { launch_smooth<T>(L, 1, oth, cur, B.b, B.K, bs, s); });
     }
 }
 
@@ -296,15 +297,26 @@ void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
         return;
     }
     const int bs = blk(h);
-    smooth<T>(h, B, l, h->o.nu1, s);
+    // fused sweeps swap the buffers, so an even number of them brings the iterate back
+    // to B.x; with an odd nu1 + nu2 the last sweep of the cycle runs in place
+    const int nu1 = h->o.nu1, nu2 = h->o.nu2;
+    int f1 = 0, f2 = 0;
+    if (h->o.smoother == 2 && rb_sweep_supported<T>(L)) {
+        f1 = nu1;
+        f2 = nu2;
+        if ((nu1 + nu2) & 1) (nu2 > 0 ? f2 : f1) -= 1;
+    }
+    T* cur = B.x;
+    T* oth = B.tmp;
+    smooth<T>(h, B, l, nu1, f1, cur, oth, s);
     const Lvl& C = h->lv[l + 1];
     run(h, f32 ? "resid_restrict32" : "resid_restrict64", l, L.ncell, s,
-        [&] { launch_resid_restrict<T>(L, C, B.x, B.b, B.K, P[l + 1].b, bs, s); });
+        [&] { launch_resid_restrict<T>(L, C, cur, B.b, B.K, P[l + 1].b, bs, s); });
     if (l + 1 < h->nlev - 1) cudaMemsetAsync(P[l + 1].x, 0, sizeof(T) * C.ncell, s);
     vcycle<T>(h, P, l + 1, s);
     run(h, f32 ? "prolong32" : "prolong64", l, L.ncell, s,
-        [&] { launch_prolong<T>(L, C, B.x, P[l + 1].x, bs, s); });
-    smooth<T>(h, B, l, h->o.nu2, s);
+        [&] { launch_prolong<T>(L, C, cur, P[l + 1].x, bs, s); });
+    smooth<T>(h, B, l, nu2, f2, cur, oth, s);
 }
 
 template <typename T>
@@ -602,6 +614,7 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
         rc = FLD_ERR_NOMEM;
     }
     if (!rc && cudaMemset(h->scal, 0, sizeof(DevScalars)) != cudaSuccess) rc = FLD_ERR_CUDA;
+    if (!rc) prepare_rb_sweep();
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = FLD_ERR_CUDA;
     if (rc) {
         free_all(h);
@@ -802,6 +815,7 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
     h.g = *g;
     h.o = *o;
     h.o.graph = 0;        // graph capture and instantiation allocate: launch directly
+    prepare_rb_sweep();   // kernel attributes only (no device memory)
     build_levels(&h);
     h.ncell = h.lv[0].ncell;
     long long off = 0;

@@ -131,6 +131,7 @@ template <typename T>
 bool rb_sweep_supported(const Lvl& L);
 template <typename T>
 void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K, cudaStream_t s);
+void prepare_rb_sweep();
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K,
                            T* bc, int block, cudaStream_t s);
