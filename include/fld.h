@@ -175,14 +175,16 @@ fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* o
 
 /* The whole substep: limiter -> diffuse -> exchange, the opacity frozen at
    (rho, T^n) for all three. The handle's scratch holds D. Returns after the
-   step has finished on `stream`. */
+   step has finished on `stream`. A solve that stops at max_cycles still
+   completes the substep from its last iterate and the call returns
+   FLD_ERR_NOT_CONVERGED; any other error returns before the exchange. */
 fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
                     const double* rho, double* T, double* E, const double* E_bc,
                     fld_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------- batched substep
    Many independent problems of uneven sizes advanced by one substep each in ONE
-   persistent kernel launch (the batched workload of the spec configuration):
+   persistent kernel launch (512 uneven 2D problems is the intended scale):
    every block takes the next problem from a queue ordered by decreasing cell count
    and runs limiter -> multigrid solve -> exchange on it, so no block ever waits on
    another. The solve is the MIXED_DF scheme (FP32 V-cycles inside double-FP32

@@ -119,8 +119,12 @@ def tune_batch(problems, blocks=(256, 512, 1024), clusters=(1, 2, 4, 8),
 
 
 def tune_grid(problem, precision=2, sweeps=((2, 2), (1, 1), (2, 1), (1, 2), (3, 3)),
-              smoothers=(0, 2), inners=(1, 2, 3), tol=1e-10, store=True, reps=3):
-    """Time (nu1, nu2, smoother, inner) for one grid's full substep; return the best."""
+              smoothers=(0, 2), inners=(1, 2, 3), tol=1e-10, store=True, reps=3, presteps=3):
+    """Time (nu1, nu2, smoother, inner) for one grid's full substep; return the best.
+
+    The fields are first advanced `presteps` substeps with the default options, so the
+    candidates are timed on the state a running simulation meets after its first steps
+    (the very first substep of the synthetic initial state needs more cycles)."""
     import numpy as np
     import torch
     from . import fld
@@ -134,6 +138,8 @@ def tune_grid(problem, precision=2, sweeps=((2, 2), (1, 1), (2, 1), (1, 2), (3, 
     op = fld.make_opacity(P.opacity)
     results = []
     hd = fld.Handle(P.shape, P.h, P.bc, precision=precision, tol=tol)
+    for _ in range(presteps):
+        hd.step(consts, op, P.dt, rho, T0, E0, ebc)
     candidates = [(sm, inner, nu) for sm in smoothers for inner in inners for nu in sweeps]
     for sm, inner, (nu1, nu2) in candidates:
         hd.set_opts(precision=precision, tol=tol, max_cycles=60, nu1=nu1, nu2=nu2, smoother=sm,

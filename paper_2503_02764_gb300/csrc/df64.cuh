@@ -63,6 +63,30 @@ __device__ __forceinline__ df df_mul_f(df x, float y) {
     return fast_two_sum(p.hi, p.lo);
 }
 
+// Unnormalised double-word forms for short sums of products: the hi words combine
+// exactly (two_sum / two_prod) and the lo words accumulate without the renormalising
+// fast_two_sum, each step adding O(2^-24 |lo|) to the error. A few of them in a row keep
+// the result within a few units of 2^-47 of the operands' magnitude, at about half the
+// instructions of the renormalised forms; only the final value is rounded.
+__device__ __forceinline__ df dw_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return s;
+}
+
+__device__ __forceinline__ df dw_sub(df x, df y) {
+    df s = two_sum(x.hi, -y.hi);
+    s.lo = __fadd_rn(s.lo, __fsub_rn(x.lo, y.lo));
+    return s;
+}
+
+// x * y without the lo * lo term
+__device__ __forceinline__ df dw_mul(df x, df y) {
+    df p = two_prod(x.hi, y.hi);
+    p.lo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+    return p;
+}
+
 // x / y: quotient estimate q1 = hi/hi, its df remainder x - q1 y, one correction term
 // (the long-division step of double-word arithmetic).
 __device__ __forceinline__ df df_div(df x, df y) {

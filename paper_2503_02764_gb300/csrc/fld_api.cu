@@ -687,11 +687,14 @@ fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, d
     cudaStream_t s = (cudaStream_t)stream;
     fld_status rc = fld_limiter(h, k, op, E, rho, T, E_bc, h->Dscratch, nullptr, stream);
     if (rc) return rc;
-    rc = diffuse_impl(h, dt, h->Dscratch, E_bc, E, stats, s);
-    if (rc) return rc;
+    // a solve that stopped at max_cycles still completes the substep from its last iterate
+    // (the status reports it); any other failure stops here
+    const fld_status rs = diffuse_impl(h, dt, h->Dscratch, E_bc, E, stats, s);
+    if (rs != FLD_OK && rs != FLD_ERR_NOT_CONVERGED) return rs;
     rc = fld_exchange(h, k, op, dt, rho, T, E, stream);
     if (rc) return rc;
-    return fld_get_status(h, stream);
+    rc = fld_get_status(h, stream);
+    return rc ? rc : rs;
 }
 
 fld_status fld_get_status(fld_handle* h, void* stream) {

@@ -132,6 +132,13 @@ bool rb_sweep_supported(const Lvl& L);
 template <typename T>
 void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K, cudaStream_t s);
 void prepare_rb_sweep();
+// 3D transfers when every axis halves exactly (one thread per coarse cell).
+bool transfer3_ok(const Lvl& F, const Lvl& C);
+template <typename T>
+void launch_resid_restrict3(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
+                            cudaStream_t s);
+template <typename T>
+void launch_prolong3(const Lvl& F, const Lvl& C, T* xf, const T* xc, cudaStream_t s);
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K,
                            T* bc, int block, cudaStream_t s);

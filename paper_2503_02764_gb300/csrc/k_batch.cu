@@ -282,7 +282,9 @@ __device__ void grp_vcycle(const Grp<CS>& g, const BProb& P, float* F, int nu1, 
     }
 }
 
-// Level-0 residual in double-FP32: r = b - A x, r32 = hi(r); returns the group's sum r^2.
+// Level-0 residual in double-FP32: r = b - A x (renormalised face factors, unnormalised
+// double-word products and sums: a few units of 2^-48 of |x| and |K x|), r32 = r rounded
+// to FP32; returns the group's sum of r^2.
 template <int CS>
 __device__ double grp_df_resid(const Grp<CS>& g, const Lvl& L, const DfW& wd, const float* xh,
                                const float* xl, const float* bh, const float* bl, const float* Kh,
@@ -293,7 +295,7 @@ __device__ double grp_df_resid(const Grp<CS>& g, const Lvl& L, const DfW& wd, co
         decode(L, p, i, j, k);
         const df xc = {xh[p], xl[p]};
         const df kc = {Kh[p], Kl[p]};
-        df res = df_sub({bh[p], bl[p]}, xc);
+        df res = dw_sub({bh[p], bl[p]}, xc);
         const int c[3] = {i, j, k};
         int stride = 1;
         df dw = {0.f, 0.f};
@@ -313,17 +315,18 @@ __device__ double grp_df_resid(const Grp<CS>& g, const Lvl& L, const DfW& wd, co
                 if (q >= 0) {
                     const df kq = {Kh[q], Kl[q]};
                     const df xq = {xh[q], xl[q]};
-                    ax = df_add(ax, df_mul(df_add(kc, kq), df_sub(xc, xq)));
+                    ax = dw_add(ax, dw_mul(df_add(kc, kq), df_sub(xc, xq)));
                 } else if (kind == FLD_BC_DIRICHLET) {
                     dw = df_add(dw, df_mul({wd.hh[d], wd.hl[d]}, {4.f, 0.f}));
                 }
             }
-            res = df_sub(res, df_mul({wd.hh[d], wd.hl[d]}, ax));
+            res = dw_sub(res, dw_mul({wd.hh[d], wd.hl[d]}, ax));
             stride *= nd;
         }
-        if (dw.hi != 0.f) res = df_sub(res, df_mul(df_mul(dw, kc), xc));
-        r32[p] = res.hi;
-        a2 = fma((double)res.hi, (double)res.hi, a2);
+        if (dw.hi != 0.f) res = dw_sub(res, df_mul(df_mul(dw, kc), xc));
+        const float r = __fadd_rn(res.hi, res.lo);
+        r32[p] = r;
+        a2 = fma((double)r, (double)r, a2);
     }
     g.sync();
     return grp_sum(a2, sh, g);

@@ -32,8 +32,16 @@ __global__ void k_df_finish(long long n, double invS, const float* __restrict__ 
         E[p] = ((double)xh[p] + (double)xl[p]) * invS;
 }
 
-// x_new = x + e (when e is given), written out of place; r = b - A x_new in df;
-// r32 = hi(r); per-block partial sums of r^2.
+// x_new = x + e (when e is given), written out of place; r = b - A x_new in double-FP32;
+// r32 = r rounded to FP32; per-block partial sums of r^2.
+//
+// A x_new = x_new + sum_d (w_d/2) sum_faces (K_p + K_q)(x_p - x_q): per face the sum
+// K_p + K_q and the difference x_p - x_q in renormalised double-FP32, their product and
+// the accumulation in the unnormalised double-word forms (no renormalisation between
+// them); the error stays a few units of 2^-48 of |x| and |K x|, far below the refinement
+// tolerance. x_new of the cell itself is renormalised (it is stored); the neighbours'
+// x + e are formed as the exact sum of the hi words and e plus the lo word. The squares
+// are summed in FP32 per thread (a norm needs no more) and in FP64 across the block.
 __global__ void k_df_resid(Lvl L, DfW wd, const float* __restrict__ xh, const float* __restrict__ xl,
                            const float* __restrict__ e, const float* __restrict__ bh,
                            const float* __restrict__ bl, const float* __restrict__ Kh,
@@ -41,13 +49,15 @@ __global__ void k_df_resid(Lvl L, DfW wd, const float* __restrict__ xh, const fl
                            float* __restrict__ ol, float* __restrict__ r32,
                            double* __restrict__ partials) {
     __shared__ double sh[32];
-    double acc2 = 0.0;
+    float acc2 = 0.f;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int nrows = ny * nz;
     const int sy = nx, sz = nx * ny;
-    auto X = [&](int q) -> df {
-        df v = {xh[q], xl[q]};
-        return e ? df_add_f(v, e[q]) : v;
+    auto Xn = [&](int q) -> df {   // neighbour value x + e, lo unnormalised
+        if (!e) return df{xh[q], xl[q]};
+        df s = two_sum(xh[q], e[q]);
+        s.lo = __fadd_rn(s.lo, xl[q]);
+        return s;
     };
     for (int rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
         const int j = rr % ny, k = rr / ny;
@@ -72,30 +82,31 @@ __global__ void k_df_resid(Lvl L, DfW wd, const float* __restrict__ xh, const fl
         if (L.ndim >= 3) ndz = (!hzm && L.bclo[2] == FLD_BC_DIRICHLET) + (!hzp && L.bchi[2] == FLD_BC_DIRICHLET);
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const int p = base + i;
-            const df xc = X(p);
+            const df x0 = {xh[p], xl[p]};
+            const df xc = e ? df_add_f(x0, e[p]) : x0;
             const df kc = {Kh[p], Kl[p]};
-            df res = df_sub({bh[p], bl[p]}, xc);
-            auto face = [&](int q, df acc) -> df {
-                const df kq = {Kh[q], Kl[q]};
-                return df_add(acc, df_mul(df_add(kc, kq), df_sub(xc, X(q))));
+            df res = dw_sub({bh[p], bl[p]}, xc);
+            auto face = [&](int q, df acc, bool first) -> df {
+                const df t = dw_mul(df_add(kc, df{Kh[q], Kl[q]}), df_sub(xc, Xn(q)));
+                return first ? t : dw_add(acc, t);
             };
             const bool hxm = i > 0 || L.bclo[0] == FLD_BC_PERIODIC;
             const bool hxp = i < nx - 1 || L.bchi[0] == FLD_BC_PERIODIC;
             df ax = {0.f, 0.f};
-            if (hxm) ax = face(i > 0 ? p - 1 : p + nx - 1, ax);
-            if (hxp) ax = face(i < nx - 1 ? p + 1 : p - nx + 1, ax);
-            res = df_sub(res, df_mul({wd.hh[0], wd.hl[0]}, ax));
+            if (hxm) ax = face(i > 0 ? p - 1 : p + nx - 1, ax, true);
+            if (hxp) ax = face(i < nx - 1 ? p + 1 : p - nx + 1, ax, !hxm);
+            res = dw_sub(res, dw_mul({wd.hh[0], wd.hl[0]}, ax));
             if (L.ndim >= 2) {
                 df ay = {0.f, 0.f};
-                if (hym) ay = face(p + oym, ay);
-                if (hyp) ay = face(p + oyp, ay);
-                res = df_sub(res, df_mul({wd.hh[1], wd.hl[1]}, ay));
+                if (hym) ay = face(p + oym, ay, true);
+                if (hyp) ay = face(p + oyp, ay, !hym);
+                res = dw_sub(res, dw_mul({wd.hh[1], wd.hl[1]}, ay));
             }
             if (L.ndim >= 3) {
                 df az = {0.f, 0.f};
-                if (hzm) az = face(p + ozm, az);
-                if (hzp) az = face(p + ozp, az);
-                res = df_sub(res, df_mul({wd.hh[2], wd.hl[2]}, az));
+                if (hzm) az = face(p + ozm, az, true);
+                if (hzp) az = face(p + ozp, az, !hzm);
+                res = dw_sub(res, dw_mul({wd.hh[2], wd.hl[2]}, az));
             }
             // Dirichlet walls: 2 w_d K_p x_p per wall face (= 4 (w_d/2) K_p x_p)
             const int ndx = (!hxm && L.bclo[0] == FLD_BC_DIRICHLET) + (!hxp && L.bchi[0] == FLD_BC_DIRICHLET);
@@ -104,18 +115,19 @@ __global__ void k_df_resid(Lvl L, DfW wd, const float* __restrict__ xh, const fl
                 if (ndx) dw = df_add(dw, df_mul({wd.hh[0], wd.hl[0]}, {4.f * ndx, 0.f}));
                 if (ndy) dw = df_add(dw, df_mul({wd.hh[1], wd.hl[1]}, {4.f * ndy, 0.f}));
                 if (ndz) dw = df_add(dw, df_mul({wd.hh[2], wd.hl[2]}, {4.f * ndz, 0.f}));
-                res = df_sub(res, df_mul(df_mul(dw, kc), xc));
+                res = dw_sub(res, df_mul(df_mul(dw, kc), xc));
             }
             if (oh) {
                 oh[p] = xc.hi;
                 ol[p] = xc.lo;
             }
-            r32[p] = res.hi;
-            acc2 = fma((double)res.hi, (double)res.hi, acc2);
+            const float r = __fadd_rn(res.hi, res.lo);
+            r32[p] = r;
+            acc2 = fmaf(r, r, acc2);
         }
     }
-    acc2 = block_sum(acc2, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc2;
+    const double a2 = block_sum((double)acc2, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a2;
 }
 
 void launch_df_setup(long long n, double S, const double* E, const double* b, const double* K,

@@ -253,6 +253,7 @@ __global__ void k_resid_restrict(Lvl F, Lvl C, const T* __restrict__ x, const T*
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
                            int block, cudaStream_t s) {
+    if (transfer3_ok(F, C)) return launch_resid_restrict3<T>(F, C, x, b, K, bc, s);
     k_resid_restrict<T><<<grid_for(C.ncell, block), block, 0, s>>>(F, C, x, b, K, bc);
 }
 
@@ -284,6 +285,7 @@ __global__ void k_prolong(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict_
 
 template <typename T>
 void launch_prolong(const Lvl& F, const Lvl& C, T* xf, const T* xc, int block, cudaStream_t s) {
+    if (transfer3_ok(F, C)) return launch_prolong3<T>(F, C, xf, xc, s);
     k_prolong<T><<<rows_grid(F), block, 0, s>>>(F, C, xf, xc);
 }
 

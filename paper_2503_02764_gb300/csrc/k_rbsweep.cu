@@ -1,19 +1,22 @@
 // One full red-black Gauss-Seidel sweep of a 3D FP32 level (red cells, then black cells)
 // in a single pass over memory, out of place: xout = sweep(xin).
 //
-// Each block owns a tile of ZM_TX x TY cells of the x-y plane and marches along z over a
-// chunk of planes [z0, z1). Thread (tp, ty) owns the cell pair (tx0 + 2 tp, +1) of row
-// ty0 + ty: one red and one black cell, so both colour phases keep every lane busy, and a
-// warp is one tile row (64 cells, 256 contiguous bytes).
+// Each block owns a tile of TX x TY cells of the x-y plane and marches along z over a
+// chunk of planes [z0, z1). Lane l of warp w owns the two cells (x, y0) and (x, y0 + 1)
+// of one column pair, x = tx0 + 32 (w % WX) + l, y0 = ty0 + 2 (w / WX): one red and one
+// black cell, so both colour phases keep every lane busy. Within a warp the red cells
+// alternate between the two rows; with a shared row pitch of 8 (mod 32) words those 32
+// scalar accesses fall in 32 distinct banks, as do those of every neighbour.
 //
 // Shared memory holds a ring of ZM_R planes of x, K and b, each with a 2-row halo in y
 // and a 4-column (one 16-byte chunk) halo in x, filled by cp.async ZM_D planes ahead of
-// use. Step m evaluates the red cells of plane m in place in the shared copy, on the tile
+// use. Step k evaluates the red cells of plane k in place in the shared copy, on the tile
 // and on its 1-cell ring (the ring values are recomputed rather than exchanged between
-// blocks), then the black cells of plane m-1, which need shared data only, and stores
-// plane m-1 of xout. Per sweep each cell's x, K and b are read once from global memory
-// and xout written once: 16 B per cell, against ~29 B for two in-place half sweeps,
-// whose red and black cells share every sector.
+// blocks), and the black cells of plane k-2, which need the red values of planes k-3 ..
+// k-1 only, so the two share one barrier per step; it stores plane k-2 of xout. Per sweep
+// each cell's x, K and b are read once from global memory and xout written once: 16 B
+// per cell, against ~29 B for two in-place half sweeps, whose red and black cells share
+// every sector.
 //
 // The updates are those of the half-sweep kernels: red cells take (b + acc)/(1 + sw) of
 // the input iterate, black cells that of the red-updated one, with the same face weights
@@ -32,21 +35,22 @@ namespace fld {
 
 namespace {
 
-constexpr int ZM_TXP = 32;                 // cell pairs per tile row (one warp)
-constexpr int ZM_TX = 2 * ZM_TXP;          // tile width in cells
-constexpr int ZM_XL = 4;                   // halo columns on each side: one 16-byte chunk
-constexpr int ZM_XW = ZM_TX + 2 * ZM_XL;   // shared row length
-constexpr int ZM_CPR = ZM_XW / 4;          // 16-byte chunks per shared row
-constexpr int ZM_D = 2;                    // planes in flight ahead of use
-constexpr int ZM_R = ZM_D + 4;             // ring depth: planes m-2 .. m+1+D
+constexpr int ZM_XL = 4;         // halo columns on each side: one 16-byte chunk
+constexpr int ZM_D = 2;          // planes in flight ahead of use
+constexpr int ZM_R = ZM_D + 5;   // ring depth: planes k-3 .. k+1+D
 
-template <int TY>
+template <int TX, int TY>
 struct ZmShape {
+    static constexpr int XW = TX + 2 * ZM_XL;   // shared row pitch (words)
     static constexpr int NROW = TY + 4;
-    static constexpr int PL = ZM_XW * NROW;     // floats per plane and field
-    static constexpr int NCH = NROW * ZM_CPR;   // 16-byte chunks per plane and field
-    static constexpr int NT = ZM_TXP * TY;      // threads per block
+    static constexpr int PL = XW * NROW;        // floats per plane and field
+    static constexpr int CPR = XW / 4;          // 16-byte chunks per shared row
+    static constexpr int NCH = NROW * CPR;      // chunks per plane and field
+    static constexpr int WX = TX / 32;          // warps across the tile width
+    static constexpr int NT = 32 * WX * (TY / 2);
     static constexpr size_t SMEM = sizeof(float) * 3 * ZM_R * PL;
+    static_assert(TX % 32 == 0 && TY % 2 == 0, "tile of whole warps and row pairs");
+    static_assert(XW % 32 == 8 || XW % 32 == 24, "row pitch giving conflict-free lanes");
     static_assert(NCH <= NT, "one copy chunk per thread");
 };
 
@@ -79,47 +83,49 @@ __device__ __forceinline__ void zm_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// (b + acc)/(1 + sw) of the cell at shared offset c; S0/K0 hold its plane, Sm/Km the one
-// below, Sp/Kp the one above; h* = w_d / 2.
-__device__ __forceinline__ float zm_relax(const float* S0, const float* K0, const float* Sm,
-                                          const float* Km, const float* Sp, const float* Kp,
-                                          int c, float bv, float hx, float hy, float hz) {
-    const float kc = K0[c];
-    float f = (kc + K0[c - 1]) * hx;
+// (b + acc)/(1 + sw) of one cell: z points at the shared array, o0 is the cell's offset
+// in the slot of its plane (x at +0, K at +PL, b at +2 PL), om and op the offsets of the
+// same cell in the slots of the planes below and above; XW is the row pitch; h* = w_d / 2.
+// Every access is one shared load at an immediate offset from o0, om or op.
+template <int XW, int PL>
+__device__ __forceinline__ float zm_relax(const float* z, int o0, int om, int op, float hx,
+                                          float hy, float hz) {
+    const float kc = z[o0 + PL];
+    float f = (kc + z[o0 + PL - 1]) * hx;
     float sw = f;
-    float acc = f * S0[c - 1];
-    f = (kc + K0[c + 1]) * hx;
+    float acc = f * z[o0 - 1];
+    f = (kc + z[o0 + PL + 1]) * hx;
     sw += f;
-    acc = fmaf(f, S0[c + 1], acc);
-    f = (kc + K0[c - ZM_XW]) * hy;
+    acc = fmaf(f, z[o0 + 1], acc);
+    f = (kc + z[o0 + PL - XW]) * hy;
     sw += f;
-    acc = fmaf(f, S0[c - ZM_XW], acc);
-    f = (kc + K0[c + ZM_XW]) * hy;
+    acc = fmaf(f, z[o0 - XW], acc);
+    f = (kc + z[o0 + PL + XW]) * hy;
     sw += f;
-    acc = fmaf(f, S0[c + ZM_XW], acc);
-    f = (kc + Km[c]) * hz;
+    acc = fmaf(f, z[o0 + XW], acc);
+    f = (kc + z[om + PL]) * hz;
     sw += f;
-    acc = fmaf(f, Sm[c], acc);
-    f = (kc + Kp[c]) * hz;
+    acc = fmaf(f, z[om], acc);
+    f = (kc + z[op + PL]) * hz;
     sw += f;
-    acc = fmaf(f, Sp[c], acc);
-    return __fdividef(bv + acc, 1.0f + sw);
+    acc = fmaf(f, z[op], acc);
+    return __fdividef(z[o0 + 2 * PL] + acc, 1.0f + sw);
 }
 
 }  // namespace
 
-template <int TY, int MINB>
-__global__ void __launch_bounds__(ZM_TXP * TY, MINB)
+template <int TX, int TY, int MINB>
+__global__ void __launch_bounds__(ZmShape<TX, TY>::NT, MINB)
 k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
             const float* __restrict__ b, const float* __restrict__ K, int cz) {
-    using SH = ZmShape<TY>;
-    constexpr int PL = SH::PL;
+    using SH = ZmShape<TX, TY>;
+    constexpr int PL = SH::PL, XW = SH::XW, CPR = SH::CPR;
     extern __shared__ __align__(16) float zsm[];
 
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int tilesx = (nx + ZM_TX - 1) / ZM_TX, tilesy = (ny + TY - 1) / TY;
+    const int tilesx = (nx + TX - 1) / TX, tilesy = (ny + TY - 1) / TY;
     int bid = blockIdx.x;
-    const int tx0 = (bid % tilesx) * ZM_TX;
+    const int tx0 = (bid % tilesx) * TX;
     bid /= tilesx;
     const int ty0 = (bid % tilesy) * TY;
     bid /= tilesy;
@@ -139,8 +145,8 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
     long long goff = 0;        // plane offset of the copied cells / of the mirrored cells
     float gfac = 0.0f;
     if (tid < SH::NCH) {
-        const int r = tid / ZM_CPR, ch = tid - r * ZM_CPR;
-        soff = r * ZM_XW + 4 * ch;
+        const int r = tid / CPR, ch = tid - r * CPR;
+        soff = r * XW + 4 * ch;
         const int gy = zm_axis(ty0 - 2 + r, ny, yper);
         const int rawx = tx0 - ZM_XL + 4 * ch;
         const int gx = zm_axis(rawx, nx, xper);
@@ -164,13 +170,11 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
         }
     }
 
-    auto slot = [](int m) { return (m + ZM_R) % ZM_R; };
-    auto Sp = [&](int m) { return zsm + slot(m) * 3 * PL; };
-
-    // Copy plane m (raw z coordinate, may lie outside [0, nz)) into its ring slot.
-    auto issue = [&](int m) {
+    // Copy plane m (raw z coordinate, may lie outside [0, nz)) into the ring slot at
+    // offset `slot` of the shared array.
+    auto issue = [&](int m, int slot) {
         if (cmode < 5 && m <= z1 + 1) {
-            float* Sd = Sp(m) + soff;
+            float* Sd = zsm + slot + soff;
             float* Kd = Sd + PL;
             float* Bd = Kd + PL;
             const int gz = zm_axis(m, nz, zper);
@@ -204,108 +208,111 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
         zm_commit();
     };
 
-    // ---- the interior pair of this thread
-    const int tp = tid & (ZM_TXP - 1), ty = tid / ZM_TXP;
-    const int gx = tx0 + 2 * tp, gy = ty0 + ty;
-    const bool active = gx < nx && gy < ny;
-    const int c0 = (ty + 2) * ZM_XW + ZM_XL + 2 * tp;
+    // ---- the interior column pair of this thread
+    const int lane = tid & 31, w = tid >> 5;
+    const int lx = 32 * (w % SH::WX) + lane, ly0 = 2 * (w / SH::WX);
+    const int gx = tx0 + lx, gy0 = ty0 + ly0;
+    const bool act0 = gx < nx && gy0 < ny, act1 = gx < nx && gy0 + 1 < ny;
+    const int c0 = (ly0 + 2) * XW + ZM_XL + lx;
 
     // ---- the ring cell pair of this thread: cells at distance 1 outside the active
     // rectangle [0, ax) x [0, ay) of the tile whose red value a black interior cell reads.
     // Row pairs (lx = 2k - 1, 2k) on ly = -1 and ly = ay; column pairs (ly = 2k, 2k + 1)
     // on lx = -1 and lx = ax. Exactly one cell of a pair is red on any plane.
-    const int ax = min(ZM_TX, nx - tx0), ay = min(TY, ny - ty0);
+    const int ax = min(TX, nx - tx0), ay = min(TY, ny - ty0);
     const int nrow = (ax + 2) / 2, ncol = (ay + 1) / 2;
     int rc0 = -1, rc1 = -1;    // shared offsets of the two candidates (-1: not a cell)
     int rpar = 0;              // parity of gx + gy of candidate 0
     {
-        int lx0 = 0, ly0 = 0, dx = 0, dy = 0;
+        int qx0 = 0, qy0 = 0, dx = 0, dy = 0;
         bool has = true, colseg = false;
         if (tid < nrow) {
-            lx0 = 2 * tid - 1; ly0 = -1; dx = 1;
+            qx0 = 2 * tid - 1; qy0 = -1; dx = 1;
         } else if (tid < 2 * nrow) {
-            lx0 = 2 * (tid - nrow) - 1; ly0 = ay; dx = 1;
+            qx0 = 2 * (tid - nrow) - 1; qy0 = ay; dx = 1;
         } else if (tid < 2 * nrow + ncol) {
-            lx0 = -1; ly0 = 2 * (tid - 2 * nrow); dy = 1; colseg = true;
+            qx0 = -1; qy0 = 2 * (tid - 2 * nrow); dy = 1; colseg = true;
         } else if (tid < 2 * nrow + 2 * ncol) {
-            lx0 = ax; ly0 = 2 * (tid - 2 * nrow - ncol); dy = 1; colseg = true;
+            qx0 = ax; qy0 = 2 * (tid - 2 * nrow - ncol); dy = 1; colseg = true;
         } else {
             has = false;
         }
         if (has) {
-            rpar = (tx0 + lx0 + ty0 + ly0) & 1;
+            rpar = (tx0 + qx0 + ty0 + qy0) & 1;
             for (int q = 0; q < 2; ++q) {
-                const int lx = lx0 + q * dx, ly = ly0 + q * dy;
-                const bool cell = zm_axis(tx0 + lx, nx, xper) >= 0 &&
-                                  zm_axis(ty0 + ly, ny, yper) >= 0;
-                const int off = (cell && !(colseg && ly >= ay)) ? (ly + 2) * ZM_XW + ZM_XL + lx : -1;
+                const int qx = qx0 + q * dx, qy = qy0 + q * dy;
+                const bool cell = zm_axis(tx0 + qx, nx, xper) >= 0 &&
+                                  zm_axis(ty0 + qy, ny, yper) >= 0;
+                const int off = (cell && !(colseg && qy >= ay)) ? (qy + 2) * XW + ZM_XL + qx : -1;
                 if (q == 0) rc0 = off; else rc1 = off;
             }
         }
     }
 
-    // red cells of plane m (global index gz) on the tile and its ring, in shared memory
-    auto red = [&](int m, int gz) {
-        float* S0 = Sp(m);
-        const float* K0 = S0 + PL;
-        const float* B0 = K0 + PL;
-        const float* Sm = Sp(m - 1);
-        const float* Km = Sm + PL;
-        const float* Sq = Sp(m + 1);
-        const float* Kq = Sq + PL;
-        if (active) {
-            const int c = c0 + ((gy + gz) & 1);
-            S0[c] = zm_relax(S0, K0, Sm, Km, Sq, Kq, c, B0[c], hx, hy, hz);
-        }
-        const int q = (rpar + gz) & 1;      // candidate 0 red when gx + gy + gz is even
-        const int c = q ? rc1 : rc0;
-        if (c >= 0) S0[c] = zm_relax(S0, K0, Sm, Km, Sq, Kq, c, B0[c], hx, hy, hz);
-    };
+    // Ring slot offsets of planes k-3 .. k+3 at step k (x at +0, K at +PL, b at +2 PL);
+    // each step rotates them by one, the slot of k-3 coming back as that of k+4.
+    auto slot_of = [&](int m) { return ((m + 2 * ZM_R) % ZM_R) * 3 * PL; };
+    int pm3 = slot_of(z0 - 4), pm2 = slot_of(z0 - 3), pm1 = slot_of(z0 - 2), p00 = slot_of(z0 - 1);
+    int pp1 = slot_of(z0), pp2 = slot_of(z0 + 1), pp3 = slot_of(z0 + 2);
+    static_assert(ZM_D == 2 && ZM_R == 7, "the rotation below holds planes k-3 .. k+3");
+    const bool ring_warp = (tid & ~31) < 2 * nrow + 2 * ncol;   // warp-uniform
+    float* xo = xout + (long long)gy0 * nx + gx;
 
-    // black cells of plane m (global index gz): relax from the red-updated values and
-    // store the cell pair of xout
-    auto black = [&](int m, int gz) {
-        if (!active) return;
-        const float* S0 = Sp(m);
-        const float* K0 = S0 + PL;
-        const float* B0 = K0 + PL;
-        const float* Sm = Sp(m - 1);
-        const float* Km = Sm + PL;
-        const float* Sq = Sp(m + 1);
-        const float* Kq = Sq + PL;
-        const int qb = (gy + gz + 1) & 1;   // which cell of the pair is black
-        const float v = zm_relax(S0, K0, Sm, Km, Sq, Kq, c0 + qb, B0[c0 + qb], hx, hy, hz);
-        const float2 out = qb ? make_float2(S0[c0], v) : make_float2(v, S0[c0 + 1]);
-        *reinterpret_cast<float2*>(xout + gz * plane + (long long)gy * nx + gx) = out;
-    };
-
-    // ---- the march. Step m: planes <= m + 1 have landed; red(m), then black(m - 1).
-    // The copy of plane m + 1 + D goes into the slot of plane m - 3, last read by
-    // black(m - 2) in the previous step.
-    for (int m = z0 - 2; m <= z0 - 1 + ZM_D; ++m) issue(m);
-    for (int m = z0 - 1; m <= z1; ++m) {
+    // ---- the march. Step k: planes <= k + 1 have landed; red(k) on the tile and its ring
+    // (in place in the shared copy) and black(k - 2), which reads planes k - 3 .. k - 1
+    // only. Both are evaluated unconditionally (so their arithmetic interleaves) and only
+    // the stores are predicated. The copy of plane k + 3 goes into the slot of plane k - 4,
+    // last read by black(k - 3) in the previous step.
+    issue(z0 - 2, pm1);
+    issue(z0 - 1, p00);
+    issue(z0, pp1);
+    issue(z0 + 1, pp2);
+    for (int k = z0 - 1; k <= z1 + 1; ++k) {
         zm_wait<ZM_D - 1>();
         __syncthreads();
-        issue(m + 1 + ZM_D);
-        const int gz = zm_axis(m, nz, zper);
-        if (gz >= 0) red(m, gz);
-        __syncthreads();
-        if (m - 1 >= z0) black(m - 1, m - 1);
+        issue(k + 3, pp3);
+        const bool do_red = k <= z1 && zm_axis(k, nz, zper) >= 0;
+        const bool do_black = k - 2 >= z0;
+        // red(k): the red row of the pair (parity of gz = parity of k: periodic extents
+        // are even, ghost planes are not updated)
+        const int q = (gx + gy0 + k) & 1;
+        const int cr = c0 + q * XW, cb = cr + (1 - 2 * q) * XW;
+        const float vr = zm_relax<XW, PL>(zsm, p00 + cr, pm1 + cr, pp1 + cr, hx, hy, hz);
+        // black(k - 2): the other row of the pair at plane k - 2 (same parity as k)
+        const float vb = zm_relax<XW, PL>(zsm, pm2 + cb, pm3 + cb, pm1 + cb, hx, hy, hz);
+        const float vrb = zsm[pm2 + cr];             // its red cell, updated two steps ago
+        if (ring_warp) {
+            const bool rsel = (rpar + k) & 1;
+            const int cg = rsel ? rc1 : rc0;
+            const int cq = cg >= 0 ? cg : c0;
+            const float vg = zm_relax<XW, PL>(zsm, p00 + cq, pm1 + cq, pp1 + cq, hx, hy, hz);
+            if (do_red && cg >= 0) zsm[p00 + cg] = vg;
+        }
+        if (do_red && (q ? act1 : act0)) zsm[p00 + cr] = vr;
+        if (do_black) {
+            float* o = xo + (long long)(k - 2) * plane;
+            if (act0) o[0] = q ? vb : vrb;
+            if (act1) o[nx] = q ? vrb : vb;
+        }
+        const int t = pm3;
+        pm3 = pm2; pm2 = pm1; pm1 = p00; p00 = pp1; pp1 = pp2; pp2 = pp3; pp3 = t;
     }
     zm_wait<0>();
 }
 
 namespace {
 
-constexpr int ZM_TY = 16, ZM_MINB = 2;
+constexpr int ZM_TX = 32, ZM_TY = 16, ZM_MINB = 3;
+using ZmMain = ZmShape<ZM_TX, ZM_TY>;
 
 int g_zm_slots = 0;   // resident blocks of the sweep kernel on the whole GPU
 
-// z-chunk length: enough blocks for one full wave on every SM (the tiles times the
-// chunks), chunks of at least 8 planes so the 2-plane overlap stays small.
+// z-chunk length: about three waves of blocks over the SMs (the tiles times the chunks),
+// chunks of at least 8 planes so the 2-plane overlap stays small (32 planes at 256^3,
+// the fastest measured there).
 int zm_chunk(const Lvl& L) {
     const int tiles = ((L.n[0] + ZM_TX - 1) / ZM_TX) * ((L.n[1] + ZM_TY - 1) / ZM_TY);
-    const int nch = std::max(1, std::max(g_zm_slots, 1) / std::max(1, tiles));
+    const int nch = std::max(1, 2 * std::max(g_zm_slots, 1) / std::max(1, tiles));
     const int cz = (L.n[2] + nch - 1) / nch;
     return std::min(L.n[2], std::max(8, cz));
 }
@@ -330,12 +337,11 @@ template <typename T>
 void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K,
                      cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-        constexpr size_t sm = ZmShape<ZM_TY>::SMEM;
         const int cz = zm_chunk(L);
         const int tiles = ((L.n[0] + ZM_TX - 1) / ZM_TX) * ((L.n[1] + ZM_TY - 1) / ZM_TY);
         const int nch = (L.n[2] + cz - 1) / cz;
-        k_rb_zmarch<ZM_TY, ZM_MINB><<<tiles * nch, ZM_TXP * ZM_TY, sm, s>>>(L, xin, xout, b, K,
-                                                                             cz);
+        k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>
+            <<<tiles * nch, ZmMain::NT, ZmMain::SMEM, s>>>(L, xin, xout, b, K, cz);
     }
 }
 
@@ -344,14 +350,13 @@ void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K
 void prepare_rb_sweep() {
     static std::once_flag once;
     std::call_once(once, [] {
-        constexpr size_t sm = ZmShape<ZM_TY>::SMEM;
-        cudaFuncSetAttribute(k_rb_zmarch<ZM_TY, ZM_MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZmMain::SMEM);
         int dev = 0, nsm = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rb_zmarch<ZM_TY, ZM_MINB>,
-                                                      ZM_TXP * ZM_TY, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>,
+                                                      ZmMain::NT, ZmMain::SMEM);
         g_zm_slots = std::max(1, nsm) * std::max(1, occ);
     });
 }
