@@ -650,9 +650,17 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
     if (op->kind == FLD_OPACITY_POWER && !T) return FLD_ERR_ARG;
     if (has_dirichlet(h->g) && !E_bc && h->o.limiter == FLD_LIMITER_LP) return FLD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    // double-FP32 mode: E split once into FP32 pairs (the level-0 FP32 buffers are free
+    // until the solve), so the limiter forms the gradient without FP64 arithmetic
+    const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF;
+    const bool split = dfmode && h->o.limiter == FLD_LIMITER_LP;
+    float* Eh = split ? h->d32[0].x : nullptr;
+    float* El = split ? h->d32[0].tmp : nullptr;
+    if (split)
+        run(h, "split_df", 0, h->ncell, s, [&] { launch_split_df(h->ncell, E, Eh, El, s); });
     run(h, "limiter", 0, h->ncell, s, [&] {
         launch_limiter(h->lv[0], h->g.h, E, rho, T, E_bc, h->bc_off, to_op(op), k->c, h->o.limiter,
-                       h->o.precision == FLD_PREC_MIXED_DF, D, lambda, &h->scal->err, s);
+                       dfmode, D, lambda, &h->scal->err, s, Eh, El);
     });
     FLD_CK(cudaGetLastError());
     return FLD_OK;

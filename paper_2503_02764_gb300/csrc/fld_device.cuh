@@ -159,6 +159,38 @@ __device__ __forceinline__ double fetch_E(const Lvl& L, const double* __restrict
     return v;
 }
 
+// fetch_E from the double-FP32 split copy (Eh, El) of E: the same ghost rules, a Dirichlet
+// ghost 2 E_b - E_mirror formed in FP64 and split.
+__device__ __forceinline__ df fetch_Edf(const Lvl& L, const float* __restrict__ Eh,
+                                        const float* __restrict__ El,
+                                        const double* __restrict__ E,
+                                        const double* __restrict__ Ebc, const BcOff& bo, int i,
+                                        int j, int k, int d, int o) {
+    int c[3] = {i, j, k};
+    const int n = L.n[d];
+    const int m = c[d] + o;
+    if (m >= 0 && m < n) {
+        c[d] = m;
+        const long long q = lin(L, c[0], c[1], c[2]);
+        return {Eh[q], El[q]};
+    }
+    int kind, side, mirror;
+    if (m < 0) {
+        kind = L.bclo[d];
+        side = 0;
+        mirror = kind == FLD_BC_PERIODIC ? m + n : -m - 1;
+    } else {
+        kind = L.bchi[d];
+        side = 1;
+        mirror = kind == FLD_BC_PERIODIC ? m - n : 2 * n - 1 - m;
+    }
+    c[d] = mirror;
+    const long long q = lin(L, c[0], c[1], c[2]);
+    if (kind == FLD_BC_DIRICHLET)
+        return df_from_double(2.0 * Ebc[bo.off[2 * d + side] + face_index(L, d, i, j, k)] - E[q]);
+    return {Eh[q], El[q]};
+}
+
 __device__ __forceinline__ bool f32_ok(double v) { return v > 1e-30 && v < 1e30; }
 
 __device__ __forceinline__ double exchange_root(double alpha, double beta, double q) {
@@ -303,6 +335,9 @@ __device__ __forceinline__ bool df_opacity(const Opacity& op, const DfConst& K, 
     return df_safe(kap.hi);
 }
 
+// With Eh/El (the split copy of E, nullable) the gradient is formed in double-FP32 from the
+// split values (FP64 work left: the cell's rho and T, the output, wall ghosts); without it
+// the gradient is FP64. ihd holds 1/(12 h_d) as (hi, lo) pairs for the split form.
 __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
                                                 const double* __restrict__ E,
                                                 const double* __restrict__ rho,
@@ -310,11 +345,21 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
                                                 const double* __restrict__ Ebc, const BcOff& bo,
                                                 const Opacity& op, const DfConst& K, int mode,
                                                 int i, int j, int k, long long p, double& Dout,
-                                                double& lmout) {
-    const double Ec = E[p], r = rho[p];
+                                                double& lmout, const float* __restrict__ Eh = nullptr,
+                                                const float* __restrict__ El = nullptr,
+                                                const df* ihd = nullptr) {
+    const double r = rho[p];
     const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
-    if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t))) return false;
-    const df Ed = df_from_double(Ec), rd = df_from_double(r), td = df_from_double(t);
+    df Ed;
+    if (Eh) {
+        Ed = {Eh[p], El[p]};
+        if (!(pos_finite(r) && pos_finite(t) && Ed.hi > 0.f)) return false;
+    } else {
+        const double Ec = E[p];
+        if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t))) return false;
+        Ed = df_from_double(Ec);
+    }
+    const df rd = df_from_double(r), td = df_from_double(t);
     if (!(df_safe(Ed.hi) && df_safe(rd.hi) && df_safe(td.hi))) return false;
     df kap;
     if (!df_opacity(op, K, rd, td, kap)) return false;
@@ -323,18 +368,43 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
     if (!df_safe(m.hi)) return false;
     df lm = {0.33333334f, -9.9341077e-09f};   // 1/3 as a double-FP32 pair
     if (mode == FLD_LIMITER_LP) {
-        double g2 = 0.0;
-        for (int d = 0; d < L.ndim; ++d) {
-            const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
-            const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
-            const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
-            const double ep2 = fetch_E(L, E, Ebc, bo, i, j, k, d, 2);
-            const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
-            g2 = fma(g, g, g2);
+        df g2d = {0.f, 0.f};
+        if (Eh) {
+            // (E_-2 - 8 E_-1) + 8 E_+1 - E_+2 in double-word form (the factors 8 are exact)
+            for (int d = 0; d < L.ndim; ++d) {
+                const df em2 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, -2);
+                const df em1 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, -1);
+                const df ep1 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, 1);
+                const df ep2 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, 2);
+                if (!(df_safe(em2.hi) && df_safe(em1.hi) && df_safe(ep1.hi) && df_safe(ep2.hi)))
+                    return false;
+                df t = dw_sub(em2, df{8.f * em1.hi, 8.f * em1.lo});
+                t = dw_add(t, df{8.f * ep1.hi, 8.f * ep1.lo});
+                t = dw_sub(t, ep2);
+                t = two_sum(t.hi, t.lo);
+                const df g = df_mul(t, ihd[d]);
+                // g^2 must stay a normal FP32 number (else the FP64 form decides)
+                const float ga = fabsf(g.hi);
+                if (ga != 0.f && !(ga > 1e-18f && ga < 1e18f)) return false;
+                g2d = dw_add(g2d, dw_mul(g, g));
+            }
+            g2d = two_sum(g2d.hi, g2d.lo);
+        } else {
+            double g2 = 0.0;
+            for (int d = 0; d < L.ndim; ++d) {
+                const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
+                const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
+                const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
+                const double ep2 = fetch_E(L, E, Ebc, bo, i, j, k, d, 2);
+                const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
+                g2 = fma(g, g, g2);
+            }
+            if (g2 > 0.0) {
+                g2d = df_from_double(g2);
+                if (!df_safe(g2d.hi)) return false;
+            }
         }
-        if (g2 > 0.0) {
-            const df g2d = df_from_double(g2);
-            if (!df_safe(g2d.hi)) return false;
+        if (g2d.hi > 0.f) {
             const df R = df_div(df_sqrt(g2d), m);
             if (!(R.hi < 1e12f)) return false;
             const df P = df_add_f(R, 2.f);

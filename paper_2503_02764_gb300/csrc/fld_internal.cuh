@@ -109,7 +109,9 @@ void launch_exchange(long long n, const double* rho, double* T, double* E, Opaci
 void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
                     double c, int mode, int use_df, double* D, double* lam, unsigned* err,
-                    cudaStream_t s);
+                    cudaStream_t s, float* Eh = nullptr, float* El = nullptr);
+// E split into FP32 (hi, lo) pairs (the double-FP32 limiter's input; Eh, El: n floats each).
+void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStream_t s);
 
 // multigrid (k_mg.cu)
 void launch_prep_level0(const Lvl& L, double kscale, const double* D, const double* E,

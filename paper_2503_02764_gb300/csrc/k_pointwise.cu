@@ -64,19 +64,34 @@ void launch_exchange(long long n, const double* rho, double* T, double* E, Opaci
 }
 
 // ----------------------------------------------------------------- limiter
+// E split into FP32 (hi, lo) pairs, once per cell, for the double-FP32 limiter's gradient
+__global__ void k_split_df(long long n, const double* __restrict__ v, float* __restrict__ hi,
+                           float* __restrict__ lo) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const df d = df_from_double(v[p]);
+        hi[p] = d.hi;
+        lo[p] = d.lo;
+    }
+}
+
 __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           const double* __restrict__ rho, const double* __restrict__ T,
                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
-                          int mode, int use_df, DfConst K, double* __restrict__ D,
+                          int mode, int use_df, DfConst K, const float* __restrict__ Eh,
+                          const float* __restrict__ El, double* __restrict__ D,
                           double* __restrict__ lam, unsigned* err) {
     const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
+    df ihd[3];
+    for (int d = 0; d < 3; ++d) ihd[d] = df_from_double(ih[d]);
     const int nrows = L.n[1] * L.n[2];
     for (int rw = blockIdx.x; rw < nrows; rw += gridDim.x)
         for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
             const int j = rw % L.n[1], k = rw / L.n[1];
             const long long p = (long long)rw * L.n[0] + i;
             double Dv, lm;
-            if (use_df && limiter_cell_df(L, ih, E, rho, T, Ebc, bo, op, K, mode, i, j, k, p, Dv, lm)) {
+            if (use_df && limiter_cell_df(L, ih, E, rho, T, Ebc, bo, op, K, mode, i, j, k, p, Dv, lm,
+                                          Eh, El, ihd)) {
                 D[p] = Dv;
                 if (lam) lam[p] = lm;
                 continue;
@@ -90,10 +105,15 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
         }
 }
 
+void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStream_t s) {
+    const long long nb = std::min<long long>((n + 255) / 256, 152 * 32);
+    k_split_df<<<(int)nb, 256, 0, s>>>(n, v, hi, lo);
+}
+
 void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
                     double c, int mode, int use_df, double* D, double* lam, unsigned* err,
-                    cudaStream_t s) {
+                    cudaStream_t s, float* Eh, float* El) {
     BcOff bo;
     for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
     double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
@@ -101,7 +121,9 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     const int block = 256;
     const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
     const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
-    k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, D, lam, err);
+    if (!(use_df && mode == FLD_LIMITER_LP)) Eh = El = nullptr;
+    k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, Eh, El, D,
+                                   lam, err);
 }
 
 }  // namespace fld
