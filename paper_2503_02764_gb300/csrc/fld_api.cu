@@ -429,14 +429,15 @@ fld_status diffuse_df(fld_handle* h, double* E, double bsum, fld_stats* st, cuda
     auto resid = [&](const float* e, double* rr) -> fld_status {
         float* oh = e ? h->dfx[cur ^ 1][0] : nullptr;
         float* ol = e ? h->dfx[cur ^ 1][1] : nullptr;
+        int nparts = NORM_BLOCKS;
         run(h, "resid_df", 0, n, s, [&] {
-            launch_df_resid(L0, wd, h->dfx[cur][0], h->dfx[cur][1], e, h->dfb[0], h->dfb[1],
-                            h->dfK[0], h->dfK[1], oh, ol, h->d32[0].b, h->partials, NORM_BLOCKS,
-                            NORM_THREADS, s);
+            nparts = launch_df_resid(L0, wd, h->dfx[cur][0], h->dfx[cur][1], e, h->dfb[0],
+                                     h->dfb[1], h->dfK[0], h->dfK[1], oh, ol, h->d32[0].b,
+                                     h->partials, NORM_BLOCKS, NORM_THREADS, s);
         });
         if (e) cur ^= 1;
-        run(h, "finish_sum", 0, NORM_BLOCKS, s,
-            [&] { launch_finish_sum(h->partials, NORM_BLOCKS, &h->scal->sum, s); });
+        run(h, "finish_sum", 0, nparts, s,
+            [&] { launch_finish_sum(h->partials, nparts, &h->scal->sum, s); });
         FLD_CK(cudaGetLastError());
         unsigned err;
         return read_scalars(h, s, rr, &err);

@@ -161,7 +161,7 @@ void launch_df_setup(long long n, double S, const double* E, const double* b, co
                      cudaStream_t s);
 void launch_df_finish(long long n, double invS, const float* xh, const float* xl, double* E,
                       cudaStream_t s);
-void launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* xl, const float* e,
+int launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* xl, const float* e,
                      const float* bh, const float* bl, const float* Kh, const float* Kl, float* oh,
                      float* ol, float* r32, double* partials, int nblocks, int block,
                      cudaStream_t s);

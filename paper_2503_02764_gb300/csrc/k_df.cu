@@ -2,6 +2,8 @@
 // (df64.cuh): the iterate x, the right-hand side b and the operator coefficient K are
 // held as FP32 (hi, lo) pairs scaled by a power of two S (exact), so that the FP64-grade
 // residual r = b - A x costs FP32 instructions only and the kernel stays memory-bound.
+#include <algorithm>
+
 #include "df64.cuh"
 #include "fld_device.cuh"
 
@@ -130,6 +132,189 @@ __global__ void k_df_resid(Lvl L, DfW wd, const float* __restrict__ xh, const fl
     if (threadIdx.x == 0) partials[blockIdx.x] = a2;
 }
 
+// 3D levels: the same residual with every face evaluated once. A block owns a DR_TX x DR_TY
+// tile of the x-y plane and marches along z over [z0, z1); thread (lx, ly) owns one
+// column. For each plane it forms x_new = x + e (renormalised) for its cell, and the
+// threads of the tile's ring (the cells at distance 1 outside the tile in x and y; ghosts
+// beyond a wall: x = 0, K = -K or 3 K of the wall cell) for theirs, into shared memory.
+// Each thread then evaluates the flux G = (K_c + K_q)(x_c - x_q) of its cell's -x and
+// -y faces (the last column and row also the +x, +y faces of the tile edge) and, from
+// its registers, of the -z face against the plane below. A cell's residual is
+//   b - x - h_x (G_x(-) - G_x(+)) - h_y (G_y(-) - G_y(+)) - h_z (G_z(-) - G_z(+)),
+// its +z term arriving one plane later. Per face: renormalised K_c + K_q and x_c - x_q,
+// an unnormalised product; every flux is used with both signs, exactly antisymmetric.
+constexpr int DR_TX = 32, DR_TY = 8, DR_NT = DR_TX * DR_TY;
+constexpr int DR_PW = DR_TX + 2;                   // shared row pitch (tile + ring)
+
+__device__ __forceinline__ int dr_axis(int g, int n, bool per) {
+    if (g >= 0 && g < n) return g;
+    if (per) return g < 0 ? g + n : g - n;
+    return -1;
+}
+
+__device__ __forceinline__ float dr_factor(int bc) { return bc == FLD_BC_DIRICHLET ? 3.f : -1.f; }
+
+__global__ void __launch_bounds__(DR_NT)
+k_df_resid3(Lvl L, DfW wd, const float* __restrict__ xh, const float* __restrict__ xl,
+            const float* __restrict__ e, const float* __restrict__ bh,
+            const float* __restrict__ bl, const float* __restrict__ Kh,
+            const float* __restrict__ Kl, float* __restrict__ oh, float* __restrict__ ol,
+            float* __restrict__ r32, double* __restrict__ partials, int cz) {
+    __shared__ float XH[(DR_TY + 2) * DR_PW], XL[(DR_TY + 2) * DR_PW];
+    __shared__ float KH[(DR_TY + 2) * DR_PW], KL[(DR_TY + 2) * DR_PW];
+    __shared__ float FXH[DR_TY * (DR_TX + 1)], FXL[DR_TY * (DR_TX + 1)];
+    __shared__ float FYH[(DR_TY + 1) * DR_TX], FYL[(DR_TY + 1) * DR_TX];
+    __shared__ double sh[32];
+
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int tilesx = (nx + DR_TX - 1) / DR_TX, tilesy = (ny + DR_TY - 1) / DR_TY;
+    int bid = blockIdx.x;
+    const int tx0 = (bid % tilesx) * DR_TX;
+    bid /= tilesx;
+    const int ty0 = (bid % tilesy) * DR_TY;
+    bid /= tilesy;
+    const int z0 = bid * cz, z1 = min(z0 + cz, nz);
+    const bool xper = L.bclo[0] == FLD_BC_PERIODIC, yper = L.bclo[1] == FLD_BC_PERIODIC;
+    const bool zper = L.bclo[2] == FLD_BC_PERIODIC;
+    const long long plane = (long long)nx * ny;
+    const df hx = {wd.hh[0], wd.hl[0]}, hy = {wd.hh[1], wd.hl[1]}, hz = {wd.hh[2], wd.hl[2]};
+
+    const int tid = threadIdx.x;
+    const int lx = tid % DR_TX, ly = tid / DR_TX;
+    const int ax = min(DR_TX, nx - tx0), ay = min(DR_TY, ny - ty0);
+    const bool act = lx < ax && ly < ay;
+    const long long own = act ? (long long)(ty0 + ly) * nx + tx0 + lx : 0;
+    const int so = (ly + 1) * DR_PW + lx + 1;
+
+    // ring cell of this thread: left/right columns, then bottom/top rows
+    int rso = -1;              // its shared offset (-1: none)
+    long long rsrc = 0;        // plane offset of the value it copies (the wall cell for a ghost)
+    bool rghost = false;
+    float rfac = 0.f;
+    {
+        int qx = 0, qy = 0;
+        bool has = true;
+        if (tid < ay) { qx = -1; qy = tid; }
+        else if (tid < 2 * ay) { qx = ax; qy = tid - ay; }
+        else if (tid < 2 * ay + ax) { qx = tid - 2 * ay; qy = -1; }
+        else if (tid < 2 * ay + 2 * ax) { qx = tid - 2 * ay - ax; qy = ay; }
+        else has = false;
+        if (has) {
+            rso = (qy + 1) * DR_PW + qx + 1;
+            const int gx = dr_axis(tx0 + qx, nx, xper), gy = dr_axis(ty0 + qy, ny, yper);
+            if (gx >= 0 && gy >= 0) {
+                rsrc = (long long)gy * nx + gx;
+            } else {
+                // the ghost next to a wall mirrors the adjacent tile cell
+                rghost = true;
+                const int wx = qx < 0 ? 0 : (qx >= ax ? ax - 1 : qx);
+                const int wy = qy < 0 ? 0 : (qy >= ay ? ay - 1 : qy);
+                rsrc = (long long)(ty0 + wy) * nx + tx0 + wx;
+                const int bc = gx < 0 ? (qx < 0 ? L.bclo[0] : L.bchi[0])
+                                      : (qy < 0 ? L.bclo[1] : L.bchi[1]);
+                rfac = dr_factor(bc);
+            }
+        }
+    }
+
+    auto xnew = [&](long long q) -> df {
+        const df v = {xh[q], xl[q]};
+        return e ? df_add_f(v, e[q]) : v;
+    };
+    // own column's x_new and K at plane m (raw z; wrap, or the wall ghost of Kwall)
+    auto column = [&](int m, df Kwall, df& xv, df& kv) {
+        const int gz = dr_axis(m, nz, zper);
+        if (gz >= 0) {
+            const long long q = gz * plane + own;
+            xv = xnew(q);
+            kv = {Kh[q], Kl[q]};
+        } else {
+            xv = {0.f, 0.f};
+            kv = df_mul_f(Kwall, dr_factor(m < 0 ? L.bclo[2] : L.bchi[2]));
+        }
+    };
+
+    float acc2 = 0.f;
+    df xprev = {0.f, 0.f}, kprev = {0.f, 0.f}, gzprev = {0.f, 0.f}, part = {0.f, 0.f};
+    if (act) {
+        const long long q0 = z0 * plane + own;
+        column(z0 - 1, df{Kh[q0], Kl[q0]}, xprev, kprev);
+    }
+    for (int k = z0; k <= z1; ++k) {
+        const bool inplane = k < z1;
+        // x_new and K of this plane's column (the plane z1 only for the z face)
+        df xk = {0.f, 0.f}, kk = {0.f, 0.f};
+        if (act) column(k, kprev, xk, kk);
+        if (inplane) {
+            const long long pk = (long long)k * plane;
+            if (act) {
+                XH[so] = xk.hi; XL[so] = xk.lo; KH[so] = kk.hi; KL[so] = kk.lo;
+                if (oh) {
+                    oh[pk + own] = xk.hi;
+                    ol[pk + own] = xk.lo;
+                }
+            }
+            if (rso >= 0) {
+                const long long q = pk + rsrc;
+                df xr, kr;
+                if (rghost) {
+                    xr = {0.f, 0.f};
+                    kr = df_mul_f(df{Kh[q], Kl[q]}, rfac);
+                } else {
+                    xr = xnew(q);
+                    kr = {Kh[q], Kl[q]};
+                }
+                XH[rso] = xr.hi; XL[rso] = xr.lo; KH[rso] = kr.hi; KL[rso] = kr.lo;
+            }
+        }
+        __syncthreads();
+        // -z face against the plane below (registers); fluxes of the -x, -y faces (shared)
+        df gz = {0.f, 0.f};
+        if (act) gz = dw_mul(df_add(kk, kprev), df_sub(xk, xprev));
+        auto flux = [&](int c, int q) -> df {    // (K_c + K_q)(x_c - x_q)
+            return dw_mul(df_add(df{KH[c], KL[c]}, df{KH[q], KL[q]}),
+                          df_sub(df{XH[c], XL[c]}, df{XH[q], XL[q]}));
+        };
+        if (inplane && act) {
+            df f = flux(so, so - 1);
+            FXH[ly * (DR_TX + 1) + lx] = f.hi; FXL[ly * (DR_TX + 1) + lx] = f.lo;
+            if (lx == ax - 1) {
+                f = flux(so + 1, so);
+                FXH[ly * (DR_TX + 1) + lx + 1] = f.hi; FXL[ly * (DR_TX + 1) + lx + 1] = f.lo;
+            }
+            f = flux(so, so - DR_PW);
+            FYH[ly * DR_TX + lx] = f.hi; FYL[ly * DR_TX + lx] = f.lo;
+            if (ly == ay - 1) {
+                f = flux(so + DR_PW, so);
+                FYH[(ly + 1) * DR_TX + lx] = f.hi; FYL[(ly + 1) * DR_TX + lx] = f.lo;
+            }
+        }
+        // the plane below is complete: its +z face is this plane's -z face
+        if (act && k - 1 >= z0) {
+            const df az = dw_sub(gzprev, gz);
+            const df res = dw_sub(part, dw_mul(hz, az));
+            const float r = __fadd_rn(res.hi, res.lo);
+            r32[(long long)(k - 1) * plane + own] = r;
+            acc2 = fmaf(r, r, acc2);
+        }
+        __syncthreads();
+        if (inplane && act) {
+            const int fx = ly * (DR_TX + 1) + lx, fy = ly * DR_TX + lx;
+            const df axv = dw_sub(df{FXH[fx], FXL[fx]}, df{FXH[fx + 1], FXL[fx + 1]});
+            const df ayv = dw_sub(df{FYH[fy], FYL[fy]}, df{FYH[fy + DR_TX], FYL[fy + DR_TX]});
+            const long long q = (long long)k * plane + own;
+            df res = dw_sub(df{bh[q], bl[q]}, xk);
+            res = dw_sub(res, dw_mul(hx, axv));
+            part = dw_sub(res, dw_mul(hy, ayv));
+        }
+        xprev = xk;
+        kprev = kk;
+        gzprev = gz;
+    }
+    const double a2 = block_sum((double)acc2, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a2;
+}
+
 void launch_df_setup(long long n, double S, const double* E, const double* b, const double* K,
                      float* xh, float* xl, float* bh, float* bl, float* Kh, float* Kl,
                      cudaStream_t s) {
@@ -145,11 +330,26 @@ void launch_df_finish(long long n, double invS, const float* xh, const float* xl
     k_df_finish<<<(int)nb, 256, 0, s>>>(n, invS, xh, xl, E);
 }
 
-void launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* xl, const float* e,
-                     const float* bh, const float* bl, const float* Kh, const float* Kl, float* oh,
-                     float* ol, float* r32, double* partials, int nblocks, int block,
-                     cudaStream_t s) {
+// Returns the number of partial sums written (the blocks of the launch, <= nblocks).
+int launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* xl, const float* e,
+                    const float* bh, const float* bl, const float* Kh, const float* Kl, float* oh,
+                    float* ol, float* r32, double* partials, int nblocks, int block,
+                    cudaStream_t s) {
+    if (L.ndim == 3) {
+        const int tiles = ((L.n[0] + DR_TX - 1) / DR_TX) * ((L.n[1] + DR_TY - 1) / DR_TY);
+        if (tiles <= nblocks) {
+            // z-chunks: as many as the partial-sum slots allow, at least 8 planes each
+            int nch = std::max(1, nblocks / tiles);
+            int cz = (L.n[2] + nch - 1) / nch;
+            cz = std::min(L.n[2], std::max(8, cz));
+            nch = (L.n[2] + cz - 1) / cz;
+            k_df_resid3<<<tiles * nch, DR_NT, 0, s>>>(L, wd, xh, xl, e, bh, bl, Kh, Kl, oh, ol,
+                                                       r32, partials, cz);
+            return tiles * nch;
+        }
+    }
     k_df_resid<<<nblocks, block, 0, s>>>(L, wd, xh, xl, e, bh, bl, Kh, Kl, oh, ol, r32, partials);
+    return nblocks;
 }
 
 }  // namespace fld
