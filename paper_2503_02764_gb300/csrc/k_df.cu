@@ -217,17 +217,48 @@ k_df_resid3(Lvl L, DfW wd, const float* __restrict__ xh, const float* __restrict
         }
     }
 
-    auto xnew = [&](long long q) -> df {
-        const df v = {xh[q], xl[q]};
-        return e ? df_add_f(v, e[q]) : v;
+    // Raw words of one plane for this thread's column and ring cell, loaded one plane ahead
+    // of use so the loads are in flight during the previous plane's flux work.
+    struct Raw {
+        float xh, xl, e, kh, kl, bh, bl;      // own column
+        float rxh, rxl, re, rkh, rkl;         // ring cell
     };
-    // own column's x_new and K at plane m (raw z; wrap, or the wall ghost of Kwall)
-    auto column = [&](int m, df Kwall, df& xv, df& kv) {
+    auto load_raw = [&](int m, Raw& R) {
         const int gz = dr_axis(m, nz, zper);
-        if (gz >= 0) {
-            const long long q = gz * plane + own;
-            xv = xnew(q);
-            kv = {Kh[q], Kl[q]};
+        if (gz < 0) return;                   // a wall ghost plane: formed from K below
+        const long long pk = gz * plane;
+        if (act) {
+            const long long q = pk + own;
+            R.xh = xh[q];
+            R.xl = xl[q];
+            R.e = e ? e[q] : 0.f;
+            R.kh = Kh[q];
+            R.kl = Kl[q];
+            if (m < z1) {
+                R.bh = bh[q];
+                R.bl = bl[q];
+            }
+        }
+        if (rso >= 0 && m < z1) {
+            const long long q = pk + rsrc;
+            R.rkh = Kh[q];
+            R.rkl = Kl[q];
+            if (!rghost) {
+                R.rxh = xh[q];
+                R.rxl = xl[q];
+                R.re = e ? e[q] : 0.f;
+            }
+        }
+    };
+    auto xform = [&](float h, float l, float ev) -> df {
+        const df v = {h, l};
+        return e ? df_add_f(v, ev) : v;
+    };
+    // own column's x_new and K at plane m from its raw words (wrap), or the wall ghost of Kwall
+    auto column = [&](int m, const Raw& R, df Kwall, df& xv, df& kv) {
+        if (dr_axis(m, nz, zper) >= 0) {
+            xv = xform(R.xh, R.xl, R.e);
+            kv = {R.kh, R.kl};
         } else {
             xv = {0.f, 0.f};
             kv = df_mul_f(Kwall, dr_factor(m < 0 ? L.bclo[2] : L.bchi[2]));
@@ -236,15 +267,18 @@ k_df_resid3(Lvl L, DfW wd, const float* __restrict__ xh, const float* __restrict
 
     float acc2 = 0.f;
     df xprev = {0.f, 0.f}, kprev = {0.f, 0.f}, gzprev = {0.f, 0.f}, part = {0.f, 0.f};
+    Raw cur = {}, nxt = {};
+    load_raw(z0, cur);
     if (act) {
-        const long long q0 = z0 * plane + own;
-        column(z0 - 1, df{Kh[q0], Kl[q0]}, xprev, kprev);
+        Raw below = {};
+        load_raw(z0 - 1, below);
+        column(z0 - 1, below, df{cur.kh, cur.kl}, xprev, kprev);
     }
     for (int k = z0; k <= z1; ++k) {
         const bool inplane = k < z1;
         // x_new and K of this plane's column (the plane z1 only for the z face)
         df xk = {0.f, 0.f}, kk = {0.f, 0.f};
-        if (act) column(k, kprev, xk, kk);
+        if (act) column(k, cur, kprev, xk, kk);
         if (inplane) {
             const long long pk = (long long)k * plane;
             if (act) {
@@ -255,18 +289,18 @@ k_df_resid3(Lvl L, DfW wd, const float* __restrict__ xh, const float* __restrict
                 }
             }
             if (rso >= 0) {
-                const long long q = pk + rsrc;
                 df xr, kr;
                 if (rghost) {
                     xr = {0.f, 0.f};
-                    kr = df_mul_f(df{Kh[q], Kl[q]}, rfac);
+                    kr = df_mul_f(df{cur.rkh, cur.rkl}, rfac);
                 } else {
-                    xr = xnew(q);
-                    kr = {Kh[q], Kl[q]};
+                    xr = xform(cur.rxh, cur.rxl, cur.re);
+                    kr = {cur.rkh, cur.rkl};
                 }
                 XH[rso] = xr.hi; XL[rso] = xr.lo; KH[rso] = kr.hi; KL[rso] = kr.lo;
             }
         }
+        if (k < z1) load_raw(k + 1, nxt);
         __syncthreads();
         // -z face against the plane below (registers); fluxes of the -x, -y faces (shared)
         df gz = {0.f, 0.f};
@@ -302,14 +336,14 @@ k_df_resid3(Lvl L, DfW wd, const float* __restrict__ xh, const float* __restrict
             const int fx = ly * (DR_TX + 1) + lx, fy = ly * DR_TX + lx;
             const df axv = dw_sub(df{FXH[fx], FXL[fx]}, df{FXH[fx + 1], FXL[fx + 1]});
             const df ayv = dw_sub(df{FYH[fy], FYL[fy]}, df{FYH[fy + DR_TX], FYL[fy + DR_TX]});
-            const long long q = (long long)k * plane + own;
-            df res = dw_sub(df{bh[q], bl[q]}, xk);
+            df res = dw_sub(df{cur.bh, cur.bl}, xk);
             res = dw_sub(res, dw_mul(hx, axv));
             part = dw_sub(res, dw_mul(hy, ayv));
         }
         xprev = xk;
         kprev = kk;
         gzprev = gz;
+        cur = nxt;
     }
     const double a2 = block_sum((double)acc2, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = a2;
@@ -338,11 +372,31 @@ int launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* x
     if (L.ndim == 3) {
         const int tiles = ((L.n[0] + DR_TX - 1) / DR_TX) * ((L.n[1] + DR_TY - 1) / DR_TY);
         if (tiles <= nblocks) {
-            // z-chunks: as many as the partial-sum slots allow, at least 8 planes each
-            int nch = std::max(1, nblocks / tiles);
-            int cz = (L.n[2] + nch - 1) / nch;
-            cz = std::min(L.n[2], std::max(8, cz));
-            nch = (L.n[2] + cz - 1) / cz;
+            // z-chunks sized against the resident blocks of the whole GPU, within the
+            // partial-sum slots, at least 8 planes each
+            static int slots = 0;
+            if (slots == 0) {
+                int dev = 0, nsm = 0, occ = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_df_resid3, DR_NT, 0);
+                slots = std::max(1, nsm * occ);
+            }
+            // the chunk count minimising waves x (planes per chunk + the 2 halo planes)
+            int best = 1;
+            long long bestc = -1;
+            for (int c = 1; c <= std::max(1, nblocks / tiles); ++c) {
+                const int czc = (L.n[2] + c - 1) / c;
+                if (czc < 8 && c > 1) break;
+                const long long waves = ((long long)tiles * c + slots - 1) / slots;
+                const long long cost = waves * (czc + 2);
+                if (bestc < 0 || cost < bestc) {
+                    bestc = cost;
+                    best = c;
+                }
+            }
+            const int cz = (L.n[2] + best - 1) / best;
+            const int nch = (L.n[2] + cz - 1) / cz;
             k_df_resid3<<<tiles * nch, DR_NT, 0, s>>>(L, wd, xh, xl, e, bh, bl, Kh, Kl, oh, ol,
                                                        r32, partials, cz);
             return tiles * nch;
