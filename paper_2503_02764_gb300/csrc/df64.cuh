@@ -129,4 +129,105 @@ __device__ __forceinline__ df df_from_double(double v) {
 
 __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
 
+// The same two conversions in integer arithmetic (FP64 instructions issue at 1/58 of the
+// FP32 rate here, and a conversion costs about two of them), bit-identical to the FP64
+// forms above; each returns false outside its window and the caller then uses those.
+//
+// split: v * 2^k2 -> (RN32, RN32 of the remainder), for 2^-48 <= |v 2^k2| < 2^80. hi is
+// the double's significand rounded to 24 bits (ties to even, a carry moving it to the next
+// binade); the remainder v - hi is an integer number of the double's ulps below 2^29,
+// rounded to 24 bits by the int -> float conversion and scaled through its exponent field.
+__device__ __forceinline__ bool df_split_i(double v, int k2, df& out) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sgn = (unsigned)(b >> 63);
+    const int e = (int)((b >> 52) & 0x7FF) + k2;
+    if (((b >> 52) & 0x7FF) == 0 || e < 1023 - 48 || e >= 1023 + 80) return false;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    unsigned mf = (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFu);
+    int ef = e - 1023 + 127;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mf & 1u))) {
+        if (++mf == 0x800000u) {
+            mf = 0;
+            ++ef;
+        }
+    }
+    out.hi = __uint_as_float((sgn << 31) | ((unsigned)ef << 23) | mf);
+    const unsigned long long hd =
+        ((unsigned long long)(ef - 127 + 1023 - k2) << 52) | ((unsigned long long)mf << 29);
+    const long long du = (long long)((b & 0x7FFFFFFFFFFFFFFFull) - hd);
+    if (du == 0) {
+        out.lo = 0.f;
+        return true;
+    }
+    unsigned fb = __float_as_uint(__int2float_rn((int)du));
+    fb = (fb & 0x807FFFFFu) | ((unsigned)((int)((fb >> 23) & 0xFF) + (e - 1075)) << 23);
+    const float lo = __uint_as_float(fb);
+    out.lo = sgn ? -lo : lo;
+    return true;
+}
+
+// join: (hi, lo) -> RN64(hi + lo) * 2^k2 for a normalised pair with 2^-100 < |hi| < 2^100.
+// hi's bits become the double's; lo is added as an integer number of the result's ulps
+// (rounded to nearest, ties to even, when lo reaches below them). A sum leaving hi's binade
+// (only an unnormalised pair does) takes the FP64 form; a subtraction from a binade start
+// lands one binade down and is counted in that binade's ulp.
+__device__ __forceinline__ bool df_join_i(df x, int k2, double& out) {
+    const unsigned hb = __float_as_uint(x.hi);
+    const int eh = (int)((hb >> 23) & 0xFF);
+    if (eh < 127 - 100 || eh > 127 + 100) return false;
+    const unsigned sgn = hb >> 31;
+    const unsigned hm = hb & 0x7FFFFFu;
+    const unsigned long long hd =
+        ((unsigned long long)(eh - 127 + 1023) << 52) | ((unsigned long long)hm << 29);
+    const unsigned lb = __float_as_uint(x.lo);
+    const int el = (int)((lb >> 23) & 0xFF);
+    unsigned long long res = hd;
+    if ((lb & 0x7FFFFFFFu) != 0) {
+        if (el == 0) return false;
+        const bool sub = (lb >> 31) != sgn;
+        const unsigned long long Ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
+        int sh = (el - 150) - (eh - 179);
+        if (sub && hm == 0) sh += 1;
+        unsigned long long units;
+        if (sh >= 0) {
+            if (sh > 8) return false;
+            units = Ml << sh;
+        } else if (-sh >= 40) {
+            units = 0;
+        } else {
+            const int r = -sh;
+            const unsigned long long q = Ml >> r, rm = Ml & ((1ull << r) - 1), half = 1ull << (r - 1);
+            units = q;
+            if (rm > half) {
+                units = q + 1;
+            } else if (rm == half) {
+                const unsigned long long t = sub ? hd - q : hd + q;
+                if (t & 1ull) units = q + 1;
+            }
+        }
+        res = sub ? hd - units : hd + units;
+        const unsigned long long eres = res >> 52, ehd = hd >> 52;
+        if (!(eres == ehd || (sub && hm == 0 && eres + 1 == ehd))) return false;
+    }
+    const int ef = (int)(res >> 52) + k2;
+    if (ef <= 0 || ef >= 2047) return false;
+    res = (res & 0xFFFFFFFFFFFFFull) | ((unsigned long long)ef << 52);
+    out = __longlong_as_double((long long)((((unsigned long long)sgn) << 63) | res));
+    return true;
+}
+
+// the conversions with the integer form first
+__device__ __forceinline__ df df_from_double_i(double v, int k2 = 0) {
+    df r;
+    if (df_split_i(v, k2, r)) return r;
+    return df_from_double(k2 ? ldexp(v, k2) : v);
+}
+__device__ __forceinline__ double df_to_double_i(df x, int k2 = 0) {
+    double r;
+    if (df_join_i(x, k2, r)) return r;
+    const double v = df_to_double(x);
+    return k2 ? ldexp(v, k2) : v;
+}
+
 }  // namespace fld

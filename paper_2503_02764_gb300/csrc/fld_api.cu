@@ -119,6 +119,8 @@ struct fld_handle {
     cudaGraphExec_t vgraph = nullptr;
     int vgraph_key[6] = {0, 0, 0, 0, 0, 0};
     long long vgraph_nodes = 0;
+    // first level of the single-launch V-cycle tail (-1: none); set when the levels are built
+    int tail_start = -1;
 };
 
 namespace {
@@ -205,7 +207,18 @@ bool has_dirichlet(const fld_grid& g) {
     return false;
 }
 
-void build_levels(fld_handle* h) { h->nlev = fld::make_levels(h->g, h->lv, h->kscale_down, MAX_LEVELS); }
+void build_levels(fld_handle* h) {
+    h->nlev = fld::make_levels(h->g, h->lv, h->kscale_down, MAX_LEVELS);
+    // the tail starts at the first level small enough for one block, if the coarsest level
+    // takes the dense solve and at least two levels remain
+    h->tail_start = -1;
+    if (h->lv[h->nlev - 1].ncell > TAIL_MAX_DENSE) return;
+    for (int l = 0; l + 1 < h->nlev; ++l)
+        if (h->lv[l].ncell <= TAIL_MAX_CELLS) {
+            if (h->nlev - l <= TAIL_MAX_LEVELS) h->tail_start = l;
+            break;
+        }
+}
 
 template <typename T>
 fld_status dalloc(fld_handle* h, T** p, long long n) {
@@ -294,6 +307,22 @@ void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
     if (l == h->nlev - 1) {
         run(h, f32 ? "coarse32" : "coarse64", l, L.ncell, s,
             [&] { launch_coarse_solve<T>(L, B.x, B.b, B.K, h->o.coarse_sweeps, s); });
+        return;
+    }
+    if (l == h->tail_start) {
+        // the rest of the V-cycle (a few thousand cells at most) in one launch
+        TailLevels<T> t{};
+        t.n = h->nlev - l;
+        t.nu1 = h->o.nu1;
+        t.nu2 = h->o.nu2;
+        for (int q = 0; q < t.n; ++q) {
+            t.L[q] = h->lv[l + q];
+            t.x[q] = P[l + q].x;
+            t.b[q] = P[l + q].b;
+            t.K[q] = P[l + q].K;
+            t.tmp[q] = P[l + q].tmp;
+        }
+        run(h, f32 ? "tail32" : "tail64", l, L.ncell, s, [&] { launch_vcycle_tail<T>(t, s); });
         return;
     }
     const int bs = blk(h);

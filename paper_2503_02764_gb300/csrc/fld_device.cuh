@@ -359,6 +359,8 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
         if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t))) return false;
         Ed = df_from_double(Ec);
     }
+    // FP64 conversions here: this kernel is bound by instruction issue, where the integer
+    // forms would cost more than the FP64 pipe does
     const df rd = df_from_double(r), td = df_from_double(t);
     if (!(df_safe(Ed.hi) && df_safe(rd.hi) && df_safe(td.hi))) return false;
     df kap;
@@ -371,7 +373,9 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
         df g2d = {0.f, 0.f};
         if (Eh) {
             // (E_-2 - 8 E_-1) + 8 E_+1 - E_+2 in double-word form (the factors 8 are exact)
-            for (int d = 0; d < L.ndim; ++d) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d >= L.ndim) break;
                 const df em2 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, -2);
                 const df em1 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, -1);
                 const df ep1 = fetch_Edf(L, Eh, El, E, Ebc, bo, i, j, k, d, 1);
@@ -391,7 +395,9 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
             g2d = two_sum(g2d.hi, g2d.lo);
         } else {
             double g2 = 0.0;
-            for (int d = 0; d < L.ndim; ++d) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d >= L.ndim) break;
                 const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
                 const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
                 const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
@@ -422,7 +428,7 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
 __device__ __forceinline__ bool exchange_cell_df(double r, double& t, double& er,
                                                  const Opacity& op, const DfConst& K) {
     if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) return false;
-    const df rd = df_from_double(r), td = df_from_double(t), Ed = df_from_double(er);
+    const df rd = df_from_double_i(r), td = df_from_double_i(t), Ed = df_from_double_i(er);
     if (!(df_safe(rd.hi) && df_safe(td.hi) && df_safe(Ed.hi))) return false;
     df kap;
     if (!df_opacity(op, K, rd, td, kap)) return false;
@@ -467,6 +473,8 @@ __device__ __forceinline__ bool exchange_cell_df(double r, double& t, double& er
     const df T2n = df_mul(Tn, Tn);
     const df En = df_add(df_mul(Ed, onemw), df_mul(beta, df_mul(T2n, T2n)));
     if (!(df_safe(Tn.hi) && df_safe(En.hi))) return false;
+    // inputs split in integer arithmetic, outputs joined on the FP64 pipe: the two pipes
+    // share the conversion work
     t = df_to_double(Tn);
     er = df_to_double(En);
     return true;

@@ -134,6 +134,24 @@ bool rb_sweep_supported(const Lvl& L);
 template <typename T>
 void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K, cudaStream_t s);
 void prepare_rb_sweep();
+// The coarse end of a V-cycle in one single-block launch: the levels from the first with at
+// most TAIL_MAX_CELLS cells to the coarsest (which must hold at most TAIL_MAX_DENSE cells).
+constexpr long long TAIL_MAX_CELLS = 4096;
+constexpr int TAIL_MAX_DENSE = 64;
+constexpr int TAIL_MAX_LEVELS = 10;
+template <typename T>
+struct TailLevels {
+    Lvl L[TAIL_MAX_LEVELS];
+    T* x[TAIL_MAX_LEVELS];
+    T* b[TAIL_MAX_LEVELS];
+    T* K[TAIL_MAX_LEVELS];
+    T* tmp[TAIL_MAX_LEVELS];
+    int n;          // levels in the tail, the last one the coarsest
+    int nu1, nu2;
+};
+template <typename T>
+void launch_vcycle_tail(const TailLevels<T>& t, cudaStream_t s);
+
 // 3D transfers when every axis halves exactly (one thread per coarse cell).
 bool transfer3_ok(const Lvl& F, const Lvl& C);
 template <typename T>

@@ -3,35 +3,39 @@
 // held as FP32 (hi, lo) pairs scaled by a power of two S (exact), so that the FP64-grade
 // residual r = b - A x costs FP32 instructions only and the kernel stays memory-bound.
 #include <algorithm>
+#include <cmath>
 
 #include "df64.cuh"
 #include "fld_device.cuh"
 
 namespace fld {
 
-__global__ void k_df_setup(long long n, double S, const double* __restrict__ E,
+// x = S E, b = S b, K split into double-FP32 pairs; S = 2^k2 (exact), applied in the
+// exponent by the integer split.
+__global__ void k_df_setup(long long n, int k2, const double* __restrict__ E,
                            const double* __restrict__ b, const double* __restrict__ K,
                            float* __restrict__ xh, float* __restrict__ xl, float* __restrict__ bh,
                            float* __restrict__ bl, float* __restrict__ Kh, float* __restrict__ Kl) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        df v = df_from_double(S * E[p]);
+        df v = df_from_double_i(E[p], k2);
         xh[p] = v.hi;
         xl[p] = v.lo;
-        v = df_from_double(S * b[p]);
+        v = df_from_double_i(b[p], k2);
         bh[p] = v.hi;
         bl[p] = v.lo;
-        v = df_from_double(K[p]);
+        v = df_from_double_i(K[p]);
         Kh[p] = v.hi;
         Kl[p] = v.lo;
     }
 }
 
-__global__ void k_df_finish(long long n, double invS, const float* __restrict__ xh,
+// E = (hi + lo) / S, S = 2^-k2 applied in the exponent by the integer join
+__global__ void k_df_finish(long long n, int k2, const float* __restrict__ xh,
                             const float* __restrict__ xl, double* __restrict__ E) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x)
-        E[p] = ((double)xh[p] + (double)xl[p]) * invS;
+        E[p] = df_to_double_i(df{xh[p], xl[p]}, k2);
 }
 
 // x_new = x + e (when e is given), written out of place; r = b - A x_new in double-FP32;
@@ -354,14 +358,14 @@ void launch_df_setup(long long n, double S, const double* E, const double* b, co
                      cudaStream_t s) {
     long long nb = (n + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_df_setup<<<(int)nb, 256, 0, s>>>(n, S, E, b, K, xh, xl, bh, bl, Kh, Kl);
+    k_df_setup<<<(int)nb, 256, 0, s>>>(n, std::ilogb(S), E, b, K, xh, xl, bh, bl, Kh, Kl);
 }
 
 void launch_df_finish(long long n, double invS, const float* xh, const float* xl, double* E,
                       cudaStream_t s) {
     long long nb = (n + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
-    k_df_finish<<<(int)nb, 256, 0, s>>>(n, invS, xh, xl, E);
+    k_df_finish<<<(int)nb, 256, 0, s>>>(n, std::ilogb(invS), xh, xl, E);
 }
 
 // Returns the number of partial sums written (the blocks of the launch, <= nblocks).

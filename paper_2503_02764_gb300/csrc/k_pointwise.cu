@@ -69,7 +69,7 @@ __global__ void k_split_df(long long n, const double* __restrict__ v, float* __r
                            float* __restrict__ lo) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        const df d = df_from_double(v[p]);
+        const df d = df_from_double_i(v[p]);
         hi[p] = d.hi;
         lo[p] = d.lo;
     }
