@@ -209,13 +209,15 @@ bool has_dirichlet(const fld_grid& g) {
 
 void build_levels(fld_handle* h) {
     h->nlev = fld::make_levels(h->g, h->lv, h->kscale_down, MAX_LEVELS);
-    // the tail starts at the first level small enough for one block, if the coarsest level
-    // takes the dense solve and at least two levels remain
+    // the tail starts at the first level small enough for one block (cells, and all its
+    // levels in shared memory even in FP64), if the coarsest level takes the dense solve
+    // and at least two levels remain
     h->tail_start = -1;
     if (h->lv[h->nlev - 1].ncell > TAIL_MAX_DENSE) return;
     for (int l = 0; l + 1 < h->nlev; ++l)
-        if (h->lv[l].ncell <= TAIL_MAX_CELLS) {
-            if (h->nlev - l <= TAIL_MAX_LEVELS) h->tail_start = l;
+        if (h->lv[l].ncell <= TAIL_MAX_CELLS && h->nlev - l <= TAIL_MAX_LEVELS &&
+            tail_smem_bytes<double>(h->lv + l, h->nlev - l) <= TAIL_SMEM_MAX) {
+            h->tail_start = l;
             break;
         }
 }
@@ -644,7 +646,10 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
         rc = FLD_ERR_NOMEM;
     }
     if (!rc && cudaMemset(h->scal, 0, sizeof(DevScalars)) != cudaSuccess) rc = FLD_ERR_CUDA;
-    if (!rc) prepare_rb_sweep();
+    if (!rc) {
+        prepare_rb_sweep();
+        prepare_vcycle_tail();
+    }
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = FLD_ERR_CUDA;
     if (rc) {
         free_all(h);
@@ -857,6 +862,7 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
     h.o = *o;
     h.o.graph = 0;        // graph capture and instantiation allocate: launch directly
     prepare_rb_sweep();   // kernel attributes only (no device memory)
+    prepare_vcycle_tail();
     build_levels(&h);
     h.ncell = h.lv[0].ncell;
     long long off = 0;

@@ -136,7 +136,7 @@ void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K
 void prepare_rb_sweep();
 // The coarse end of a V-cycle in one single-block launch: the levels from the first with at
 // most TAIL_MAX_CELLS cells to the coarsest (which must hold at most TAIL_MAX_DENSE cells).
-constexpr long long TAIL_MAX_CELLS = 4096;
+constexpr long long TAIL_MAX_CELLS = 512;
 constexpr int TAIL_MAX_DENSE = 64;
 constexpr int TAIL_MAX_LEVELS = 10;
 template <typename T>
@@ -151,6 +151,12 @@ struct TailLevels {
 };
 template <typename T>
 void launch_vcycle_tail(const TailLevels<T>& t, cudaStream_t s);
+// dynamic shared memory of a tail (4 arrays of every level) and its cap; the dense
+// coarsest solve adds 33 KB of static shared memory
+constexpr size_t TAIL_SMEM_MAX = 180 * 1024;
+template <typename T>
+size_t tail_smem_bytes(const Lvl* lv, int n);
+void prepare_vcycle_tail();
 
 // 3D transfers when every axis halves exactly (one thread per coarse cell).
 bool transfer3_ok(const Lvl& F, const Lvl& C);

@@ -1,16 +1,19 @@
-// The coarse end of a V-cycle in ONE single-block launch. From the first level with at
-// most TAIL_MAX_CELLS cells down to the coarsest, every step of the V-cycle (the pre- and
-// post-smoothing sweeps, residual restriction, zeroing of the coarse iterate, the exact
-// coarsest solve, prolongation) runs as block-stride loops separated by block barriers.
-// The levels there hold a few thousand cells at most, so each step is a few microseconds of
-// one SM, where separate launches would each cost their launch and tail latency (about
-// two dozen launches per V-cycle).
+// The coarse end of a V-cycle in ONE single-block launch, its levels held in shared memory.
+// From the first level with at most TAIL_MAX_CELLS cells down to the coarsest, every step
+// of the V-cycle (the pre- and post-smoothing sweeps, residual restriction, zeroing of the
+// coarse iterate, the exact coarsest solve, prolongation) runs as block-stride loops over
+// shared memory separated by block barriers. Those levels hold a few thousand cells at
+// most (8^3 and below at the measured best), so each step costs a few microseconds of one SM, where separate launches would
+// each cost their launch and tail latency (about two dozen launches per V-cycle), and a
+// global-memory form would wait on an L2 round trip per step.
 //
 // The arithmetic is that of the per-level kernels: red-black sweeps as two out-of-place
 // colour phases (the half-sweep update; on even periodic extents identical to the
 // in-place form), the average of the children's residuals b - A x, cell-centred
 // trilinear prolongation with mirrored walls, and Gauss-Jordan elimination in FP64 on
 // the coarsest level (at most TAIL_MAX_DENSE cells).
+#include <mutex>
+
 #include "fld_device.cuh"
 
 namespace fld {
@@ -155,32 +158,80 @@ __device__ void tail_dense(const Lvl& L, T* __restrict__ x, const T* __restrict_
     __syncthreads();
 }
 
+// All tail levels live in shared memory for the whole launch: the first level's x and b
+// and every level's K are read once, the first level's x written back once; every phase
+// in between touches shared memory only.
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailLevels<T> t) {
     __shared__ double A[TAIL_MAX_DENSE][TAIL_MAX_DENSE + 1];
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    T* xs[TAIL_MAX_LEVELS];
+    T* bs[TAIL_MAX_LEVELS];
+    T* Ks[TAIL_MAX_LEVELS];
+    T* ts[TAIL_MAX_LEVELS];
+    {
+        T* p = reinterpret_cast<T*>(tail_smem);
+        for (int q = 0; q < t.n; ++q) {
+            const int n = (int)t.L[q].ncell;
+            xs[q] = p; bs[q] = p + n; Ks[q] = p + 2 * n; ts[q] = p + 3 * n;
+            p += 4 * n;
+        }
+    }
+    for (int q = 0; q < t.n; ++q)
+        for (int p = threadIdx.x; p < (int)t.L[q].ncell; p += blockDim.x) {
+            Ks[q][p] = t.K[q][p];
+            if (q == 0) {
+                xs[0][p] = t.x[0][p];
+                bs[0][p] = t.b[0][p];
+            }
+        }
+    __syncthreads();
     const int last = t.n - 1;
     // down: pre-smooth, restrict the residual, clear the coarse iterate
     for (int l = 0; l < last; ++l) {
-        tail_smooth<T>(t.L[l], t.nu1, t.x[l], t.tmp[l], t.b[l], t.K[l]);
-        tail_restrict<T>(t.L[l], t.L[l + 1], t.x[l], t.b[l], t.K[l], t.b[l + 1]);
-        for (int p = threadIdx.x; p < (int)t.L[l + 1].ncell; p += blockDim.x) t.x[l + 1][p] = T(0);
+        tail_smooth<T>(t.L[l], t.nu1, xs[l], ts[l], bs[l], Ks[l]);
+        tail_restrict<T>(t.L[l], t.L[l + 1], xs[l], bs[l], Ks[l], bs[l + 1]);
+        for (int p = threadIdx.x; p < (int)t.L[l + 1].ncell; p += blockDim.x) xs[l + 1][p] = T(0);
         __syncthreads();
     }
-    tail_dense<T>(t.L[last], t.x[last], t.b[last], t.K[last], A);
+    tail_dense<T>(t.L[last], xs[last], bs[last], Ks[last], A);
     // up: prolong the correction, post-smooth
     for (int l = last - 1; l >= 0; --l) {
-        tail_prolong<T>(t.L[l], t.L[l + 1], t.x[l], t.x[l + 1]);
+        tail_prolong<T>(t.L[l], t.L[l + 1], xs[l], xs[l + 1]);
         __syncthreads();
-        tail_smooth<T>(t.L[l], t.nu2, t.x[l], t.tmp[l], t.b[l], t.K[l]);
+        tail_smooth<T>(t.L[l], t.nu2, xs[l], ts[l], bs[l], Ks[l]);
     }
+    for (int p = threadIdx.x; p < (int)t.L[0].ncell; p += blockDim.x) t.x[0][p] = xs[0][p];
 }
 
 }  // namespace
 
 template <typename T>
-void launch_vcycle_tail(const TailLevels<T>& t, cudaStream_t s) {
-    k_vcycle_tail<T><<<1, TAIL_THREADS, 0, s>>>(t);
+size_t tail_smem_bytes(const Lvl* lv, int n) {
+    size_t c = 0;
+    for (int q = 0; q < n; ++q) c += (size_t)lv[q].ncell;
+    return 4 * sizeof(T) * c;
 }
+
+template <typename T>
+void launch_vcycle_tail(const TailLevels<T>& t, cudaStream_t s) {
+    k_vcycle_tail<T><<<1, TAIL_THREADS, tail_smem_bytes<T>(t.L, t.n), s>>>(t);
+}
+
+// Opt the tail kernels into TAIL_SMEM_MAX bytes of dynamic shared memory: once per process,
+// outside any stream capture (called when a handle is created).
+void prepare_vcycle_tail() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TAIL_SMEM_MAX);
+        cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TAIL_SMEM_MAX);
+    });
+}
+
+template size_t tail_smem_bytes<float>(const Lvl*, int);
+template size_t tail_smem_bytes<double>(const Lvl*, int);
 
 template void launch_vcycle_tail<float>(const TailLevels<float>&, cudaStream_t);
 template void launch_vcycle_tail<double>(const TailLevels<double>&, cudaStream_t);
