@@ -2,10 +2,9 @@
 // From the first level with at most TAIL_MAX_CELLS cells down to the coarsest, every step
 // of the V-cycle (the pre- and post-smoothing sweeps, residual restriction, zeroing of the
 // coarse iterate, the exact coarsest solve, prolongation) runs as block-stride loops over
-// shared memory separated by block barriers. Those levels hold a few thousand cells at
-// most (8^3 and below at the measured best), so each step costs a few microseconds of one SM, where separate launches would
-// each cost their launch and tail latency (about two dozen launches per V-cycle), and a
-// global-memory form would wait on an L2 round trip per step.
+// shared memory separated by block barriers. Those levels are small (8^3 and below, the
+// measured best start), so the steps cost microseconds of one SM, where separate launches
+// would each cost their launch and tail latency (about two dozen launches per V-cycle).
 //
 // The arithmetic is that of the per-level kernels: red-black sweeps as two out-of-place
 // colour phases (the half-sweep update; on even periodic extents identical to the
