@@ -41,6 +41,8 @@ BYTES_PER_CELL = {
     "limiter": 32.0,          # E, rho, T read; D written (power-law opacity)
     "prep": 36.0,             # D, E read; K64, K32, b written
     "split_df": 16.0,         # E read; its FP32 (hi, lo) pair written
+    "df_setup": 48.0,         # E, b, K read; their FP32 (hi, lo) pairs written
+    "df_finish": 16.0,        # x (hi, lo) read; E written
     "sumsq": 8.0,             # b read
     "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
     "resid_df": 40.0,         # x (hi, lo), e32, b (hi, lo), K (hi, lo) read; x (hi, lo), r32 written
