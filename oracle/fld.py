@@ -138,6 +138,39 @@ def limiter(E, rho, T, h, bc, E_bc, c, op, mode=0):
     return D, lam, R
 
 
+def coupling(E, rho, T, h, bc, E_bc, c, op, v=None, mode=0):
+    """Explicit coupling terms of the limiter pass (Sect. 3), from the same gradient.
+
+    F = -D grad E (Eq. fld_F); the radiation force f_r = rho kappa F / c = -lambda grad E
+    (Eq. rad_force with Eq. fld_F); the scalar Eddington factor f = lambda + lambda^2 R^2
+    (Eq. fld_f); the Eddington tensor ((1 - f) I + (3f - 1) n n) / 2 with n = grad E /
+    |grad E| (Eq. fld_Eddington_tensor; n n drops out where grad E = 0, since f = 1/3
+    there); P = tensor E (Eq. fld_P). With a velocity field v (ndim components, v[d] along
+    physical axis d): v . f_r and the photon-tiring term P : grad v = sum_ij P_ij d_j v_i,
+    grad v by the same 5-point stencil with velocity ghosts wrapping on periodic axes and
+    mirroring evenly at walls (zero gradient; the paper does not fix them).
+
+    Returns a dict with F, fr (lists of ndim arrays), f, P (ndim x ndim nested lists),
+    and vfr, ptire when v is given.
+    """
+    D, lam, R = limiter(E, rho, T, h, bc, E_bc, c, op, mode)
+    g = gradient5(E, h, bc, E_bc)
+    nd = E.ndim
+    gnorm = np.sqrt(sum(gi * gi for gi in g))
+    safe = np.where(gnorm > 0, gnorm, 1.0)
+    n = [np.where(gnorm > 0, gi / safe, 0.0) for gi in g]
+    f = eddington_factor(lam, R)
+    P = [[(0.5 * (1.0 - f) * (1.0 if i == j else 0.0) + 0.5 * (3.0 * f - 1.0) * n[i] * n[j]) * E
+          for j in range(nd)] for i in range(nd)]
+    out = {"F": [-D * gi for gi in g], "fr": [-lam * gi for gi in g], "f": f, "P": P}
+    if v is not None:
+        out["vfr"] = sum(v[d] * out["fr"][d] for d in range(nd))
+        bcv = tuple((PERIODIC, PERIODIC) if b[0] == PERIODIC else (NEUMANN, NEUMANN) for b in bc)
+        gv = [gradient5(v[i], h, bcv, {}) for i in range(nd)]       # gv[i][j] = d_j v_i
+        out["ptire"] = sum(P[i][j] * gv[i][j] for i in range(nd) for j in range(nd))
+    return out
+
+
 # ----------------------------------------------------------------- diffusion
 def assemble(D, h, bc, E_bc, dt):
     """Backward-Euler matrix A and the Dirichlet right-hand-side term g.
