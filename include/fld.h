@@ -154,6 +154,28 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
                        const double* E, const double* rho, const double* T,
                        const double* E_bc, double* D, double* lambda, void* stream);
 
+/* Explicit coupling terms of the limiter pass (Sect. 3, which adds them explicitly):
+   from the same gradient, R and lambda as fld_limiter (the handle's limiter option),
+     F   = -D grad E = -(c lambda/(kappa rho)) grad E             (Eq. fld_F),
+     f_r = rho kappa F / c = -lambda grad E                         (Eq. rad_force),
+     f   = lambda + lambda^2 R^2                                    (Eq. fld_f),
+   and, given the velocity v, the work of the radiation force v . f_r and the photon
+   tiring term P : grad v = sum_ij P_ij d_j v_i with P = E f_tensor (Eq. fld_P),
+   f_tensor = ((1 - f) I + (3f - 1) n n)/2, n = grad E/|grad E| (Eq.
+   fld_Eddington_tensor; n n drops out where grad E = 0, since f = 1/3 there). grad v
+   uses the same 5-point stencil; velocity ghosts wrap on periodic axes and mirror evenly
+   (zero gradient) at walls.
+   In:  E, rho, T, E_bc as for fld_limiter; v (device float64, ndim * ncell, component d
+        at v + d * ncell, may be NULL).
+   Out (device float64, each may be NULL): F and fr (ndim * ncell, component-major like v),
+        f_edd (ncell), vfr and ptire (ncell; need v).
+   FLD_ERR_ARG for a missing required input; invalid cells set the domain flag and keep
+   their outputs unchanged. FP64 arithmetic. Asynchronous. */
+fld_status fld_coupling(fld_handle* h, const fld_consts* k, const fld_opacity* op,
+                        const double* E, const double* rho, const double* T,
+                        const double* E_bc, const double* v, double* F, double* fr,
+                        double* f_edd, double* vfr, double* ptire, void* stream);
+
 /* Backward-Euler diffusion step: solves A E^{n+1} = E^n + g in place,
      (A x)_i = x_i + sum_faces (dt/h_d^2) w_f (x_i - x_j),  w_f = (D_i + D_j)/2,
    a Dirichlet face adding (dt/h_d^2) 2 D_i (x_i - E_b) (g holds the E_b part),

@@ -701,6 +701,23 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
     return FLD_OK;
 }
 
+fld_status fld_coupling(fld_handle* h, const fld_consts* k, const fld_opacity* op,
+                        const double* E, const double* rho, const double* T, const double* E_bc,
+                        const double* v, double* F, double* fr, double* f_edd, double* vfr,
+                        double* ptire, void* stream) {
+    if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho) return FLD_ERR_ARG;
+    if (op->kind == FLD_OPACITY_POWER && !T) return FLD_ERR_ARG;
+    if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
+    if ((vfr || ptire) && !v) return FLD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    run(h, "coupling", 0, h->ncell, s, [&] {
+        launch_coupling(h->lv[0], h->g.h, E, rho, T, E_bc, h->bc_off, to_op(op), k->c,
+                        h->o.limiter, v, F, fr, f_edd, vfr, ptire, &h->scal->err, s);
+    });
+    FLD_CK(cudaGetLastError());
+    return FLD_OK;
+}
+
 fld_status fld_diffuse(fld_handle* h, double dt, const double* D, const double* E_bc, double* E,
                        fld_stats* stats, void* stream) {
     if (!h || !D || !E || !(dt > 0) || !std::isfinite(dt)) return FLD_ERR_ARG;

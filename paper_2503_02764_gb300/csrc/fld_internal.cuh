@@ -110,6 +110,11 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
                     double c, int mode, int use_df, double* D, double* lam, unsigned* err,
                     cudaStream_t s, float* Eh = nullptr, float* El = nullptr);
+// explicit coupling terms of the limiter pass (nullable outputs; v, vfr and pt together)
+void launch_coupling(const Lvl& L, const double* h, const double* E, const double* rho,
+                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
+                     double c, int mode, const double* v, double* F, double* fr, double* fe,
+                     double* vfr, double* pt, unsigned* err, cudaStream_t s);
 // E split into FP32 (hi, lo) pairs (the double-FP32 limiter's input; Eh, El: n floats each).
 void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStream_t s);
 

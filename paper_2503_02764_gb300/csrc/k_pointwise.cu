@@ -105,6 +105,109 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
         }
 }
 
+// ----------------------------------------------------------------- coupling terms
+// v_c at offset o (|o| <= 2) along axis d: periodic wrap, an even mirror at walls.
+__device__ __forceinline__ double fetch_v(const Lvl& L, const double* __restrict__ v, int i,
+                                          int j, int k, int d, int o) {
+    int c[3] = {i, j, k};
+    const int n = L.n[d];
+    int m = c[d] + o;
+    if (m < 0) m = L.bclo[d] == FLD_BC_PERIODIC ? m + n : -m - 1;
+    else if (m >= n) m = L.bchi[d] == FLD_BC_PERIODIC ? m - n : 2 * n - 1 - m;
+    c[d] = m;
+    return v[lin(L, c[0], c[1], c[2])];
+}
+
+// Explicit coupling terms of one cell, in FP64 from the limiter's gradient: F = -D grad E,
+// f_r = -lambda grad E, f = lambda + lambda^2 R^2, and with v: v . f_r and
+// P : grad v, P = E ((1 - f) I + (3f - 1) n n) / 2, n = grad E / |grad E|.
+__global__ void k_coupling(Lvl L, double3 inv12h, double3 inv12hv, const double* __restrict__ E,
+                           const double* __restrict__ rho, const double* __restrict__ T,
+                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
+                           int mode, const double* __restrict__ v, double* __restrict__ F,
+                           double* __restrict__ fr, double* __restrict__ fe,
+                           double* __restrict__ vfr, double* __restrict__ pt, unsigned* err) {
+    const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
+    const double ihv[3] = {inv12hv.x, inv12hv.y, inv12hv.z};
+    const int nd = L.ndim;
+    const long long nc = L.ncell;
+    const int nrows = L.n[1] * L.n[2];
+    for (int rw = blockIdx.x; rw < nrows; rw += gridDim.x)
+        for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+            const int j = rw % L.n[1], k = rw / L.n[1];
+            const long long p = (long long)rw * L.n[0] + i;
+            const double Ec = E[p], r = rho[p];
+            const double t = op.kind == FLD_OPACITY_CONST ? 1.0 : T[p];
+            if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t))) {
+                atomicOr(err, ERRBIT_DOMAIN);
+                continue;
+            }
+            const double kap = opacity_eval(op, r, t);
+            if (!pos_finite(kap)) {
+                atomicOr(err, ERRBIT_DOMAIN);
+                continue;
+            }
+            double g[3] = {0.0, 0.0, 0.0};
+            double g2 = 0.0;
+            for (int d = 0; d < nd; ++d) {
+                const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
+                const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
+                const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
+                const double ep2 = fetch_E(L, E, Ebc, bo, i, j, k, d, 2);
+                g[d] = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
+                g2 = fma(g[d], g[d], g2);
+            }
+            const double gn = sqrt(g2);
+            const double kr = kap * r;
+            const double R = gn / (kr * Ec);
+            const double lam = mode == FLD_LIMITER_LP ? (2.0 + R) / (6.0 + 3.0 * R + R * R)
+                                                      : 1.0 / 3.0;
+            const double D = c * lam / kr;
+            const double f = lam + lam * lam * R * R;
+            double vf = 0.0;
+            for (int d = 0; d < nd; ++d) {
+                const double frd = -lam * g[d];
+                if (F) F[d * nc + p] = -D * g[d];
+                if (fr) fr[d * nc + p] = frd;
+                if (v) vf = fma(v[d * nc + p], frd, vf);
+            }
+            if (fe) fe[p] = f;
+            if (v && vfr) vfr[p] = vf;
+            if (v && pt) {
+                double n[3] = {0.0, 0.0, 0.0};
+                if (gn > 0.0)
+                    for (int d = 0; d < nd; ++d) n[d] = g[d] / gn;
+                const double a = 0.5 * (1.0 - f), bq = 0.5 * (3.0 * f - 1.0);
+                double acc = 0.0;
+                for (int a1 = 0; a1 < nd; ++a1) {            // velocity component
+                    const double* vi = v + a1 * nc;
+                    for (int a2 = 0; a2 < nd; ++a2) {        // derivative axis
+                        const double gv = ((fetch_v(L, vi, i, j, k, a2, -2) -
+                                            8.0 * fetch_v(L, vi, i, j, k, a2, -1)) +
+                                           8.0 * fetch_v(L, vi, i, j, k, a2, 1) -
+                                           fetch_v(L, vi, i, j, k, a2, 2)) * ihv[a2];
+                        const double Pij = ((a1 == a2 ? a : 0.0) + bq * n[a1] * n[a2]) * Ec;
+                        acc = fma(Pij, gv, acc);
+                    }
+                }
+                pt[p] = acc;
+            }
+        }
+}
+
+void launch_coupling(const Lvl& L, const double* h, const double* E, const double* rho,
+                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
+                     double c, int mode, const double* v, double* F, double* fr, double* fe,
+                     double* vfr, double* pt, unsigned* err, cudaStream_t s) {
+    BcOff bo;
+    for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
+    const double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
+                                    L.ndim > 2 ? 1.0 / (12.0 * h[2]) : 0.0);
+    const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
+    k_coupling<<<nb, 256, 0, s>>>(L, ih, ih, E, rho, T, E_bc, bo, op, c, mode, v, F, fr, fe, vfr,
+                                  pt, err);
+}
+
 void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStream_t s) {
     const long long nb = std::min<long long>((n + 255) / 256, 152 * 32);
     k_split_df<<<(int)nb, 256, 0, s>>>(n, v, hi, lo);

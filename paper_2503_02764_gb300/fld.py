@@ -79,6 +79,8 @@ def lib():
         "fld_num_levels": (C.c_int, [H]),
         "fld_limiter": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), P, P, P, P, P,
                                   P, P]),
+        "fld_coupling": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), P, P, P, P,
+                                   P, P, P, P, P, P, P]),
         "fld_diffuse": (C.c_int, [H, C.c_double, P, P, P, C.POINTER(fld_stats), P]),
         "fld_exchange": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), C.c_double,
                                    P, P, P, P]),
@@ -200,6 +202,13 @@ def fld_num_levels(h):
 def fld_limiter(h, consts, opacity, E, rho, T, E_bc, D, lam=None, stream=None):
     _check(lib().fld_limiter(h, C.byref(consts), C.byref(opacity), _ptr(E), _ptr(rho), _ptr(T),
                              _ptr(E_bc), _ptr(D), _ptr(lam), _stream(stream)), "fld_limiter")
+
+
+def fld_coupling(h, consts, opacity, E, rho, T, E_bc, v=None, F=None, fr=None, f_edd=None,
+                 vfr=None, ptire=None, stream=None):
+    _check(lib().fld_coupling(h, C.byref(consts), C.byref(opacity), _ptr(E), _ptr(rho), _ptr(T),
+                              _ptr(E_bc), _ptr(v), _ptr(F), _ptr(fr), _ptr(f_edd), _ptr(vfr),
+                              _ptr(ptire), _stream(stream)), "fld_coupling")
 
 
 def fld_diffuse(h, dt, D, E_bc, E, stream=None, raise_on_error=True):
@@ -349,6 +358,11 @@ class Handle:
 
     def limiter(self, consts, opacity, E, rho, T, E_bc, D, lam=None, stream=None):
         fld_limiter(self.h, consts, opacity, E, rho, T, E_bc, D, lam, stream)
+
+    def coupling(self, consts, opacity, E, rho, T, E_bc, v=None, F=None, fr=None, f_edd=None,
+                 vfr=None, ptire=None, stream=None):
+        fld_coupling(self.h, consts, opacity, E, rho, T, E_bc, v, F, fr, f_edd, vfr, ptire,
+                     stream)
 
     def diffuse(self, dt, D, E_bc, E, stream=None, raise_on_error=True):
         return fld_diffuse(self.h, dt, D, E_bc, E, stream, raise_on_error)
