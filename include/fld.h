@@ -61,7 +61,7 @@ enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2 };
 /* opacity laws: kappa = kappa0 (CONST) or kappa0 rho^a_rho T^a_T (POWER) */
 enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_POWER = 1 };
 /* limiter: Levermore-Pomraning (Eq. fld_lambda) or the diffusion limit lambda = 1/3 */
-enum { FLD_LIMITER_LP = 0, FLD_LIMITER_DIFFUSION = 1 };
+enum { FLD_LIMITER_LP = 0, FLD_LIMITER_DIFFUSION = 1, FLD_LIMITER_MINERBO = 2 };
 /* solve precision:
    FP64      plain FP64 V-cycles;
    MIXED     FP32 V-cycles (smoothing, restriction, prolongation) inside iterative
@@ -99,7 +99,7 @@ typedef struct {
     int max_cycles;     /* V-cycle limit (outer refinement steps in MIXED)          */
     int nu1, nu2;       /* red-black Gauss-Seidel sweeps before / after coarse corr. */
     int coarse_sweeps;  /* red-black sweeps of the coarsest-level solve             */
-    int limiter;        /* FLD_LIMITER_LP or FLD_LIMITER_DIFFUSION                  */
+    int limiter;        /* FLD_LIMITER_LP, _DIFFUSION (lambda = 1/3) or _MINERBO    */
     int block;          /* threads per block of the row-mapped kernels (0 = default) */
     int smoother;       /* 0: in-place red and black half sweeps (levels with no odd
                            periodic extent; others as 1); 1: two out-of-place half

@@ -65,6 +65,16 @@ def lp_lambda(R):
     return (2.0 + R) / (6.0 + 3.0 * R + R * R)
 
 
+def minerbo_lambda(R):
+    """Minerbo's flux limiter, which the paper implements (Sect. 2) but does not print; the
+    published closed form: 2 / (3 + sqrt(9 + 12 R^2)) for R <= 3/2, else
+    1 / (1 + R + sqrt(1 + 2R))."""
+    R = np.asarray(R, dtype=float)
+    lo = 2.0 / (3.0 + np.sqrt(9.0 + 12.0 * R * R))
+    hi = 1.0 / (1.0 + R + np.sqrt(1.0 + 2.0 * R))
+    return np.where(R <= 1.5, lo, hi)
+
+
 def eddington_factor(lam, R):
     """Scalar Eddington factor f = lambda + lambda^2 R^2, Eq. fld_f."""
     return lam + lam * lam * R * R
@@ -125,7 +135,8 @@ def gradient5(E, h, bc, E_bc):
 def limiter(E, rho, T, h, bc, E_bc, c, op, mode=0):
     """Cell-centred D = c lambda / (kappa rho); returns (D, lambda, R).
 
-    mode 0: Levermore-Pomraning lambda(R); mode 1: diffusion limit lambda = 1/3.
+    mode 0: Levermore-Pomraning lambda(R); mode 1: diffusion limit lambda = 1/3;
+    mode 2: Minerbo lambda(R).
     """
     if np.any(~(E > 0)) or np.any(~(rho > 0)) or np.any(~(T > 0)):
         raise ValueError("E, rho and T must be positive and finite")
@@ -133,7 +144,12 @@ def limiter(E, rho, T, h, bc, E_bc, c, op, mode=0):
     g = gradient5(E, h, bc, E_bc)
     gnorm = np.sqrt(sum(gi * gi for gi in g))
     R = gnorm / (kappa * rho * E)
-    lam = lp_lambda(R) if mode == 0 else np.full(E.shape, 1.0 / 3.0)
+    if mode == 0:
+        lam = lp_lambda(R)
+    elif mode == 2:
+        lam = minerbo_lambda(R)
+    else:
+        lam = np.full(E.shape, 1.0 / 3.0)
     D = c * lam / (kappa * rho)
     return D, lam, R
 

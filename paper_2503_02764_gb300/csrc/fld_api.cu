@@ -171,7 +171,8 @@ bool fld::opts_valid(const fld_opts* o) {
                  o->precision == FLD_PREC_MIXED_DF) && o->tol > 0 &&
            o->max_cycles >= 1 && o->nu1 >= 0 && o->nu2 >= 0 && (o->nu1 + o->nu2) >= 1 &&
            o->coarse_sweeps >= 1 &&
-           (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION) &&
+           (o->limiter == FLD_LIMITER_LP || o->limiter == FLD_LIMITER_DIFFUSION ||
+            o->limiter == FLD_LIMITER_MINERBO) &&
            (o->block == 0 || (o->block >= 32 && o->block <= 1024 && o->block % 32 == 0)) &&
            (o->smoother >= 0 && o->smoother <= 2) &&
            (o->cluster == 0 || o->cluster == 1 || o->cluster == 2 || o->cluster == 4 ||
@@ -683,12 +684,12 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
                        double* lambda, void* stream) {
     if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho || !D) return FLD_ERR_ARG;
     if (op->kind == FLD_OPACITY_POWER && !T) return FLD_ERR_ARG;
-    if (has_dirichlet(h->g) && !E_bc && h->o.limiter == FLD_LIMITER_LP) return FLD_ERR_ARG;
+    if (has_dirichlet(h->g) && !E_bc && h->o.limiter != FLD_LIMITER_DIFFUSION) return FLD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     // double-FP32 mode: E split once into FP32 pairs (the level-0 FP32 buffers are free
     // until the solve), so the limiter forms the gradient without FP64 arithmetic
     const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF;
-    const bool split = dfmode && h->o.limiter == FLD_LIMITER_LP;
+    const bool split = dfmode && h->o.limiter != FLD_LIMITER_DIFFUSION;
     float* Eh = split ? h->d32[0].x : nullptr;
     float* El = split ? h->d32[0].tmp : nullptr;
     if (split)

@@ -159,6 +159,20 @@ __device__ __forceinline__ double fetch_E(const Lvl& L, const double* __restrict
     return v;
 }
 
+// Minerbo's limiter (the paper implements it but does not print it; the published closed
+// form): 2 / (3 + sqrt(9 + 12 R^2)) for R <= 3/2, 1 / (1 + R + sqrt(1 + 2R)) above; both
+// branches give 2/9 and the same slope at R = 3/2, and lambda R -> 1 as R -> infinity.
+__device__ __forceinline__ double minerbo_lambda(double R) {
+    return R <= 1.5 ? 2.0 / (3.0 + sqrt(fma(12.0 * R, R, 9.0)))
+                    : 1.0 / ((1.0 + R) + sqrt(fma(2.0, R, 1.0)));
+}
+
+__device__ __forceinline__ df minerbo_lambda_df(df R) {
+    if (R.hi <= 1.5f)
+        return df_div({2.f, 0.f}, df_add_f(df_sqrt(df_add_f(df_mul_f(df_mul(R, R), 12.f), 9.f)), 3.f));
+    return df_div({1.f, 0.f}, df_add(df_add_f(R, 1.f), df_sqrt(df_add_f(df_mul_f(R, 2.f), 1.f))));
+}
+
 // fetch_E from the double-FP32 split copy (Eh, El) of E: the same ghost rules, a Dirichlet
 // ghost 2 E_b - E_mirror formed in FP64 and split.
 __device__ __forceinline__ df fetch_Edf(const Lvl& L, const float* __restrict__ Eh,
@@ -258,7 +272,7 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
     if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t) && pos_finite(kap))) return false;
     const double kr = kap * r;
     double lm = 1.0 / 3.0;
-    if (mode == FLD_LIMITER_LP) {
+    if (mode != FLD_LIMITER_DIFFUSION) {
         double g2 = 0.0;
         for (int d = 0; d < L.ndim; ++d) {
             const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
@@ -272,14 +286,18 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
         if (in_f32_range(m) && (g2 == 0.0 || in_f32_range(g2))) {
             const double v = rcp_nr(m);
             const double R = g2 > 0.0 ? g2 * rsqrt_nr(g2, 2) * v : 0.0;
-            const double P = 2.0 + R, Q = fma(R, R + 3.0, 6.0);
-            const double rQ = in_f32_range(Q) ? rcp_nr(Q) : 1.0 / Q;
-            lmout = P * rQ;
+            if (mode == FLD_LIMITER_MINERBO) {
+                lmout = minerbo_lambda(R);
+            } else {
+                const double P = 2.0 + R, Q = fma(R, R + 3.0, 6.0);
+                const double rQ = in_f32_range(Q) ? rcp_nr(Q) : 1.0 / Q;
+                lmout = P * rQ;
+            }
             Dout = c * lmout * (Ec * v);
             return true;
         }
         const double R = sqrt(g2) / m;
-        lm = (2.0 + R) / (6.0 + 3.0 * R + R * R);
+        lm = mode == FLD_LIMITER_MINERBO ? minerbo_lambda(R) : (2.0 + R) / (6.0 + 3.0 * R + R * R);
     }
     lmout = lm;
     Dout = in_f32_range(kr) ? c * lm * rcp_nr(kr) : c * lm / kr;
@@ -369,7 +387,7 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
     const df m = df_mul(kr, Ed);
     if (!df_safe(m.hi)) return false;
     df lm = {0.33333334f, -9.9341077e-09f};   // 1/3 as a double-FP32 pair
-    if (mode == FLD_LIMITER_LP) {
+    if (mode != FLD_LIMITER_DIFFUSION) {
         df g2d = {0.f, 0.f};
         if (Eh) {
             // (E_-2 - 8 E_-1) + 8 E_+1 - E_+2 in double-word form (the factors 8 are exact)
@@ -413,9 +431,13 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
         if (g2d.hi > 0.f) {
             const df R = df_div(df_sqrt(g2d), m);
             if (!(R.hi < 1e12f)) return false;
-            const df P = df_add_f(R, 2.f);
-            const df Q = df_add_f(df_mul(R, df_add_f(R, 3.f)), 6.f);
-            lm = df_div(P, Q);
+            if (mode == FLD_LIMITER_MINERBO) {
+                lm = minerbo_lambda_df(R);
+            } else {
+                const df P = df_add_f(R, 2.f);
+                const df Q = df_add_f(df_mul(R, df_add_f(R, 3.f)), 6.f);
+                lm = df_div(P, Q);
+            }
         }
     }
     const df D = df_div(df_mul({K.c_h, K.c_l}, lm), kr);

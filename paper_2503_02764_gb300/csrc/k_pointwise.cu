@@ -160,8 +160,9 @@ __global__ void k_coupling(Lvl L, double3 inv12h, double3 inv12hv, const double*
             const double gn = sqrt(g2);
             const double kr = kap * r;
             const double R = gn / (kr * Ec);
-            const double lam = mode == FLD_LIMITER_LP ? (2.0 + R) / (6.0 + 3.0 * R + R * R)
-                                                      : 1.0 / 3.0;
+            const double lam = mode == FLD_LIMITER_LP        ? (2.0 + R) / (6.0 + 3.0 * R + R * R)
+                               : mode == FLD_LIMITER_MINERBO ? minerbo_lambda(R)
+                                                             : 1.0 / 3.0;
             const double D = c * lam / kr;
             const double f = lam + lam * lam * R * R;
             double vf = 0.0;
@@ -224,7 +225,7 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     const int block = 256;
     const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
     const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
-    if (!(use_df && mode == FLD_LIMITER_LP)) Eh = El = nullptr;
+    if (!(use_df && mode != FLD_LIMITER_DIFFUSION)) Eh = El = nullptr;
     k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, Eh, El, D,
                                    lam, err);
 }

@@ -15,7 +15,7 @@ LIBPATH = os.path.join(HERE, "libfld_gb300.so")
 FLD_OK, FLD_ERR_ARG, FLD_ERR_DOMAIN, FLD_ERR_NOT_CONVERGED, FLD_ERR_TIMEOUT, FLD_ERR_CUDA, \
     FLD_ERR_NOMEM = range(7)
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
-LIMITER_LP, LIMITER_DIFFUSION = 0, 1
+LIMITER_LP, LIMITER_DIFFUSION, LIMITER_MINERBO = 0, 1, 2
 
 
 class FldError(RuntimeError):

@@ -25,7 +25,7 @@ def _velocity(shape, seed):
 
 
 @pytest.mark.parametrize("cfg", [1, 2, 3])
-@pytest.mark.parametrize("limiter", [0, 1])
+@pytest.mark.parametrize("limiter", [0, 1, 2])
 def test_coupling_matches_oracle(cfg, limiter):
     torch = torch_cuda()
     fld = library()

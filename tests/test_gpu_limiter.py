@@ -41,7 +41,7 @@ def test_limiter_matches_oracle(shape, h, bc, op, precision):
     torch = torch_cuda()
     fld = library()
     E, rho, T, Eb = _fields(shape, bc, len(shape) * 100 + shape[-1])
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         hd = fld.Handle(shape, h, bc, limiter=mode, precision=precision)
         D = torch.empty(E.size, dtype=torch.float64, device="cuda")
         lam = torch.empty_like(D)

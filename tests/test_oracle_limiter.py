@@ -124,3 +124,35 @@ def test_limiter_rejects_nonpositive():
     E[3] = -1.0
     with pytest.raises(ValueError):
         O.limiter(E, np.ones(8), np.ones(8), (1.0,), ((0, 0),), {}, 1.0, (0, 1.0, 0, 0))
+
+
+def test_minerbo_limiter_pins():
+    # the published closed form: lambda(0) = 1/3; the two branches meet at R = 3/2 with the
+    # value 2/9 and the same slope; lambda R -> 1 as R -> infinity; lambda R < 1
+    assert O.minerbo_lambda(0.0) == pytest.approx(1.0 / 3.0, rel=1e-15)
+    lo = lambda R: 2.0 / (3.0 + np.sqrt(9.0 + 12.0 * R * R))
+    hi = lambda R: 1.0 / (1.0 + R + np.sqrt(1.0 + 2.0 * R))
+    assert lo(1.5) == pytest.approx(2.0 / 9.0, rel=1e-15)
+    assert hi(1.5) == pytest.approx(2.0 / 9.0, rel=1e-15)
+    eps = 1e-6
+    slope_lo = (lo(1.5) - lo(1.5 - eps)) / eps
+    slope_hi = (hi(1.5 + eps) - hi(1.5)) / eps
+    assert slope_lo == pytest.approx(slope_hi, rel=1e-4)
+    R = np.logspace(-6, 9, 500)
+    lam = O.minerbo_lambda(R)
+    assert np.all(lam * R < 1.0) and np.all(np.diff(lam) < 0)
+    assert abs(O.minerbo_lambda(1e9) * 1e9 - 1.0) < 1e-4
+    # both limiters agree at the two ends and differ in between
+    assert abs(O.minerbo_lambda(1e-8) - O.lp_lambda(1e-8)) < 1e-8
+    assert abs(O.minerbo_lambda(1.0) - O.lp_lambda(1.0)) > 1e-3
+
+
+def test_limiter_mode_minerbo_in_the_field():
+    rng = np.random.default_rng(4)
+    E = 1.0 + rng.uniform(0, 1, (6, 9))
+    rho = np.full(E.shape, 0.3)
+    T = np.ones(E.shape)
+    bc = ((0, 0), (1, 1))
+    D, lam, R = O.limiter(E, rho, T, (0.1, 0.1), bc, {}, 2.0, (0, 1.0, 0.0, 0.0), mode=2)
+    np.testing.assert_allclose(lam, O.minerbo_lambda(R), rtol=1e-15)
+    np.testing.assert_allclose(D, 2.0 * lam / 0.3, rtol=1e-15)
