@@ -103,10 +103,13 @@ typedef struct {
     int block;          /* threads per block of the row-mapped kernels (0 = default) */
     int smoother;       /* 0: in-place red and black half sweeps (levels with no odd
                            periodic extent; others as 1); 1: two out-of-place half
-                           sweeps; 2: the fused single-pass shared-memory sweep
-                           (2D/3D, nx >= 8; others as 1)                               */
-    int graph;          /* batched step: capture the step in a CUDA graph on the first
-                           call with given field pointers and replay it afterwards      */
+                           sweeps; 2: one z-marching pass per sweep (3D FP32 levels
+                           with nx a multiple of 4, nx >= 16, even periodic extents;
+                           others as 0). The levels from 8^3 cells down run in one
+                           single-block launch whatever the smoother.                  */
+    int graph;          /* single grid: replay the FP32 V-cycle from a CUDA graph
+                           captured on first use; batched step: capture the step on
+                           the first call with given field pointers and replay it       */
     int cluster;        /* batched step: blocks per problem (1, 2, 4 or 8, a thread-block
                            cluster when > 1); 0 = chosen from the largest problem      */
     int inner;          /* MIXED/MIXED_DF: FP32 V-cycles per refinement step (the later

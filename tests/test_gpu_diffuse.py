@@ -59,7 +59,7 @@ def _solve_gpu(fld, torch, shape, h, bc, dt, D, E, Eb, precision, tol=1e-14, smo
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10), (2, 1e-10)])
 @pytest.mark.parametrize("shape,h,bc,dt,sigma", CASES)
 def test_diffuse_matches_direct_solve(shape, h, bc, dt, sigma, precision, tol, smoother):
-    # smoother 0: in-place half sweeps, 1: out-of-place half sweeps, 2: fused single pass
+    # smoother 0: in-place half sweeps, 1: out-of-place half sweeps, 2: z-marching sweep
     torch = torch_cuda()
     fld = library()
     D, E, Eb = _problem(shape, bc, sigma, 17 + len(shape) + shape[0])
