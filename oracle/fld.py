@@ -46,13 +46,39 @@ PERIODIC, NEUMANN, DIRICHLET = 0, 1, 2
 
 
 # ----------------------------------------------------------------- opacity
+def opacity_table(kappa0, table, grid, rho, T):
+    """Tabulated opacity: kappa0 times 10 to the bilinear interpolant of log10 kappa.
+
+    The paper uses constant opacities and names opacity tables as the next step
+    (Sect. 5). Reading taken here: ``table[j, i]`` holds log10 kappa at
+    log10 rho = log_rho0 + i dlog_rho and log10 T = log_T0 + j dlog_T; a point is
+    located by its fractional grid coordinates, clamped to the table (outside it the
+    edge value holds), and log10 kappa is the bilinear interpolant of the four
+    surrounding nodes.
+    """
+    log_rho0, dlog_rho, log_T0, dlog_T = grid
+    n_T, n_rho = table.shape
+    x = np.clip((np.log10(rho) - log_rho0) / dlog_rho, 0.0, n_rho - 1.0)
+    y = np.clip((np.log10(T) - log_T0) / dlog_T, 0.0, n_T - 1.0)
+    i = np.minimum(np.floor(x).astype(np.int64), n_rho - 2)
+    j = np.minimum(np.floor(y).astype(np.int64), n_T - 2)
+    fx, fy = x - i, y - j
+    logk = ((1.0 - fx) * (1.0 - fy) * table[j, i] + fx * (1.0 - fy) * table[j, i + 1]
+            + (1.0 - fx) * fy * table[j + 1, i] + fx * fy * table[j + 1, i + 1])
+    return kappa0 * 10.0 ** logk
+
+
 def opacity(op, rho, T):
-    """kappa = kappa0 rho^a_rho T^a_T (constant when kind == 0).
+    """kappa = kappa0 rho^a_rho T^a_T (constant when kind == 0); kind 2 is a table
+    ``(2, kappa0, table, grid)`` read by ``opacity_table``.
 
     ``op = ("field", kappa)`` passes an already evaluated opacity through.
     """
     if op[0] == "field":
         return np.asarray(op[1])
+    if op[0] == 2:
+        return opacity_table(op[1], np.asarray(op[2]), op[3], np.asarray(rho, dtype=float),
+                             np.asarray(T, dtype=float))
     kind, kappa0, a_rho, a_T = op
     if kind == 0:
         return np.full(np.shape(rho), kappa0, dtype=np.asarray(rho).dtype)

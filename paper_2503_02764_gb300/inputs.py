@@ -30,7 +30,7 @@ import numpy as np
 
 SEED_BASE = 250302764
 PERIODIC, NEUMANN, DIRICHLET = 0, 1, 2
-OPACITY_CONST, OPACITY_POWER = 0, 1
+OPACITY_CONST, OPACITY_POWER, OPACITY_TABLE = 0, 1, 2
 LIMITER_LP, LIMITER_DIFFUSION = 0, 1
 
 
@@ -44,7 +44,8 @@ class Problem:
     a_r: float
     gamma: float
     R_gas: float
-    opacity: tuple          # (kind, kappa0, a_rho, a_T): kappa = kappa0 rho^a_rho T^a_T
+    opacity: tuple          # (kind, kappa0, a_rho, a_T): kappa = kappa0 rho^a_rho T^a_T, or
+                            # (OPACITY_TABLE, kappa0, log10 kappa table, grid): see opacity_table
     dt: float
     rho: np.ndarray
     T: np.ndarray
@@ -238,6 +239,40 @@ def linear_mode_3d(n=512, ratio=1.0, amp=1e-4, seed=None, ny=None, nz=None,
         bc=((PERIODIC, PERIODIC),) * 3, c=1.0e4, a_r=a_r, gamma=5.0 / 3.0, R_gas=1.0,
         opacity=(OPACITY_CONST, 1.0e4, 0.0, 0.0), dt=dt,
         rho=np.ones((nz, ny, nx)), T=T, E=E, tol=1e-10, steps=steps)
+
+
+def opacity_table(kappa0, log_rho=(-2.0, 0.3), log_T=(-0.1, 1.05), n_rho=24, n_T=30,
+                  bump=2.0, bump_logT=0.6, bump_width=0.1, noise=0.02, seed=None):
+    """A synthetic opacity table with the structure of tabulated stellar opacities.
+
+    log10 kappa on a uniform grid in (log10 rho, log10 T): a Kramers-like law
+    kappa0 rho T^-3.5, raised by a Gaussian bump in log10 T (factor 1 + bump at
+    its peak, the shape of the iron bump of real tables), plus seeded noise of
+    ``noise`` dex so that the table is not bilinear in the logs. Returns
+    (table, grid) with table[j, i] at log10 rho = log_rho0 + i dlog_rho,
+    log10 T = log_T0 + j dlog_T, and grid = (log_rho0, dlog_rho, log_T0, dlog_T).
+    """
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 91 if seed is None else seed))
+    lr = np.linspace(log_rho[0], log_rho[1], n_rho)
+    lt = np.linspace(log_T[0], log_T[1], n_T)
+    LR, LT = np.meshgrid(lr, lt, indexing="xy")          # (n_T, n_rho), rho fastest
+    table = (np.log10(kappa0) + LR - 3.5 * LT
+             + np.log10(1.0 + bump * np.exp(-0.5 * ((LT - bump_logT) / bump_width) ** 2))
+             + noise * rng.uniform(-1.0, 1.0, LR.shape))
+    grid = (float(lr[0]), float(lr[1] - lr[0]), float(lt[0]), float(lt[1] - lt[0]))
+    return np.ascontiguousarray(table), grid
+
+
+def stratified_3d_table(n=32, seed=None, nz=24, ny=20):
+    """The stratified box with a tabulated opacity in place of the power law: the
+    table of ``opacity_table`` built around the box's own Kramers coefficient. Its
+    density range stops above the box's lowest densities, so the top cells take
+    the table's edge values (clamped lookups)."""
+    P = stratified_3d(n, seed, nz=nz, ny=ny)
+    table, grid = opacity_table(P.opacity[1])
+    P.opacity = (OPACITY_TABLE, 1.0, table, grid)
+    P.name = P.name.replace("stratified3d", "stratified3d_table")
+    return P
 
 
 def random_cells(ncell, seed=0):
