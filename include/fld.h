@@ -58,8 +58,10 @@ typedef enum {
 
 /* boundary kinds, per axis side */
 enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2 };
-/* opacity laws: kappa = kappa0 (CONST) or kappa0 rho^a_rho T^a_T (POWER) */
-enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_POWER = 1 };
+/* opacity laws: kappa = kappa0 (CONST), kappa0 rho^a_rho T^a_T (POWER), or kappa0 times
+   10 to a bilinear interpolant of a table of log10 kappa over (log10 rho, log10 T) (TABLE;
+   the paper uses constant opacities and names tables as the next step, Sect. 5) */
+enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_POWER = 1, FLD_OPACITY_TABLE = 2 };
 /* limiter: Levermore-Pomraning (Eq. fld_lambda) or the diffusion limit lambda = 1/3 */
 enum { FLD_LIMITER_LP = 0, FLD_LIMITER_DIFFUSION = 1, FLD_LIMITER_MINERBO = 2 };
 /* solve precision:
@@ -90,7 +92,25 @@ typedef struct {
     int bc_lo[3], bc_hi[3];
 } fld_grid;
 
-typedef struct { int kind; double kappa0, a_rho, a_T; } fld_opacity;
+/* Opacity law, read on the host at each call (kappa0 > 0 and finite in every kind).
+   POWER uses a_rho and a_T. TABLE uses the table fields:
+     table     device array of n_rho * n_T float64, caller-owned, read by the call's
+               kernels (keep it alive and unchanged until they finish): log10 kappa at
+               log10 rho = log_rho0 + i dlog_rho, log10 T = log_T0 + j dlog_T stored at
+               [j * n_rho + i] (rho fastest);
+     n_rho, n_T >= 2 with n_rho * n_T < 2^31; dlog_rho, dlog_T > 0, all four finite.
+   A cell's (log10 rho, log10 T) is clamped to the table's range (outside it the edge
+   values hold) and log10 kappa interpolated bilinearly between the four nodes around
+   it, in FP64. TABLE is taken by fld_limiter, fld_coupling, fld_exchange and fld_step
+   (which then read T); fld_step_batched returns FLD_ERR_ARG for it. The other kinds
+   ignore the table fields (zero them). */
+typedef struct {
+    int kind;
+    double kappa0, a_rho, a_T;
+    const double* table;
+    int n_rho, n_T;
+    double log_rho0, dlog_rho, log_T0, dlog_T;
+} fld_opacity;
 
 /* Solver options; fld_default_opts fills sensible values. */
 typedef struct {
@@ -143,7 +163,8 @@ fld_status fld_destroy(fld_handle* h);
 fld_status fld_set_opts(fld_handle* h, const fld_opts* o);
 
 /* Limiter (Eqs. fld_R, fld_lambda, fld_F; Sect. 3 gradient).
-   In:  E, rho, T (device, ncell float64 each; T is only read by a POWER opacity),
+   In:  E, rho, T (device, ncell float64 each; T is only read by a POWER or TABLE
+        opacity and may be NULL for a CONST one),
         E_bc (device float64, may be NULL when no side is Dirichlet): the
         Dirichlet face values packed side after side in the order x-lo, x-hi,
         y-lo, y-hi, z-lo, z-hi (Dirichlet sides only), each face row-major over

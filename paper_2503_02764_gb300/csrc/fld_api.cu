@@ -188,13 +188,36 @@ Opacity to_op(const fld_opacity* op) {
     o.kappa0 = op->kappa0;
     o.a_rho = op->a_rho;
     o.a_T = op->a_T;
+    o.tab = nullptr;
+    o.nr = o.nt = 0;
+    o.lr0 = o.ilr = o.lt0 = o.ilt = 0.0;
+    if (op->kind == FLD_OPACITY_TABLE) {
+        o.a_rho = o.a_T = 0.0;
+        o.tab = op->table;
+        o.nr = op->n_rho;
+        o.nt = op->n_T;
+        o.lr0 = op->log_rho0;
+        o.ilr = 1.0 / op->dlog_rho;
+        o.lt0 = op->log_T0;
+        o.ilt = 1.0 / op->dlog_T;
+    }
     return o;
 }
 
+bool table_ok(const fld_opacity* op) {
+    return op->table && op->n_rho >= 2 && op->n_T >= 2 &&
+           (long long)op->n_rho * op->n_T < (1LL << 31) && op->dlog_rho > 0 &&
+           op->dlog_T > 0 && std::isfinite(op->dlog_rho) && std::isfinite(op->dlog_T) &&
+           std::isfinite(op->log_rho0) && std::isfinite(op->log_T0) &&
+           std::isfinite(1.0 / op->dlog_rho) && std::isfinite(1.0 / op->dlog_T);
+}
+
 bool op_ok(const fld_opacity* op) {
-    return op && (op->kind == FLD_OPACITY_CONST || op->kind == FLD_OPACITY_POWER) &&
-           op->kappa0 > 0 && std::isfinite(op->kappa0) && std::isfinite(op->a_rho) &&
-           std::isfinite(op->a_T);
+    if (!op || !(op->kappa0 > 0) || !std::isfinite(op->kappa0)) return false;
+    if (op->kind == FLD_OPACITY_CONST) return true;
+    if (op->kind == FLD_OPACITY_POWER)
+        return std::isfinite(op->a_rho) && std::isfinite(op->a_T);
+    return op->kind == FLD_OPACITY_TABLE && table_ok(op);
 }
 
 bool consts_ok(const fld_consts* k) {
@@ -683,7 +706,7 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
                        const double* rho, const double* T, const double* E_bc, double* D,
                        double* lambda, void* stream) {
     if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho || !D) return FLD_ERR_ARG;
-    if (op->kind == FLD_OPACITY_POWER && !T) return FLD_ERR_ARG;
+    if (op->kind != FLD_OPACITY_CONST && !T) return FLD_ERR_ARG;
     if (has_dirichlet(h->g) && !E_bc && h->o.limiter != FLD_LIMITER_DIFFUSION) return FLD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     // double-FP32 mode: E split once into FP32 pairs (the level-0 FP32 buffers are free
@@ -707,7 +730,7 @@ fld_status fld_coupling(fld_handle* h, const fld_consts* k, const fld_opacity* o
                         const double* v, double* F, double* fr, double* f_edd, double* vfr,
                         double* ptire, void* stream) {
     if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho) return FLD_ERR_ARG;
-    if (op->kind == FLD_OPACITY_POWER && !T) return FLD_ERR_ARG;
+    if (op->kind != FLD_OPACITY_CONST && !T) return FLD_ERR_ARG;
     if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
     if ((vfr || ptire) && !v) return FLD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -218,6 +218,7 @@ fld_status fld_step_batched(fld_batch* b, const fld_consts* k, const fld_opacity
             !(ops[p].kappa0 > 0))
             return FLD_ERR_ARG;
         b->hdyn[p].dt = dt[p];
+        b->hdyn[p].op = Opacity{};
         b->hdyn[p].op.kind = ops[p].kind;
         b->hdyn[p].op.kappa0 = ops[p].kappa0;
         b->hdyn[p].op.a_rho = ops[p].a_rho;

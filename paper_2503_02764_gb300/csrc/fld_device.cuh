@@ -259,6 +259,7 @@ __device__ __forceinline__ double exchange_root(double alpha, double beta, doubl
 // 4th-order difference. With v = 1/(kappa rho E), D = c lambda E v: two reciprocals and
 // one square root, by FP32-seeded Newton-Raphson where the operands allow it (FP64
 // issues at a small fraction of the FP32 rate). Returns false on a domain error.
+template <bool kTables = true>
 __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
                                              const double* __restrict__ E,
                                              const double* __restrict__ rho,
@@ -268,7 +269,7 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
                                              int k, long long p, double& Dout, double& lmout) {
     const double Ec = E[p], r = rho[p];
     const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
-    const double kap = opacity_eval(op, r, t);
+    const double kap = opacity_eval<kTables>(op, r, t);
     if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t) && pos_finite(kap))) return false;
     const double kr = kap * r;
     double lm = 1.0 / 3.0;
@@ -308,10 +309,11 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
 // Backward Euler on de/dt = +qdot, dE/dt = -qdot (Eqs. heating, qdot) with kappa from
 // (rho, T on entry): solves alpha T' + beta T'^4 = q (exchange_root) and sets
 // E' = (E + chi a_r T'^4)/(1 + chi). Returns false (cell unchanged) on a domain error.
+template <bool kTables = true>
 __device__ __forceinline__ bool exchange_cell(double r, double& t, double& er, const Opacity& op,
                                               double dtc, double a_r, double cv) {
     if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) return false;
-    const double kap = opacity_eval(op, r, t);
+    const double kap = opacity_eval<kTables>(op, r, t);
     if (!pos_finite(kap)) return false;
     const double chi = dtc * kap * r;
     const double alpha = r * cv;
@@ -345,7 +347,7 @@ __device__ __forceinline__ bool df_opacity(const Opacity& op, const DfConst& K, 
         kap = k0;
         return true;
     }
-    if (op.a_rho != 1.0 || op.a_T != -3.5) return false;
+    if (op.kind != FLD_OPACITY_POWER || op.a_rho != 1.0 || op.a_T != -3.5) return false;
     const df y = df_rsqrt(T);                 // T^-1/2
     const df y2 = df_mul(y, y);
     const df y7 = df_mul(df_mul(df_mul(y2, y2), y2), y);

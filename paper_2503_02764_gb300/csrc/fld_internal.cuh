@@ -35,6 +35,9 @@ __host__ __device__ __forceinline__ float wgt<float>(const Lvl& L, int d) { retu
 struct Opacity {
     int kind;
     double kappa0, a_rho, a_T;
+    const double* tab;           // TABLE: log10 kappa, [j * nr + i]
+    int nr, nt;
+    double lr0, ilr, lt0, ilt;   // first node and inverse spacing in log10 rho, log10 T
 };
 
 // v > 0 and finite, tested on the bit pattern (integer pipe, not the FP64 one).
@@ -71,8 +74,34 @@ __device__ __forceinline__ bool in_f32_range(double v) {
     return e > -100 && e < 99;
 }
 
+// kappa0 10^(bilinear interpolant of the log10 kappa table) at (log10 rho, log10 T), the
+// coordinates clamped to the table; fmax/fmin also send a NaN coordinate to the first
+// node, so every read stays inside the nr x nt array (nr, nt >= 2 on the host). Out of
+// line, with scalar arguments, so the kernels' register allocation for the other laws
+// is what it is without tables.
+static __device__ __noinline__ double opacity_table(const double* __restrict__ tab, int nr,
+                                                    int nt, double lr0, double ilr, double lt0,
+                                                    double ilt, double kappa0, double rho,
+                                                    double T) {
+    double x = (log10(rho) - lr0) * ilr;
+    double y = (log10(T) - lt0) * ilt;
+    x = fmin(fmax(x, 0.0), (double)(nr - 1));
+    y = fmin(fmax(y, 0.0), (double)(nt - 1));
+    const int i = min((int)x, nr - 2), j = min((int)y, nt - 2);
+    const double fx = x - i, fy = y - j;
+    const double* t = tab + (long long)j * nr + i;
+    const double lo = fma(fx, t[1] - t[0], t[0]);
+    const double hi = fma(fx, t[nr + 1] - t[nr], t[nr]);
+    return kappa0 * exp10(fma(fy, hi - lo, lo));
+}
+
+// kTables = false compiles the table law out (callers that never receive it)
+template <bool kTables = true>
 __device__ __forceinline__ double opacity_eval(const Opacity& op, double rho, double T) {
     if (op.kind == FLD_OPACITY_CONST) return op.kappa0;
+    if (kTables && op.kind == FLD_OPACITY_TABLE)
+        return opacity_table(op.tab, op.nr, op.nt, op.lr0, op.ilr, op.lt0, op.ilt, op.kappa0,
+                             rho, T);
     const double fr = (op.a_rho == 1.0) ? rho : pow(rho, op.a_rho);
     double ft;
     if (op.a_T == 0.0) {

@@ -392,7 +392,8 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
             double Dv = 0.0, lm;
             if (!limiter_cell_df(L0, ih, E_, r_, T_, eb, bo, op, KC, prm.limiter, i, j, k, p, Dv,
                                  lm) &&
-                !limiter_cell(L0, ih, E_, r_, T_, eb, bo, op, prm.c, prm.limiter, i, j, k, p, Dv, lm))
+                !limiter_cell<false>(L0, ih, E_, r_, T_, eb, bo, op, prm.c, prm.limiter, i, j, k,
+                                     p, Dv, lm))
                 bad += 1.0;
             D[p] = Dv;
         }
@@ -482,7 +483,7 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
                 if (!exchange_cell_df(r_[p], t, e_new, op, KC)) {
                     t = T_[p];
                     e_new = e_sol;
-                    exchange_cell(r_[p], t, e_new, op, dtc, prm.a_r, prm.cv);
+                    exchange_cell<false>(r_[p], t, e_new, op, dtc, prm.a_r, prm.cv);
                 }
                 T_[p] = t;
                 E_[p] = e_new;

@@ -16,6 +16,7 @@ FLD_OK, FLD_ERR_ARG, FLD_ERR_DOMAIN, FLD_ERR_NOT_CONVERGED, FLD_ERR_TIMEOUT, FLD
     FLD_ERR_NOMEM = range(7)
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
 LIMITER_LP, LIMITER_DIFFUSION, LIMITER_MINERBO = 0, 1, 2
+OPACITY_CONST, OPACITY_POWER, OPACITY_TABLE = 0, 1, 2
 
 
 class FldError(RuntimeError):
@@ -34,7 +35,10 @@ class fld_grid(C.Structure):
 
 
 class fld_opacity(C.Structure):
-    _fields_ = [("kind", C.c_int), ("kappa0", C.c_double), ("a_rho", C.c_double), ("a_T", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("kappa0", C.c_double), ("a_rho", C.c_double), ("a_T", C.c_double),
+                ("table", C.c_void_p), ("n_rho", C.c_int), ("n_T", C.c_int),
+                ("log_rho0", C.c_double), ("dlog_rho", C.c_double), ("log_T0", C.c_double),
+                ("dlog_T", C.c_double)]
 
 
 class fld_opts(C.Structure):
@@ -169,9 +173,24 @@ def make_consts(c, a_r, gamma, R_gas):
     return fld_consts(c, a_r, gamma, R_gas)
 
 
-def make_opacity(op):
-    kind, k0, ar, at = op
-    return fld_opacity(int(kind), float(k0), float(ar), float(at))
+def make_opacity(op, table=None):
+    """fld_opacity from (kind, kappa0, a_rho, a_T), or for a table from
+    (OPACITY_TABLE, kappa0, log10 kappa array (n_T, n_rho), (log_rho0, dlog_rho, log_T0, dlog_T))
+    with ``table`` the same values on the device (contiguous float64; the returned
+    structure keeps a reference to it)."""
+    kind = int(op[0])
+    if kind != OPACITY_TABLE:
+        _, k0, ar, at = op
+        return fld_opacity(kind, float(k0), float(ar), float(at))
+    _, k0, host_table, grid = op
+    n_T, n_rho = host_table.shape
+    if table is None or table.numel() != n_rho * n_T:
+        raise FldError(FLD_ERR_ARG, "make_opacity: a table opacity needs its device table "
+                       "(n_T x n_rho float64)")
+    o = fld_opacity(kind, float(k0), 0.0, 0.0, _ptr(table), int(n_rho), int(n_T),
+                    *(float(g) for g in grid))
+    o._table = table
+    return o
 
 
 def stats_dict(st):
