@@ -14,7 +14,7 @@ roofline the dominant kernel's algorithmic bytes per launch / its event-timed
          launch duration, against the measured copy bandwidth
 cpu_baseline  the CPU oracle on a bounded sample of the same workload (rank 0)
 
---impl reference times that CPU oracle alone (the comparison arm for this build).
+--impl reference times that CPU oracle alone (the comparison arm).
 Multi-GPU: each rank solves its own independent replica (no data-path collective).
 """
 from __future__ import annotations
