@@ -42,3 +42,37 @@ def test_host_validation_without_gpu():
     assert L.fld_create(ctypes.byref(h), ctypes.byref(g),
                         ctypes.byref(fld.make_opts(nu1=0, nu2=0))) == fld.FLD_ERR_ARG
     assert fld.strerror(fld.FLD_ERR_NOT_CONVERGED).startswith("multigrid")
+
+
+def test_binding_structs_match_header_layout():
+    # every ctypes mirror has the size and field offsets the C compiler gives the header's
+    # struct (a wrong layout would pass garbage to the library without any error)
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2503_02764_gb300 import build, fld
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [fld.fld_consts, fld.fld_grid, fld.fld_opacity, fld.fld_opts, fld.fld_stats,
+               fld.fld_prof_entry, fld.fld_batch_stat]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fld.h"', "int main(void) {"]
+    for s in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s.__name__, s.__name__))
+        for name, *_ in s._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));'
+                         % (s.__name__, name, s.__name__, name))
+    lines.append("return 0; }")
+    os.makedirs(build.BUILD, exist_ok=True)
+    src = os.path.join(build.BUILD, "abi_layout.c")
+    exe = os.path.join(build.BUILD, "abi_layout")
+    with open(src, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([exe], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for s in structs:
+        assert int(got[s.__name__]) == ctypes.sizeof(s), s.__name__
+        for name, *_ in s._fields_:
+            assert int(got["%s.%s" % (s.__name__, name)]) == getattr(s, name).offset, (s, name)
