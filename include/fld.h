@@ -317,6 +317,57 @@ long long fld_launch_count(void);
 fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, double dt, const double* D,
                               const double* E_bc, double* E, fld_stats* stats, void* stream);
 
+/* ---------------------------------------------------------------- 1D RMHD wave step
+   One step of the one-dimensional radiation-MHD problem of the paper's linear-wave tests
+   (Sect. 4.3) with the scheme of Sect. 3, for the travelling radiation-damped waves:
+   1. the hyperbolic terms (left-hand sides of Eqs. mhd_mass, mhd_mom, mhd_energy,
+      mhd_mag and the advection term of Eq. mhd_r_e) plus the explicit coupling terms
+      (radiation force f_r = -lambda grad E, its work v . f_r, photon tiring P : grad v,
+      as fld_coupling computes them) by the three-stage SSP Runge-Kutta scheme of Shu and
+      Osher, with HLL interface fluxes (signal speeds v_x -+ the gas fast magnetosonic
+      speed) and third-order WENO reconstruction (Jiang-Shu weights, epsilon 1e-6 on
+      smoothness indicators divided by the largest square of the stencil's four cells)
+      of the primitive variables;
+   2. the FLD substep (as fld_step: limiter, backward-Euler diffusion, implicit exchange)
+      on (rho, T_g = p / (rho R_gas), E); the exchange's change of T_g is added to the
+      total gas energy.
+   Units are the caller's; the magnetic field is in Heaviside-Lorentz form (magnetic
+   pressure B^2/2) with B_x constant.
+   State U: caller-owned device float64 array [8][n] (variable-major): rho, rho v_x,
+   rho v_y, rho v_z, B_y, B_z, e (total gas energy: p/(gamma-1) + rho v^2/2 + B^2/2), E.
+   Boundaries: the first n_driven cells and the two left ghost cells take the driving
+   wave W0 + hat sin(k x - omega t) (primitive variables rho, v_x, v_y, v_z, B_y, B_z, p,
+   E; cell centres x = (i + 1/2) dx) at every Runge-Kutta stage and after the substep;
+   on the right, zero gradient for every variable and a Dirichlet face value E_right
+   for E in the diffusion solve and the gradient; E's gradient takes an even mirror on
+   the left. */
+typedef struct {
+    int n;                      /* cells, >= 8                                          */
+    int n_driven;               /* driven cells at the left end, 0 .. n - 4            */
+    double dx, gamma, Bx, R_gas;
+    fld_consts consts;          /* c, a_r (gamma and R_gas as above)                    */
+    fld_opacity opacity;
+    double E_right;             /* Dirichlet face value of E on the right, > 0           */
+    double W0[8], hat[8];       /* driving wave, primitive variables                    */
+    double k, omega;
+    fld_opts opts;              /* options of the FLD substep (limiter, precision, tol)  */
+} fld_wave1d_params;
+
+typedef struct fld_wave1d fld_wave1d;
+
+/* Allocates the 1D FLD handle and the step's device scratch (about 30 n doubles). */
+fld_status fld_wave1d_create(fld_wave1d** w, const fld_wave1d_params* p);
+fld_status fld_wave1d_destroy(fld_wave1d* w);
+/* cfl dx / max_i (|v_x| + c_f) over the cells of U (device); synchronises `stream`. */
+fld_status fld_wave1d_max_dt(fld_wave1d* w, const double* U, double cfl, double* dt,
+                             void* stream);
+/* Advances U (device, in place) from t to t + dt. Returns after the step has finished on
+   `stream`, with fld_step's status (FLD_ERR_NOT_CONVERGED when the diffusion solve
+   stopped at max_cycles: the step is still completed; FLD_ERR_DOMAIN when a cell left
+   the physical domain: U holds the stage where it happened). stats may be NULL. */
+fld_status fld_wave1d_step(fld_wave1d* w, double* U, double t, double dt, fld_stats* stats,
+                           void* stream);
+
 /* Static string for a status code. */
 const char* fld_strerror(fld_status s);
 

@@ -144,64 +144,36 @@ def diffuse_1d(E, D, h, bc, E_bc, dt):
 
 
 class Wave:
-    """A driven wave in a uniform radiative-equilibrium background
-    (``oracle.dispersion.background``), on n_cells cells over n_wavelengths wavelengths.
+    """The oracle's run of a driven 1D wave problem (``inputs.wave1d``: background, grid
+    and driving wave of Sect. 4.3). The driven cells and the left ghost cells hold the
+    problem's W0 + hat sin(k x - omega t) at every stage. With ``problem.radiation``
+    False the coupling terms and the FLD substep are off (ideal MHD)."""
 
-    kind "fast" or "slow": the ideal-MHD magnetosonic wave of Sect. 4.3 (Eqs.
-    cfast_pert_v_x .. cfast_pert_B_z) with the isothermal sound speed in the magnetosonic
-    speed and p_1 = (p_0/rho_0) rho_1, so that T_g, and with it E, is unperturbed:
-    rho_1 = amp rho_0 sin(k x - omega t). With ``radiation=False`` the coupling terms and
-    the FLD substep are off and the driving wave uses the adiabatic sound speed (an
-    ideal-MHD eigenmode). kind "alfven": omega/k = v_Ax, v_y1 = amp v_Ax sin(k x - omega t),
-    B_y1 = -(B_x k/omega) v_y1 (Eqs. alfven_pert_v_y, alfven_pert_B_y).
-    """
-
-    def __init__(self, bg, n_cells, n_wavelengths, kind="fast", amp=1e-2, cfl=0.8, mode=0,
-                 radiation=True):
-        self.bg = bg
-        self.gamma = bg["gamma"]
-        self.R_gas = Disp.K_B / (bg["mu"] * Disp.M_P)
-        self.c, self.a_r = bg["c"], bg["a_r"]
-        self.Bx = bg["B"][0]
-        self.k = bg["k"]
-        self.lam = 2.0 * np.pi / self.k
-        self.n = n_cells
-        self.nw = n_wavelengths
-        self.dx = n_wavelengths * self.lam / n_cells
-        self.x = (np.arange(n_cells) + 0.5) * self.dx
+    def __init__(self, problem, cfl=0.8, mode=0):
+        P = problem
+        self.P = P
+        self.gamma = P.gamma
+        self.R_gas = P.R_gas
+        self.c, self.a_r = P.c, P.a_r
+        self.Bx = P.Bx
+        self.k = P.k
+        self.lam = P.lam
+        self.n = P.n
+        self.nw = P.n_wavelengths
+        self.dx = P.dx
+        self.x = P.x
         self.cfl = cfl
         self.mode = mode
-        self.radiation = radiation
-        self.op = (0, bg["kappa"], 0.0, 0.0)          # constant opacity
+        self.radiation = P.radiation
+        self.op = (0, P.kappa, 0.0, 0.0)          # constant opacity
         self.bcE = ((F.NEUMANN, F.DIRICHLET),)
-        self.E_bc = {(0, 1): np.array(bg["E0"])}
-        r0, p0 = bg["rho0"], bg["p0"]
-        Bx, By, Bz = bg["B"]
-        vax2 = Bx * Bx / r0
-        hat = np.zeros(NV)
-        if kind == "alfven":
-            cw = np.sqrt(vax2)
-            hat[VY] = amp * cw
-            hat[BY] = -(Bx / cw) * hat[VY]
-        else:
-            fast = kind == "fast"
-            if radiation:
-                cw = Disp.magnetosonic_speed(bg, fast=fast, isothermal=True)
-                cg2 = p0 / r0
-            else:
-                cw = Disp.magnetosonic_speed(bg, fast=fast, isothermal=False)
-                cg2 = self.gamma * p0 / r0
-            hat[RHO] = amp * r0
-            hat[VX] = cw * amp
-            hat[VZ] = (Bz / Bx) * cw / (1.0 - cw * cw / vax2) * amp
-            hat[BZ] = Bz / (1.0 - vax2 / (cw * cw)) * amp
-            hat[PG] = cg2 * hat[RHO]
-        self.kind = kind
-        self.phase_speed = cw
-        self.omega = self.k * cw
-        self.hat = hat
-        self.W0 = np.array([r0, 0.0, 0.0, 0.0, By, Bz, p0, bg["E0"]])
-        self.driven = self.x < self.lam
+        self.E_bc = {(0, 1): np.array(P.E0)}
+        self.kind = P.kind
+        self.phase_speed = P.phase_speed
+        self.omega = P.omega
+        self.hat = np.asarray(P.hat, dtype=float)
+        self.W0 = np.asarray(P.W0, dtype=float)
+        self.driven = np.arange(P.n) < P.n_driven
 
     def analytic(self, x, t):
         return self.W0[:, None] + self.hat[:, None] * np.sin(self.k * x - self.omega * t)[None, :]

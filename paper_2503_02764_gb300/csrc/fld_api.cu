@@ -92,6 +92,8 @@ int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl) {
     }
     return nl;
 }
+// launches made outside this file's launch wrapper (the wave step's kernels)
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace fld
 
 struct fld_handle {

@@ -129,6 +129,7 @@ inline void split_host(double v, float& h, float& l) {
 // ----------------------------------------------------------------- host helpers
 int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl);
 bool grid_valid(const fld_grid* g);
+void note_launches(long long n);   // adds to fld_launch_count
 bool opts_valid(const fld_opts* o);
 
 // ----------------------------------------------------------------- launchers

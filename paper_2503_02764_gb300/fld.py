@@ -62,6 +62,14 @@ class fld_batch_stat(C.Structure):
     _fields_ = [("cycles", C.c_int), ("rel_resid", C.c_double), ("rel_resid0", C.c_double)]
 
 
+class fld_wave1d_params(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_driven", C.c_int), ("dx", C.c_double), ("gamma", C.c_double),
+                ("Bx", C.c_double), ("R_gas", C.c_double), ("consts", fld_consts),
+                ("opacity", fld_opacity), ("E_right", C.c_double), ("W0", C.c_double * 8),
+                ("hat", C.c_double * 8), ("k", C.c_double), ("omega", C.c_double),
+                ("opts", fld_opts)]
+
+
 _lib = None
 P = C.c_void_p
 H = C.c_void_p
@@ -105,6 +113,10 @@ def lib():
                                        P]),
         "fld_diffuse_static": (C.c_int, [C.POINTER(fld_grid), C.POINTER(fld_opts), C.c_double, P,
                                          P, P, C.POINTER(fld_stats), P]),
+        "fld_wave1d_create": (C.c_int, [C.POINTER(H), C.POINTER(fld_wave1d_params)]),
+        "fld_wave1d_destroy": (C.c_int, [H]),
+        "fld_wave1d_max_dt": (C.c_int, [H, P, C.c_double, C.POINTER(C.c_double), P]),
+        "fld_wave1d_step": (C.c_int, [H, P, C.c_double, C.c_double, C.POINTER(fld_stats), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -400,3 +412,79 @@ class Handle:
 
     def prof_read(self, cap=256):
         return fld_prof_read(self.h, cap)
+
+
+# ------------------------------------------------ 1D radiation-MHD wave step
+def fld_wave1d_create(params):
+    w = H()
+    _check(lib().fld_wave1d_create(C.byref(w), C.byref(params)), "fld_wave1d_create")
+    return w
+
+
+def fld_wave1d_destroy(w):
+    _check(lib().fld_wave1d_destroy(w), "fld_wave1d_destroy")
+
+
+def fld_wave1d_max_dt(w, U, cfl, stream=None):
+    dt = C.c_double()
+    _check(lib().fld_wave1d_max_dt(w, _ptr(U), float(cfl), C.byref(dt), _stream(stream)),
+           "fld_wave1d_max_dt")
+    return dt.value
+
+
+def fld_wave1d_step(w, U, t, dt, stream=None, raise_on_error=True):
+    st = fld_stats()
+    rc = lib().fld_wave1d_step(w, _ptr(U), float(t), float(dt), C.byref(st), _stream(stream))
+    if raise_on_error and rc not in (FLD_OK, FLD_ERR_NOT_CONVERGED):
+        _check(rc, "fld_wave1d_step")
+    return stats_dict(st) | {"status": rc}
+
+
+def make_wave1d_params(problem, **opts):
+    """fld_wave1d_params from a 1D wave problem (attributes n, n_driven, dx, gamma, Bx,
+    R_gas, c, a_r, kappa, E0, W0, hat, k, omega) and the FLD substep's options."""
+    p = fld_wave1d_params()
+    p.n, p.n_driven = int(problem.n), int(problem.n_driven)
+    p.dx, p.gamma, p.Bx, p.R_gas = (float(problem.dx), float(problem.gamma), float(problem.Bx),
+                                    float(problem.R_gas))
+    p.consts = make_consts(problem.c, problem.a_r, problem.gamma, problem.R_gas)
+    p.opacity = make_opacity((OPACITY_CONST, problem.kappa, 0.0, 0.0))
+    p.E_right = float(problem.E0)
+    for v in range(8):
+        p.W0[v] = float(problem.W0[v])
+        p.hat[v] = float(problem.hat[v])
+    p.k, p.omega = float(problem.k), float(problem.omega)
+    p.opts = make_opts(**opts)
+    return p
+
+
+class Wave1D:
+    """Owns an fld_wave1d: the 1D radiation-MHD step on a caller's state U (device
+    float64 [8][n])."""
+
+    def __init__(self, problem, **opts):
+        self.params = make_wave1d_params(problem, **opts)
+        self.n = self.params.n
+        self.w = fld_wave1d_create(self.params)
+
+    def _state(self, U):
+        if U.numel() != 8 * self.n:
+            raise ValueError("the state must hold 8 x n float64 values")
+        return U
+
+    def max_dt(self, U, cfl, stream=None):
+        return fld_wave1d_max_dt(self.w, self._state(U), cfl, stream)
+
+    def step(self, U, t, dt, stream=None, raise_on_error=True):
+        return fld_wave1d_step(self.w, self._state(U), t, dt, stream, raise_on_error)
+
+    def close(self):
+        if self.w:
+            fld_wave1d_destroy(self.w)
+            self.w = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

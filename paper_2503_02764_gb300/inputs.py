@@ -275,6 +275,92 @@ def stratified_3d_table(n=32, seed=None, nz=24, ny=20):
     return P
 
 
+# CGS constants of the radiation-MHD wave recipes
+C_LIGHT = 2.99792458e10
+K_B = 1.380649e-16
+M_P = 1.67262192e-24
+SIGMA_SB = 5.670374e-5
+A_RAD = 4.0 * SIGMA_SB / C_LIGHT
+
+
+@dataclass
+class Wave1D:
+    """A driven 1D wave problem (the linear-wave tests of Sect. 4.3), CGS units, the
+    magnetic field in Heaviside-Lorentz form (B_gauss / sqrt(4 pi)). W0 and hat are the
+    background and the driving amplitudes of the primitive variables (rho, v_x, v_y,
+    v_z, B_y, B_z, p, E); the driven cells hold W0 + hat sin(k x - omega t)."""
+    name: str
+    n: int
+    n_wavelengths: int
+    dx: float
+    lam: float
+    k: float
+    omega: float
+    phase_speed: float
+    gamma: float
+    mu: float
+    Bx: float
+    R_gas: float
+    c: float
+    a_r: float
+    kappa: float
+    E0: float
+    W0: np.ndarray
+    hat: np.ndarray
+    n_driven: int
+    kind: str
+    radiation: bool
+
+    @property
+    def x(self):
+        return (np.arange(self.n) + 0.5) * self.dx
+
+
+def wave1d(background, n_cells, n_wavelengths, kind="fast", amp=1e-2, radiation=True):
+    """The Sect. 4.3 wave set-up on n_cells cells over n_wavelengths wavelengths.
+
+    ``background``: rho0, p0, B0_gauss, gamma, mu, kappa, tau (optical depth per
+    wavelength), as printed for the weakly and strongly radiative cases. T0 from the ideal
+    gas law, E0 = a_r T0^4 (radiative equilibrium), lambda_w = tau / (kappa rho0).
+    kind "fast"/"slow": the magnetosonic wave with omega/k the ideal-MHD speed built from
+    the isothermal sound speed (the adiabatic one when ``radiation`` is False), rho_1 =
+    amp rho0, v_x1 = (omega/k) amp, p_1 = c_s^2 rho_1 with that sound speed, v_z1 and B_z1
+    from the transverse balance (Sect. 4.3), E_1 = 0. kind "alfven": omega/k = v_Ax,
+    v_y1 = amp v_Ax, B_y1 = -(B_x k / omega) v_y1.
+    """
+    r0, p0, g, mu = background["rho0"], background["p0"], background["gamma"], background["mu"]
+    kappa = background["kappa"]
+    T0 = p0 * mu * M_P / (r0 * K_B)
+    E0 = A_RAD * T0 ** 4
+    Bx, By, Bz = (np.asarray(background["B0_gauss"], dtype=float) / np.sqrt(4.0 * np.pi))
+    lam = background["tau"] / (kappa * r0)
+    k = 2.0 * np.pi / lam
+    vax2 = Bx * Bx / r0
+    hat = np.zeros(8)
+    if kind == "alfven":
+        cw = np.sqrt(vax2)
+        hat[2] = amp * cw
+        hat[4] = -(Bx / cw) * hat[2]
+    else:
+        cs2 = p0 / r0 if radiation else g * p0 / r0
+        va2 = (Bx * Bx + By * By + Bz * Bz) / r0
+        s = cs2 + va2
+        root = np.sqrt(s * s - 4.0 * cs2 * vax2)
+        cw = np.sqrt(0.5 * (s + root) if kind == "fast" else 0.5 * (s - root))
+        hat[0] = amp * r0
+        hat[1] = cw * amp
+        hat[3] = (Bz / Bx) * cw / (1.0 - cw * cw / vax2) * amp
+        hat[5] = Bz / (1.0 - vax2 / (cw * cw)) * amp
+        hat[6] = cs2 * hat[0]
+    dx = n_wavelengths * lam / n_cells
+    x = (np.arange(n_cells) + 0.5) * dx
+    return Wave1D(name="wave1d_%s_%d" % (kind, n_cells), n=n_cells, n_wavelengths=n_wavelengths,
+                  dx=dx, lam=lam, k=k, omega=k * cw, phase_speed=cw, gamma=g, mu=mu, Bx=Bx,
+                  R_gas=K_B / (mu * M_P), c=C_LIGHT, a_r=A_RAD, kappa=kappa, E0=E0,
+                  W0=np.array([r0, 0.0, 0.0, 0.0, By, Bz, p0, E0]), hat=hat,
+                  n_driven=int(np.count_nonzero(x < lam)), kind=kind, radiation=radiation)
+
+
 def random_cells(ncell, seed=0):
     """Random per-cell exchange inputs spanning chi = dt c kappa rho in [1e-6, 1e12]
     and gas/radiation energy ratios over many decades."""

@@ -55,7 +55,7 @@ def test_binding_structs_match_header_layout():
     if cc is None:
         pytest.skip("no host C compiler")
     structs = [fld.fld_consts, fld.fld_grid, fld.fld_opacity, fld.fld_opts, fld.fld_stats,
-               fld.fld_prof_entry, fld.fld_batch_stat]
+               fld.fld_prof_entry, fld.fld_batch_stat, fld.fld_wave1d_params]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fld.h"', "int main(void) {"]
     for s in structs:
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s.__name__, s.__name__))

@@ -13,6 +13,7 @@ import pytest
 from oracle import dispersion as Disp
 from oracle import fld as F
 from oracle import rmhd1d as R
+from paper_2503_02764_gb300 import inputs as I
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
@@ -21,6 +22,24 @@ def _bg(case):
     b = GOLD[case]["background"]
     return Disp.background(b["rho0"], b["p0"], b["B0_gauss"], b["gamma"], b["mu"], b["kappa"],
                            tau=b["tau"])
+
+
+def _wave(case, n, nw, kind="fast", radiation=True, cfl=0.8):
+    return R.Wave(I.wave1d(GOLD[case]["background"], n, nw, kind, radiation=radiation), cfl=cfl)
+
+
+@pytest.mark.parametrize("case", ["table2_weak", "table3_strong"])
+def test_recipe_matches_the_dispersion_background(case):
+    bg = _bg(case)
+    P = I.wave1d(GOLD[case]["background"], 40, 1)
+    assert P.E0 == pytest.approx(bg["E0"], rel=1e-14)
+    assert P.k == pytest.approx(bg["k"], rel=1e-14)
+    assert P.Bx == pytest.approx(bg["B"][0], rel=1e-14)
+    assert P.phase_speed == pytest.approx(Disp.magnetosonic_speed(bg, fast=True), rel=1e-14)
+    assert P.E0 == pytest.approx(GOLD[case]["E0"], rel=1e-5)           # printed E_0
+    S = I.wave1d(GOLD[case]["background"], 40, 1, "slow", radiation=False)
+    assert S.phase_speed == pytest.approx(
+        Disp.magnetosonic_speed(bg, fast=False, isothermal=False), rel=1e-14)
 
 
 def test_weno3_exact_on_lines_third_order_and_bounded_at_a_step():
@@ -87,7 +106,7 @@ def test_spatial_damping_matches_printed_damping_per_length(case, kind):
     # the wave driven at omega = k c_ms (isothermal magnetosonic speed) decays as
     # exp(-Im k x); the paper prints omega_Im / (omega_Re / k) for the same modes
     bg = _bg(case)
-    wv = R.Wave(bg, 40, 1, kind=kind)
+    wv = _wave(case, 40, 1, kind)
     k = R.spatial_damping(bg, wv.omega, bg["k"])
     assert k.imag == pytest.approx(GOLD[case]["damping_per_length_" + kind], rel=3e-3)
     assert k.real == pytest.approx(bg["k"], rel=3e-3)
@@ -97,7 +116,7 @@ def test_ideal_mhd_fast_wave_travels_at_its_speed():
     # radiation off, adiabatic eigenmode: after 5.5 wavelengths of travel the profile
     # behind the front is the analytic wave, up to the scheme's small numerical damping
     bg = _bg("table3_strong")
-    wv = R.Wave(bg, 280, 7, kind="fast", radiation=False)
+    wv = _wave("table3_strong", 280, 7, "fast", radiation=False)
     U, t, _ = wv.run(5.5 * wv.lam / wv.phase_speed)
     assert wv.damping(U, 1, 5) * wv.lam < 0.05
     W = R.primitive(U, wv.Bx, wv.gamma)
@@ -115,7 +134,7 @@ def test_radiation_leaves_the_alfven_wave_alone():
     bg = _bg("table3_strong")
     out = []
     for rad in (True, False):
-        wv = R.Wave(bg, 200, 5, kind="alfven", radiation=rad)
+        wv = _wave("table3_strong", 200, 5, "alfven", radiation=rad)
         U, _, _ = wv.run(3.5 * wv.lam / wv.phase_speed)
         out.append(R.primitive(U, wv.Bx, wv.gamma))
     np.testing.assert_allclose(out[0][R.VY], out[1][R.VY], rtol=0, atol=1e-3 * wv.hat[R.VY])
@@ -131,7 +150,7 @@ def test_radiative_fast_wave_damping_converges_to_the_dispersion_relation():
     bg = _bg("table3_strong")
     rates = []
     for cfl in (0.2, 0.1):
-        wv = R.Wave(bg, 280, 7, kind="fast", cfl=cfl)
+        wv = _wave("table3_strong", 280, 7, "fast", cfl=cfl)
         U, _, _ = wv.run(5.5 * wv.lam / wv.phase_speed)
         rates.append(wv.damping(U, 1, 5))
     exact = R.spatial_damping(bg, wv.omega, bg["k"]).imag
