@@ -178,6 +178,90 @@ def dist_env():
     return rank, world, local
 
 
+def next_rows(hd, P, prec, gkw, consts, op, rho, T, E, ebc, peak_hbm):
+    """Per-call timings of the widening rows on the bench workload (CUDA events, after
+    warm-up, averaged over a few calls): the explicit coupling terms (with a velocity
+    field), the three limiters, a tabulated opacity against the power law it extends (the
+    table built around the recipe's Kramers coefficient), and the 1D radiation-MHD wave
+    step of the strongly radiative fast wave (280 cells)."""
+    import torch
+    from paper_2503_02764_gb300 import fld, inputs as I
+    stream = torch.cuda.current_stream()
+    n = P.ncells
+
+    def timed(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def hbm(ms, bpc):
+        gbs = bpc * n / (ms * 1e-3) / 1e9
+        return {"ms": ms, "bytes_per_cell": bpc, "achieved_GBs": gbs, "frac": gbs / peak_hbm}
+
+    out = {"cells": n}
+    z = lambda m: torch.empty(m, dtype=torch.float64, device="cuda")
+    hd.set_opts(precision=prec, tol=1e-10, max_cycles=50, limiter=fld.LIMITER_LP, **gkw)
+    v = z(3 * n).uniform_(-1.0, 1.0)
+    Fo, fro, fe, vfr, pt = z(3 * n), z(3 * n), z(n), z(n), z(n)
+    # reads E, rho, T, v (6 words), writes F, f_r (3 each), f, v.f_r, P:grad v
+    out["coupling"] = hbm(timed(lambda: hd.coupling(consts, op, E, rho, T, ebc, v, Fo, fro, fe,
+                                                    vfr, pt)), 120.0)
+    del v, Fo, fro, fe, vfr, pt
+    D = z(n)
+    lim = {}
+    for name, mode in (("levermore_pomraning", fld.LIMITER_LP),
+                       ("diffusion_1_3", fld.LIMITER_DIFFUSION),
+                       ("minerbo", fld.LIMITER_MINERBO)):
+        hd.set_opts(precision=prec, tol=1e-10, max_cycles=50, limiter=mode, **gkw)
+        # the split of E into FP32 pairs (16 B) and the limiter proper (32 B) in MIXED_DF
+        lim[name] = hbm(timed(lambda: hd.limiter(consts, op, E, rho, T, ebc, D)),
+                        48.0 if prec == fld.PREC_MIXED_DF else 32.0)
+    out["limiter"] = lim
+    hd.set_opts(precision=prec, tol=1e-10, max_cycles=50, limiter=fld.LIMITER_LP, **gkw)
+    table, grid = I.opacity_table(P.opacity[1])
+    tdev = torch.from_numpy(table).cuda()
+    top = fld.make_opacity((I.OPACITY_TABLE, 1.0, table, grid), tdev)
+    tab = {"table_shape": list(table.shape)}
+    for name, o in (("power_law", op), ("table", top)):
+        Tc, Ec = T.clone(), E.clone()
+        tab[name] = {
+            "limiter": hbm(timed(lambda: hd.limiter(consts, o, E, rho, T, ebc, D)),
+                           48.0 if prec == fld.PREC_MIXED_DF else 32.0),
+            "exchange": hbm(timed(lambda: hd.exchange(consts, o, P.dt, rho, Tc, Ec)), 40.0),
+            "step_ms": timed(lambda: hd.step(consts, o, P.dt, rho, Tc, Ec, ebc,
+                                             raise_on_error=False), reps=3, warm=1),
+        }
+        del Tc, Ec
+    out["tabulated_opacity"] = tab
+    wp = I.wave1d(I.WAVE_BACKGROUNDS["strong"], 280, 7, "fast")
+    wv = fld.Wave1D(wp, precision=fld.PREC_FP64, tol=1e-13, max_cycles=200)
+    W = np.repeat(np.asarray(wp.W0, dtype=float)[:, None], wp.n, axis=1)
+    U = np.stack([W[0], W[0] * W[1], W[0] * W[2], W[0] * W[3], W[4], W[5],
+                  W[6] / (wp.gamma - 1.0) + 0.5 * (wp.Bx ** 2 + W[4] ** 2 + W[5] ** 2), W[7]])
+    Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    state = {"t": 0.0}
+
+    def wave_step():
+        dt = wv.max_dt(Ud, 0.8)
+        wv.step(Ud, state["t"], dt)
+        state["t"] += dt
+
+    ms = timed(wave_step, reps=50, warm=5)
+    out["wave1d"] = {"cells": wp.n, "ms_per_step": ms, "cell_updates_per_s": wp.n / (ms * 1e-3),
+                     "note": "launch- and synchronisation-bound on 280 cells: three Runge-Kutta "
+                             "stages of four launches, the substep's FP64 multigrid cycles and "
+                             "several host synchronisations per step"}
+    wv.close()
+    return out
+
+
 def workload_name(n):
     return ("stratified3d_%d^3 (x,y periodic, z Dirichlet, Kramers opacity, "
             "dt = 10x explicit limit)" % n)
@@ -302,6 +386,9 @@ def main():
     ap.add_argument("--precision", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the timings of the widening rows (coupling, limiters, tabulated "
+                         "opacity, 1D wave step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--smoother", type=int, default=-1,
                     help="-1 the tuned choice (else 0); 0 in-place half sweeps, 1 out-of-place "
@@ -528,6 +615,14 @@ def main():
                 cyc = st["cycles"]
             ttt[name] = {"ms": float(np.median(times)), "cycles": cyc}
 
+    # ---------------- the widening rows, timed on the same workload (rank 0)
+    rows = None
+    if rank == 0 and not args.no_next:
+        try:
+            rows = next_rows(hd, P, prec, gkw, consts, op, rho, T, E, ebc, load_peaks()[0])
+        except Exception as exc:                 # reported, never fatal to the headline
+            rows = {"error": "%s: %s" % (type(exc).__name__, exc)}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -549,6 +644,8 @@ def main():
             "profiled_pass_ms_per_step": ms_prof / args.steps,
             "roofline": roof, "kernel_breakdown": breakdown,
             "time_to_1e-10_ms": ttt, "clocks": clocks, "e2e": e2e}
+    if rows is not None:
+        line["next_rows"] = rows
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -283,6 +283,16 @@ SIGMA_SB = 5.670374e-5
 A_RAD = 4.0 * SIGMA_SB / C_LIGHT
 
 
+# the two backgrounds of the linear-wave tests (Sect. 4.3): weakly radiative and
+# radiation-dominant, the same rho_0, B_0, gamma, mu, kappa and optical depth per wavelength
+WAVE_BACKGROUNDS = {
+    "weak": dict(rho0=3.216e-9, p0=17.34e3, B0_gauss=(330.14, 0.0, 330.14), gamma=5.0 / 3.0,
+                 mu=0.5, kappa=0.4, tau=1e3),
+    "strong": dict(rho0=3.216e-9, p0=43.35e3, B0_gauss=(330.14, 0.0, 330.14), gamma=5.0 / 3.0,
+                   mu=0.5, kappa=0.4, tau=1e3),
+}
+
+
 @dataclass
 class Wave1D:
     """A driven 1D wave problem (the linear-wave tests of Sect. 4.3), CGS units, the

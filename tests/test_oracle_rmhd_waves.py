@@ -28,6 +28,15 @@ def _wave(case, n, nw, kind="fast", radiation=True, cfl=0.8):
     return R.Wave(I.wave1d(GOLD[case]["background"], n, nw, kind, radiation=radiation), cfl=cfl)
 
 
+def test_recipe_backgrounds_are_the_printed_ones():
+    for key, case in (("weak", "table2_weak"), ("strong", "table3_strong")):
+        g = GOLD[case]["background"]
+        b = I.WAVE_BACKGROUNDS[key]
+        for name in ("rho0", "p0", "gamma", "mu", "kappa", "tau"):
+            assert b[name] == pytest.approx(g[name], rel=1e-15), (key, name)
+        assert list(b["B0_gauss"]) == list(g["B0_gauss"])
+
+
 @pytest.mark.parametrize("case", ["table2_weak", "table3_strong"])
 def test_recipe_matches_the_dispersion_background(case):
     bg = _bg(case)
