@@ -2,4 +2,9 @@
 
 Imported by the tests, the smoke check and the benchmark's CPU-baseline leg;
 never by the library.
+
+* ``fld``: the substep (limiter, backward-Euler diffusion, exchange), its explicit
+  coupling terms and the opacity laws (constant, power law, table);
+* ``dispersion``: the linear RMHD modes of Appendix B;
+* ``rmhd1d``: the 1D radiation-MHD wave step of the linear-wave tests.
 """

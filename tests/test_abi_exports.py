@@ -76,3 +76,28 @@ def test_binding_structs_match_header_layout():
         assert int(got[s.__name__]) == ctypes.sizeof(s), s.__name__
         for name, *_ in s._fields_:
             assert int(got["%s.%s" % (s.__name__, name)]) == getattr(s, name).offset, (s, name)
+
+
+def test_wave1d_parameter_checks_without_gpu():
+    # fld_wave1d_create validates its parameters on the host before any device work
+    from paper_2503_02764_gb300 import fld, inputs as I
+    L = fld.lib()
+    P = I.wave1d(I.WAVE_BACKGROUNDS["strong"], 64, 4, "fast")
+    w = fld.H()
+
+    def rc(**change):
+        p = fld.make_wave1d_params(P)
+        for k, v in change.items():
+            setattr(p, k, v)
+        return L.fld_wave1d_create(ctypes.byref(w), ctypes.byref(p))
+
+    assert rc(n=7) == fld.FLD_ERR_ARG                      # too few cells
+    assert rc(n_driven=61) == fld.FLD_ERR_ARG              # driven region too long
+    assert rc(n_driven=-1) == fld.FLD_ERR_ARG
+    assert rc(dx=0.0) == fld.FLD_ERR_ARG
+    assert rc(gamma=1.0) == fld.FLD_ERR_ARG
+    assert rc(E_right=-1.0) == fld.FLD_ERR_ARG
+    p = fld.make_wave1d_params(P)
+    p.hat[0] = 2.0 * p.W0[0]                               # the drive would make rho < 0
+    assert L.fld_wave1d_create(ctypes.byref(w), ctypes.byref(p)) == fld.FLD_ERR_ARG
+    assert L.fld_wave1d_create(None, ctypes.byref(p)) == fld.FLD_ERR_ARG
