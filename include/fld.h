@@ -18,13 +18,19 @@
  *        Euler on de/dt = +qdot, dE/dt = -qdot, qdot = c kappa rho (E - a_r T^4),
  *        e = rho R_gas T / (gamma - 1) (Eqs. energy_density, ideal_gas_law).
  *
+ * Around the substep: its explicit coupling terms (fld_coupling), a batched
+ * substep over many independent grids in one launch (fld_step_batched), an
+ * allocation-free solve (fld_diffuse_static) and a 1D radiation-MHD step that
+ * runs the substep inside a hyperbolic update (fld_wave1d_*).
+ *
  * Layout: every field is a contiguous float64 array of n[0]*n[1]*n[2] cells,
  * x fastest: index = (k * n[1] + j) * n[0] + i. Absent axes have n = 1.
  *
  * Memory: field pointers are DEVICE pointers owned by the caller. The handle
  * owns its workspace (the multigrid level pyramid, scratch and reduction
- * buffers), allocated once in fld_create and freed in fld_destroy; no entry
- * point other than those two allocates device memory.
+ * buffers), allocated once in fld_create and freed in fld_destroy; only the
+ * create calls (fld_create, fld_batch_create, fld_wave1d_create) allocate device
+ * memory.
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream). Work is enqueued on it. fld_diffuse and fld_step read the residual
@@ -51,7 +57,8 @@ typedef enum {
     FLD_ERR_DOMAIN = 2,         /* a cell had E, rho, T or kappa <= 0 or non-finite     */
     FLD_ERR_NOT_CONVERGED = 3,  /* max_cycles V-cycles did not reach tol; E holds the
                                    last iterate                                        */
-    FLD_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired                  */
+    FLD_ERR_TIMEOUT = 4,        /* reserved for a bounded device-side wait; no kernel of
+                                   this library waits on another block, so none returns it */
     FLD_ERR_CUDA = 5,           /* a CUDA runtime call failed                          */
     FLD_ERR_NOMEM = 6           /* device allocation failed in a create call           */
 } fld_status;
