@@ -69,9 +69,15 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 ALU peak of the GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA lanes
-# per SM per clock (the rate a dependent-FMA probe sustains) x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 operations per cell of the FP64-bound level-0 kernels, counted in their source for
+# an interior cell of the 3D workload (add, multiply = 1 flop, FMA = 2; the FP32 seeds and
+# the format conversions are not counted): the FP64 limiter with the Kramers opacity, the
+# FP64 exchange (FP32 Newton seed, one FP64 Newton step), the FP64 refinement residual.
+FP64_FLOPS_PER_CELL = {
+    "limiter": 76.0,
+    "exchange": 47.0,
+    "resid64": 33.0,
+}
 
 
 def ncu_traffic(kernel, cells_per_launch):
@@ -296,14 +302,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def tuned_opts(kind, problems):
-    """Autotuner cache entry for this GPU and workload, or None."""
-    try:
-        from paper_2503_02764_gb300 import autotune
-        c = autotune.cached(kind, autotune.signature(kind, problems))
-        return c["best"] if c else None
-    except Exception:
-        return None
+DTYPE = {
+    "mixed": "f32 V-cycles (smoothing, restriction, prolongation) inside f64 iterative "
+             "refinement (f64 residual and correction); f64 coarsest solve; f64 limiter; "
+             "f64 exchange (f32 Newton seed, f64 Newton polish)",
+    "mixed_df": "f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
+                "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
+                "exponent window)",
+    "fp64": "f64 V-cycles; f64 coarsest solve; f64 limiter; f64 exchange (f32 Newton seed, "
+            "f64 Newton polish)",
+}
+BATCH_DTYPE = ("f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
+               "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
+               "exponent window)")
+PREC = {"mixed_df": 2, "mixed": 1, "fp64": 0}
+
+# FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per SM per
+# clock x 2 flop x the maximum SM clock (1.26 TFLOP/s at 2070 MHz)
+def fp64_peak_tflops():
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
 def run_batch(args):
@@ -323,22 +344,46 @@ def run_batch(args):
     if dist is not None:
         dist.barrier()
     # each rank advances its own independent batch (weak scaling, no collective)
-    ps = I.batch(args.nprob, seed_base=I.SEED_BASE + 4 + 100000 * rank)
-    tuned = tuned_opts("batch", ps)
-    kw = dict(block=args.block, cluster=args.cluster, nu1=2, nu2=2)
-    if tuned and not (args.block or args.cluster):
-        kw = {k: tuned[k] for k in ("block", "cluster", "nu1", "nu2")}
-        kw["inner"] = tuned.get("inner", 1)
+    seed = I.SEED_BASE + 4 + 100000 * rank
+    res = batch_workload(fld, I, torch, args.nprob, seed, args.steps, args.warmup, args.block,
+                         args.cluster, dist=dist, local=local)
+    ms, cells_all, value = aggregate(res["ms_per_step"] * args.steps, res["cells"], args.steps,
+                                     dist, "cuda")
+    line = {"metric": METRIC + " [batched]", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": BATCH_DTYPE, "data": "synthetic",
+            "config": {"workload": res["workload"], "cells": res["cells"],
+                       "block": res["options"]["block"], "cluster": res["options"]["cluster"],
+                       "nu1": res["options"]["nu1"], "nu2": res["options"]["nu2"],
+                       "inner": res["options"]["inner"], "autotuned": res["autotuned"]},
+            "max_cycles_per_step": res["max_cycles_per_step"], "clocks": res["clocks"],
+            "gpu_launches": res["gpu_launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def batch_workload(fld, I, torch, nprob, seed, steps, warmup, block=0, cluster=0, dist=None,
+                   local=0):
+    """Time `steps` batched substeps (after `warmup`) of the nprob-member batch."""
+    ps = I.batch(nprob, seed_base=seed)
+    from paper_2503_02764_gb300 import autotune
+    tuned = autotune.batch_options(ps)
+    kw = dict(block=block, cluster=cluster, nu1=2, nu2=2, inner=1)
+    if tuned and not (block or cluster):
+        kw = tuned
     b = fld.Batch([(p.shape, p.h, p.bc) for p in ps], tol=1e-10, max_cycles=50, graph=1, **kw)
     cat = lambda xs: torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
     rho, T, E = cat([p.rho for p in ps]), cat([p.T for p in ps]), cat([p.E for p in ps])
     consts = fld.make_consts(1.0, 1.0, 5.0 / 3.0, 1.0)
     ops = [fld.make_opacity(p.opacity) for p in ps]
     dts = [p.dt for p in ps]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.step(consts, ops, dts, rho, T, E)
-    n0 = fld.fld_launch_count()
     stream = torch.cuda.current_stream()
+    n0 = fld.fld_launch_count()
     clk = Clocks(local)
     if dist is not None:
         dist.barrier()
@@ -346,7 +391,7 @@ def run_batch(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     cyc = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         rc, st = b.step(consts, ops, dts, rho, T, E)
         cyc.append(max(x["cycles"] for x in st))
     ev1.record(stream)
@@ -354,27 +399,216 @@ def run_batch(args):
     if dist is not None:
         dist.barrier()
     clocks = clk.stop()
-    ms_local = ev0.elapsed_time(ev1)
-    ms, cells_all, value = aggregate(ms_local, b.cells, args.steps, dist, "cuda")
+    ms = ev0.elapsed_time(ev1)
     cells = b.cells
-    line = {"metric": METRIC + " [batched]", "value": value,
-            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "f32 V-cycles + double-f32 refinement + f64 limiter/exchange",
-            "data": "synthetic",
-            "config": {"workload": "batch of %d 2D problems, sides U{32..512}, one persistent "
-                                   "launch per step, CUDA graph" % args.nprob,
-                       "cells": cells, "block": kw["block"] or 512,
-                       "cluster": kw["cluster"] or "auto", "nu1": kw["nu1"], "nu2": kw["nu2"],
-                       "inner": kw.get("inner", 1),
-                       "autotuned": bool(tuned and not (args.block or args.cluster))},
-            "max_cycles_per_step": cyc, "clocks": clocks,
-            "gpu_launches": args.steps}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    b.close()
+    return {"workload": "batch of %d 2D problems, sides U{32..512}, one persistent launch per "
+                        "step, CUDA graph" % nprob,
+            "cells": cells, "ms_per_step": ms / steps, "cell_updates_per_s": cells * steps / (ms * 1e-3),
+            "options": {"block": kw["block"] or 512, "cluster": kw["cluster"] or "auto",
+                        "nu1": kw["nu1"], "nu2": kw["nu2"], "inner": kw.get("inner", 1)},
+            "autotuned": bool(tuned and not (block or cluster)),
+            "max_cycles_per_step": cyc, "clocks": clocks, "precision": "mixed_df",
+            "dtype": BATCH_DTYPE, "gpu_launches": fld.fld_launch_count() - n0}
+
+
+def step_series(hd, consts, op, P, rho, T, E, ebc, steps, warmup, torch):
+    """Event-timed `steps` substeps after `warmup` ones on the caller's stream (the fields
+    evolve in place); returns (ms per step, cycles per step, last status)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        hd.step(consts, op, P.dt, rho, T, E, ebc, raise_on_error=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    cyc, st = [], None
+    for _ in range(steps):
+        st = hd.step(consts, op, P.dt, rho, T, E, ebc, raise_on_error=False)
+        cyc.append(st["cycles"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps, cyc, st
+
+
+def profile_steps(hd, consts, op, P, rho, T, E, ebc, steps, torch, peak_hbm, prec):
+    """The same steps with every launch bracketed by events: per-kernel breakdown, the
+    whole step's algorithmic bytes, the dominant level-0 kernel's roofline."""
+    hd.prof_enable(True, 65536)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(steps):
+        hd.step(consts, op, P.dt, rho, T, E, ebc, raise_on_error=False)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = e2.elapsed_time(e3)
+    prof = hd.prof_read()
+    hd.prof_enable(False)
+
+    def bpc(e):
+        b = BYTES_PER_CELL.get(e["name"])
+        if e["name"] == "resid64" and prec == 0:
+            b = 24.0
+        return b
+
+    total_ms = sum(e["ms"] for e in prof)
+    alg_bytes = sum(bpc(e) * e["cells"] for e in prof if bpc(e) is not None)
+    lvl0 = [e for e in prof if e["level"] == 0 and bpc(e) is not None]
+    dom = max(lvl0, key=lambda e: e["ms"]) if lvl0 else None
+    kernels = []
+    for e in sorted(prof, key=lambda e: -e["ms"])[:14]:
+        k = {"kernel": e["name"], "level": e["level"], "launches": e["launches"],
+             "ms": round(e["ms"], 4), "share": round(e["ms"] / total_ms, 4),
+             "avg_launch_us": round(1e3 * e["ms"] / e["launches"], 2)}
+        if bpc(e) is not None:
+            gbs = bpc(e) * e["cells"] / (e["ms"] * 1e-3) / 1e9
+            k.update(bytes_per_cell=bpc(e), achieved_GBs=round(gbs, 1),
+                     frac_hbm=round(gbs / peak_hbm, 4))
+        kernels.append(k)
+    def hbm_roof(e):
+        b = bpc(e)
+        achieved = b * e["cells"] / (e["ms"] * 1e-3) / 1e9
+        return {"kernel": e["name"], "bound": "hbm", "achieved": achieved, "peak": peak_hbm,
+                "unit": "GB/s", "frac": achieved / peak_hbm,
+                "traffic": ncu_traffic(e["name"], e["cells"] / e["launches"]),
+                "peak_source": "measured", "launches": e["launches"],
+                "avg_launch_us": 1e3 * e["ms"] / e["launches"], "bytes_per_cell": b}
+
+    fp64_bound = lambda e: (e["name"] in FP64_FLOPS_PER_CELL and
+                            not (prec == 2 and e["name"] in ("limiter", "exchange")))
+    roof = None
+    if dom and fp64_bound(dom):
+        # an FP64-bound kernel: its FP64 flops against the FP64 peak
+        f = FP64_FLOPS_PER_CELL[dom["name"]]
+        pk = fp64_peak_tflops()
+        achieved = f * dom["cells"] / (dom["ms"] * 1e-3) / 1e12
+        roof = {"kernel": dom["name"], "bound": "alu", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk,
+                "traffic": ncu_traffic(dom["name"], dom["cells"] / dom["launches"]),
+                "peak_source": "FP64 unit counts and clock: 152 SMs x 2 FMA/clk x 2 flop x "
+                               "max SM clock", "launches": dom["launches"],
+                "avg_launch_us": 1e3 * dom["ms"] / dom["launches"],
+                "fp64_flops_per_cell": f}
+    elif dom:
+        roof = hbm_roof(dom)
+    hb = [e for e in lvl0 if not fp64_bound(e)]
+    roof_hbm = hbm_roof(max(hb, key=lambda e: e["ms"])) if hb else None
+    whole = {"algorithmic_bytes_per_cell": alg_bytes / steps / P.ncells,
+             "achieved_GBs": alg_bytes / (ms_prof * 1e-3) / 1e9,
+             "frac_hbm": alg_bytes / (ms_prof * 1e-3) / 1e9 / peak_hbm}
+    return prof, ms_prof / steps, kernels, roof, whole, roof_hbm
+
+
+def fp64_kernels(prof, peak_tflops, prec):
+    """The FP64-bound level-0 kernels against the FP64 peak: their FP64 operations per
+    cell (FMA = 2 flops) counted from the kernels' source, times the cells, over the
+    event-timed duration. In MIXED_DF mode the limiter and exchange are double-FP32
+    kernels and are not listed."""
+    out = {}
+    for e in prof:
+        f = FP64_FLOPS_PER_CELL.get(e["name"])
+        if f is None or e["level"] != 0:
+            continue
+        if prec == 2 and e["name"] in ("limiter", "exchange"):
+            continue
+        tf = f * e["cells"] / (e["ms"] * 1e-3) / 1e12
+        out[e["name"]] = {"fp64_flops_per_cell": f, "achieved_TFLOPs": round(tf, 4),
+                          "peak_TFLOPs": round(peak_tflops, 4), "frac": round(tf / peak_tflops, 4),
+                          "avg_launch_us": round(1e3 * e["ms"] / e["launches"], 2)}
+    return out
+
+
+def config_workloads(fld, I, torch, peak_hbm, nprob=512, big=512):
+    """The other workloads of the metric, each with its own precision, bounded in time:
+    the 1D pulse (FP64, tol 1e-12), the 2D log-normal field at 1024^2 (FP64, 10 steps, tol
+    1e-10), the 512-member batch (one launch per step) and the linear mode at big^3 (mixed,
+    100 steps) for both radiation-to-gas pressure ratios, with its decay against the exact
+    per-step amplification and the roofline of its dominant kernel at that size."""
+    out = {}
+    consts_of = lambda P: fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    # 1: pulse1d, FP64 plain method, one step + exchange, tol 1e-12
+    P = I.gaussian_pulse_1d(256)
+    hd = fld.Handle(P.shape, P.h, P.bc, precision=fld.PREC_FP64, tol=1e-12, max_cycles=50)
+    first = hd.step(consts_of(P), fld.make_opacity(P.opacity), P.dt, dev(P.rho), dev(P.T),
+                    dev(P.E), None, raise_on_error=False)
+    rho, T, E = dev(P.rho), dev(P.T), dev(P.E)
+    ms, cyc, st = step_series(hd, consts_of(P), fld.make_opacity(P.opacity), P, rho, T, E, None,
+                              20, 3, torch)
+    out["pulse1d_256"] = {"cells": P.ncells, "precision": "fp64", "tol": 1e-12,
+                          "first_step_cycles": first["cycles"], "ms_per_step": ms,
+                          "cycles_per_step": cyc[-1], "cell_updates_per_s": P.ncells / (ms * 1e-3),
+                          "note": "256 cells: latency-bound (launches and the per-cycle "
+                                  "residual read-back), no HBM roofline"}
+    hd.close()
+    # 2: lognormal2d 1024^2, FP64 plain GMG, 10 implicit steps, tol 1e-10
+    P = I.lognormal_2d(1024)
+    for name, prec in (("fp64", fld.PREC_FP64), ("mixed", fld.PREC_MIXED)):
+        hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50)
+        rho, T, E = dev(P.rho), dev(P.T), dev(P.E)
+        hd.step(consts_of(P), fld.make_opacity(P.opacity), P.dt, dev(P.rho), dev(P.T),
+                dev(P.E), None, raise_on_error=False)          # warm-up on a copy
+        ms, cyc, st = step_series(hd, consts_of(P), fld.make_opacity(P.opacity), P, rho, T, E,
+                                  None, 10, 0, torch)
+        _, msp, _, _, whole, _ = profile_steps(hd, consts_of(P), fld.make_opacity(P.opacity), P,
+                                               dev(P.rho), dev(P.T), dev(P.E), None, 2, torch,
+                                               peak_hbm, prec)
+        out.setdefault("lognormal2d_1024", {"cells": P.ncells, "steps": 10, "tol": 1e-10,
+                                            "note": "8 MB per field: L2-resident, so the "
+                                                    "whole-step fraction is of HBM peak but "
+                                                    "the traffic is largely L2"})
+        out["lognormal2d_1024"][name] = {"ms_per_step": ms, "cycles_per_step": cyc,
+                                         "cell_updates_per_s": P.ncells / (ms * 1e-3),
+                                         "whole_step": whole}
+        hd.close()
+    # 4: the 512-member batch, one launch per step
+    out["batch_%d" % nprob] = batch_workload(fld, I, torch, nprob, I.SEED_BASE + 4, 5, 2)
+    # 5: linear mode at big^3, mixed, 100 steps, for both pressure ratios
+    from oracle import dispersion as Disp       # closed-form amplification (host arithmetic)
+    res = {}
+    for ratio in (0.1, 1.0):
+        P = I.linear_mode_3d(big, ratio=ratio, amp=1e-4, steps=100)
+        opts = dict(nu1=2, nu2=2, smoother=2, inner=2)
+        hd = fld.Handle(P.shape, P.h, P.bc, precision=fld.PREC_MIXED, tol=1e-12, max_cycles=60,
+                        **opts)
+        rho, T, E = dev(P.rho), dev(P.T), dev(P.E)
+        x = (np.arange(big) + 0.5) / big
+        cosx = np.cos(2 * np.pi * x)
+
+        def modes(Tf, Ef):
+            e = (P.R_gas * Tf / (P.gamma - 1)).reshape(P.shape).mean(axis=(0, 1))
+            Em = Ef.reshape(P.shape).mean(axis=(0, 1))
+            return np.array([2.0 / big * np.sum((e - e.mean()) * cosx),
+                             2.0 / big * np.sum((Em - Em.mean()) * cosx)])
+
+        v0 = modes(P.T, P.E)
+        ms, cyc, st = step_series(hd, consts_of(P), fld.make_opacity(P.opacity), P, rho, T, E,
+                                  None, 100, 0, torch)
+        got = modes(T.cpu().numpy(), E.cpu().numpy())
+        D = P.c / (3.0 * 1e4)
+        G = Disp.substep_amplification(P.dt, P.c, 1e4, 1.0, P.a_r, 1.0, P.gamma, P.R_gas, D,
+                                       Disp.discrete_k2(2 * np.pi, 1.0 / big))
+        want = np.linalg.matrix_power(G, 100) @ v0
+        r = {"cells": P.ncells, "steps": 100, "precision": "mixed", "tol": 1e-12,
+             "options": opts, "ms_per_step": ms, "cycles_last_step": cyc[-1],
+             "cell_updates_per_s": P.ncells / (ms * 1e-3),
+             "mode_after_100": got.tolist(), "exact_G100": want.tolist(),
+             "max_rel_dev": float(np.max(np.abs(got - want)) / np.max(np.abs(want)))}
+        if ratio == 1.0:
+            _, msp, kern, roof, whole, roof_h = profile_steps(
+                hd, consts_of(P), fld.make_opacity(P.opacity), P, rho, T, E, None, 2, torch,
+                peak_hbm, fld.PREC_MIXED)
+            r["roofline"] = roof
+            r["roofline_hbm_kernel"] = roof_h
+            r["whole_step"] = whole
+            r["kernels"] = kern[:6]
+        res["Pr/Pg=%g" % ratio] = r
+        hd.close()
+        del rho, T, E
+        torch.cuda.empty_cache()
+    out["linmode3d_%d" % big] = res
+    return out
 
 
 def main():
@@ -383,13 +617,17 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_df", choices=["mixed_df", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the timings of the widening rows (coupling, limiters, tabulated "
                          "opacity, 1D wave step)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the substep in the other two precision modes")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (1D pulse, 2D log-normal, batch, 512^3 mode)")
     ap.add_argument("--smoother", type=int, default=-1,
                     help="-1 the tuned choice (else 0); 0 in-place half sweeps, 1 out-of-place "
                          "half sweeps, 2 single-pass z-marching sweep")
@@ -401,6 +639,7 @@ def main():
     ap.add_argument("--workload", default="stratified", choices=["stratified", "batch"],
                     help="stratified: one 3D box (default); batch: 512 uneven 2D problems")
     ap.add_argument("--nprob", type=int, default=512)
+    ap.add_argument("--big", type=int, default=512, help="side of the linear-mode workload")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cluster", type=int, default=0)
     args = ap.parse_args()
@@ -421,24 +660,24 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    from paper_2503_02764_gb300 import build, fld
+    from paper_2503_02764_gb300 import autotune, build, fld
     from paper_2503_02764_gb300 import inputs as I
     if rank == 0:
         build.build()
     barrier()
 
     P = I.stratified_3d(args.n)
-    prec = {"mixed_df": fld.PREC_MIXED_DF, "mixed": fld.PREC_MIXED, "fp64": fld.PREC_FP64}[
-        args.precision]
-    tuned = tuned_opts("grid", [P])
-    gkw = dict(nu1=2, nu2=2, smoother=0, inner=1)
-    if tuned:
-        gkw = {k: tuned[k] for k in ("nu1", "nu2", "smoother")}
-        gkw["inner"] = tuned.get("inner", 1)
-    for k in ("smoother", "nu1", "nu2", "inner"):     # explicit choices override the tuner
-        if getattr(args, k) >= 0:
-            gkw[k] = getattr(args, k)
-            tuned = None
+    prec = PREC[args.precision]
+
+    def options(pr):
+        o, t = autotune.grid_options(P, pr)
+        for k in ("smoother", "nu1", "nu2", "inner"):     # explicit choices override the tuner
+            if getattr(args, k) >= 0:
+                o[k] = getattr(args, k)
+                t = False
+        return o, t
+
+    gkw, tuned = options(prec)
     hd = fld.Handle(P.shape, P.h, P.bc, precision=prec, tol=1e-10, max_cycles=50, **gkw)
     consts = fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
     op = fld.make_opacity(P.opacity)
@@ -447,9 +686,19 @@ def main():
     ebc = dev(I.pack_dirichlet(P.shape, P.bc, P.E_bc))
     stream = torch.cuda.current_stream()
 
-    stats = None
-    for _ in range(args.warmup):
-        stats = hd.step(consts, op, P.dt, rho, T, E, ebc)
+    # the first substep from the recipe's fields (graphs captured on a copy beforehand)
+    hd.step(consts, op, P.dt, rho.clone(), T.clone(), E.clone(), ebc)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    st_first = hd.step(consts, op, P.dt, rho, T, E, ebc)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    first = {"ms": f0.elapsed_time(f1), "cycles": st_first["cycles"],
+             "rel_resid": st_first["rel_resid"]}
+    for _ in range(max(args.warmup - 1, 0)):
+        hd.step(consts, op, P.dt, rho, T, E, ebc)
+    T_start, E_start = T.clone(), E.clone()          # the state the timed steps start from
 
     # ---------------- timed region (device-resident inputs, graphs on, no profiling)
     n0 = fld.fld_launch_count()
@@ -473,50 +722,27 @@ def main():
     # ---------------- the same steps again with every launch bracketed by events: the
     # per-kernel durations for the roofline and the breakdown (graphs are off while
     # profiling, so this pass is slightly slower than the one above)
-    hd.prof_enable(True, 65536)
-    torch.cuda.synchronize()
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for _ in range(args.steps):
-        hd.step(consts, op, P.dt, rho, T, E, ebc)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    ms_prof = e2.elapsed_time(e3)
-    prof = hd.prof_read()
-    hd.prof_enable(False)
-
-    # ---------------- roofline of the dominant level-0 kernel
     peak_hbm, peak_kind = load_peaks()
-    lvl0 = [e for e in prof if e["level"] == 0 and e["name"] in BYTES_PER_CELL]
-    dom = max(lvl0, key=lambda e: e["ms"]) if lvl0 else None
-    roof = None
-    if dom:
-        bpc = BYTES_PER_CELL[dom["name"]]
-        if dom["name"] == "resid64" and prec == fld.PREC_FP64:
-            bpc = 24.0
-        achieved = bpc * dom["cells"] / (dom["ms"] * 1e-3) / 1e9
-        roof = {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak_hbm,
-                "unit": "GB/s", "frac": achieved / peak_hbm,
-                "traffic": ncu_traffic(dom["name"], dom["cells"] / dom["launches"]),
-                "peak_source": peak_kind, "launches": dom["launches"],
-                "avg_launch_us": 1e3 * dom["ms"] / dom["launches"],
-                "bytes_per_cell": bpc}
-    total_prof = sum(e["ms"] for e in prof)
-    breakdown = sorted(({"kernel": e["name"], "level": e["level"], "launches": e["launches"],
-                         "ms": round(e["ms"], 4), "share": round(e["ms"] / total_prof, 4)}
-                        for e in prof), key=lambda d: -d["ms"])[:12]
+    Tp, Ep = T_start.clone(), E_start.clone()
+    prof, ms_prof, kernels, roof, whole, roof_hbm = profile_steps(
+        hd, consts, op, P, rho, Tp, Ep, ebc, args.steps, torch, peak_hbm, prec)
+    for r in (roof, roof_hbm):
+        if r and r["bound"] == "hbm":
+            r["peak_source"] = peak_kind
+    del Tp, Ep
+    fp64 = fp64_kernels(prof, fp64_peak_tflops(), prec)
 
     # ---------------- end to end through the C ABI with host buffers. Every step copies its
     # inputs (rho, T, E, the Dirichlet face values) from pinned host memory and reads its
-    # results (T, E) back. The inputs are the state the device-resident steps above reached,
-    # so that these steps do the same solve work as those (steps from the initial fields
-    # take longer). Serial: copy in, step, copy out, on one stream.
+    # results (T, E) back. The inputs are the state the device-resident steps started
+    # from, so that these steps do the same solve work as those. Serial: copy in, step,
+    # copy out, on one stream.
     # Pipelined (the reported value): three device buffer sets; while step k computes, step
     # k+1's inputs go up on one copy stream and step k-1's results come down on another (the
     # two directions overlap each other too), each transfer ordered by events.
     e2e = None
     if not args.no_e2e:
-        h_in = tuple(x.detach().cpu().pin_memory() for x in (rho, T, E, ebc))
+        h_in = tuple(x.detach().cpu().pin_memory() for x in (rho, T_start, E_start, ebc))
         e2e_cycles = []
         NSET = 3
         h_out = [tuple(torch.empty_like(h_in[i]).pin_memory() for i in (1, 2))
@@ -592,18 +818,39 @@ def main():
                "pipelined": True, "serial_ms_per_step": ms_serial / args.steps,
                "max_rel_diff_pipelined_vs_serial": diff,
                "cycles_per_step_mean": float(np.mean(e2e_cycles))}
+        del d_in, h_out, h_in
+
+    # ---------------- the whole substep in the other two precision modes, each with its own
+    # tuned options, from the same state (rank 0)
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        for name in ("mixed_df", "fp64", "mixed"):
+            if name == args.precision:
+                continue
+            o, t = options(PREC[name])
+            hv = fld.Handle(P.shape, P.h, P.bc, precision=PREC[name], tol=1e-10, max_cycles=50, **o)
+            Tv, Ev = T_start.clone(), E_start.clone()
+            nst = max(5, args.steps // 4) if name == "fp64" else args.steps
+            msv, cyc, stv = step_series(hv, consts, op, P, rho, Tv, Ev, ebc, nst, 2, torch)
+            variants[name] = {"ms_per_step": msv, "cell_updates_per_s": P.ncells / (msv * 1e-3),
+                              "steps": nst, "cycles_per_step": cyc[-1], "options": o,
+                              "autotuned": t, "dtype": DTYPE[name],
+                              "rel_resid_last": stv["rel_resid"]}
+            hv.close()
+            del Tv, Ev
 
     # ---------------- mixed vs FP64 time to 1e-10 on the same GPU (diffusion solve alone)
     ttt = {}
     if rank == 0 and not args.no_ttt:
         D = torch.empty_like(E)
-        hd.limiter(consts, op, E, rho, T, ebc, D)
+        hd.limiter(consts, op, E_start, rho, T_start, ebc, D)
         for name, pr in (("mixed_df", fld.PREC_MIXED_DF), ("mixed", fld.PREC_MIXED),
                          ("fp64", fld.PREC_FP64)):
-            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, **gkw)
+            o, _ = options(pr)
+            hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, **o)
             times, cyc = [], 0
             for rep in range(4):
-                X = E.clone()
+                X = E_start.clone()
                 torch.cuda.synchronize()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
@@ -613,37 +860,51 @@ def main():
                 if rep:
                     times.append(a.elapsed_time(b))
                 cyc = st["cycles"]
-            ttt[name] = {"ms": float(np.median(times)), "cycles": cyc}
+            ttt[name] = {"ms": float(np.median(times)), "cycles": cyc, "options": o}
+        hd.set_opts(precision=prec, tol=1e-10, max_cycles=50, **gkw)
+        del D, X
 
     # ---------------- the widening rows, timed on the same workload (rank 0)
     rows = None
     if rank == 0 and not args.no_next:
         try:
-            rows = next_rows(hd, P, prec, gkw, consts, op, rho, T, E, ebc, load_peaks()[0])
+            rows = next_rows(hd, P, prec, gkw, consts, op, rho, T, E, ebc, peak_hbm)
         except Exception as exc:                 # reported, never fatal to the headline
             rows = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    hd.close()
+    del rho, T, E, T_start, E_start
+    torch.cuda.empty_cache()
+
+    # ---------------- the metric's other workloads (rank 0), each bounded in time
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        try:
+            configs = config_workloads(fld, I, torch, peak_hbm, args.nprob, args.big)
+        except Exception as exc:                 # reported, never fatal to the headline
+            configs = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {fld.PREC_MIXED_DF: "f32 V-cycles + double-f32 (48-bit) refinement residual/"
-                                         "correction + f64 limiter/exchange/coarse solve",
-                      fld.PREC_MIXED: "f32 V-cycles + f64 refinement residual/correction/"
-                                      "limiter/exchange/coarse solve",
-                      fld.PREC_FP64: "f64"}[prec],
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": workload_name(args.n),
                        "cells": P.ncells, "precision": args.precision, "tol": 1e-10,
                        "nu1": gkw["nu1"], "nu2": gkw["nu2"], "smoother": gkw["smoother"],
-                       "inner": gkw.get("inner", 1),
+                       "inner": gkw.get("inner", 1), "graph": 1,
                        "autotuned": bool(tuned),
                        "l2": "inputs larger than L2 (fields %.0f MB + workspace)" %
                              (3 * P.ncells * 8 / 1e6),
                        "parallelism": "replicas x%d" % world},
             "gpu_launches": launches, "cycles_per_step": cycles,
-            "profiled_pass_ms_per_step": ms_prof / args.steps,
-            "roofline": roof, "kernel_breakdown": breakdown,
+            "first_step_from_recipe": first,
+            "profiled_pass_ms_per_step": ms_prof,
+            "roofline": roof, "roofline_hbm_kernel": roof_hbm, "whole_step": whole,
+            "fp64_kernels": fp64,
+            "kernel_breakdown": kernels,
+            "precision_variants": variants,
             "time_to_1e-10_ms": ttt, "clocks": clocks, "e2e": e2e}
+    if configs is not None:
+        line["workloads"] = configs
     if rows is not None:
         line["next_rows"] = rows
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -69,19 +69,27 @@ enum { FLD_BC_PERIODIC = 0, FLD_BC_NEUMANN = 1, FLD_BC_DIRICHLET = 2 };
    10 to a bilinear interpolant of a table of log10 kappa over (log10 rho, log10 T) (TABLE;
    the paper uses constant opacities and names tables as the next step, Sect. 5) */
 enum { FLD_OPACITY_CONST = 0, FLD_OPACITY_POWER = 1, FLD_OPACITY_TABLE = 2 };
-/* limiter: Levermore-Pomraning (Eq. fld_lambda) or the diffusion limit lambda = 1/3 */
+/* limiter: Levermore-Pomraning (Eq. fld_lambda), the diffusion limit lambda = 1/3, or
+   Minerbo's limiter (named in Sect. 2, published closed form) */
 enum { FLD_LIMITER_LP = 0, FLD_LIMITER_DIFFUSION = 1, FLD_LIMITER_MINERBO = 2 };
-/* solve precision:
-   FP64      plain FP64 V-cycles;
+/* precision mode of a handle (solve, limiter and exchange):
+   FP64      FP64 V-cycles; FP64 limiter and exchange.
    MIXED     FP32 V-cycles (smoothing, restriction, prolongation) inside iterative
-             refinement whose residual and correction are FP64 (the coarsest-level solve
-             is FP64 arithmetic in every mode);
+             refinement whose residual and correction are FP64; the coarsest-level solve
+             is FP64 arithmetic (in every mode). Limiter and exchange are FP64 as in FP64
+             mode.
    MIXED_DF  as MIXED, but the refinement's iterate, right-hand side, coefficients,
              residual and correction are carried as double-FP32 pairs (48-bit significand,
-             error-free transformations) between reading E and writing it back: FP64-grade
-             accuracy at FP32 instruction cost, since FP64 issues at a small fraction of
-             the FP32 rate on this GPU. Values must stay within the FP32 exponent range
-             after the power-of-two scaling the solve applies (|S E| well inside 1e-30..1e30). */
+             error-free transformations) between reading E and writing it back, and the
+             limiter (gradient, R, lambda, D) and the exchange (coefficients, the Newton
+             step that polishes the FP32 root, E') run in the same double-FP32 arithmetic:
+             FP64-grade accuracy (relative error ~1e-14) at FP32 instruction cost, since
+             FP64 issues at a small fraction of the FP32 rate on this GPU. Cells whose
+             values leave the FP32 exponent window take the FP64 routines, and the solve's
+             values must stay within that window after its power-of-two scaling (|S E|
+             well inside 1e-30..1e30).
+   In FP64 and MIXED the FP64 limiter and exchange seed their reciprocals, square roots
+   and the quartic's root in FP32 and refine them by FP64 Newton steps. */
 enum { FLD_PREC_FP64 = 0, FLD_PREC_MIXED = 1, FLD_PREC_MIXED_DF = 2 };
 
 /* Physical constants in the caller's units: speed of light c, radiation
@@ -121,7 +129,7 @@ typedef struct {
 
 /* Solver options; fld_default_opts fills sensible values. */
 typedef struct {
-    int precision;      /* FLD_PREC_FP64 or FLD_PREC_MIXED                          */
+    int precision;      /* FLD_PREC_FP64, FLD_PREC_MIXED or FLD_PREC_MIXED_DF        */
     double tol;         /* stop when ||b - A x||_2 <= tol ||b||_2                    */
     int max_cycles;     /* V-cycle limit (outer refinement steps in MIXED)          */
     int nu1, nu2;       /* red-black Gauss-Seidel sweeps before / after coarse corr. */
@@ -180,7 +188,8 @@ fld_status fld_set_opts(fld_handle* h, const fld_opts* o);
         lambda (device, ncell float64, may be NULL) the limiter value.
    Ghost values for the gradient: periodic wrap; Neumann even mirror
    (E_-1 = E_0, E_-2 = E_1); Dirichlet odd reflection (E_-k = 2 E_b - E_{k-1}).
-   |grad E| = 0 gives lambda = 1/3. Asynchronous. */
+   |grad E| = 0 gives lambda = 1/3. FP64 arithmetic, or double-FP32 on a MIXED_DF handle
+   (relative error ~1e-14 in D). Asynchronous. */
 fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op,
                        const double* E, const double* rho, const double* T,
                        const double* E_bc, double* D, double* lambda, void* stream);
@@ -222,6 +231,8 @@ fld_status fld_diffuse(fld_handle* h, double dt, const double* D, const double* 
    chi = dt c kappa rho, c_v = R_gas/(gamma - 1), e = rho c_v T, solves
    rho c_v T' + (chi/(1+chi)) a_r T'^4 = e + chi E/(1+chi) for the unique positive
    T' and sets E' = (E + chi a_r T'^4)/(1 + chi). kappa = kappa(rho, T) on entry.
+   The root is found by Newton iterations in FP32 on a scaled form of the quartic, then
+   polished by one Newton step in FP64 (double-FP32 on a MIXED_DF handle).
    In: rho (device float64). In/out: T, E (device float64). Asynchronous. */
 fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
                         const double* rho, double* T, double* E, void* stream);
@@ -302,25 +313,27 @@ int fld_prof_read(fld_handle* h, fld_prof_entry* out, int cap);
 long long fld_launch_count(void);
 
 /* ---------------------------------------------------------------- no-allocation solve
-   fld_diffuse_static: the same backward-Euler multigrid solve as fld_diffuse, for
-   callers that cannot allocate device memory themselves or through a handle: host
-   codes that own every byte of the GPU through their own allocator, solvers called
-   from inside a captured or otherwise allocation-free section, or real-time loops
-   that must never reach the CUDA allocator. The paper has no counterpart; this is a
-   property of the library, not of the method.
+   fld_diffuse_static: the same backward-Euler multigrid solve as fld_diffuse, for callers
+   that cannot allocate device memory themselves or through a handle: host codes that hand
+   every byte of the GPU to their own memory pool at start-up, so that cudaMalloc would
+   fail, or real-time loops that must never enter the CUDA allocator. The paper has no
+   counterpart; this is a property of the library, not of the method.
    The workspace lives in one 16 MiB array defined in the library as a file-scope
-   __device__ variable: every GPU on which the library is loaded keeps those 16 MiB
-   until the process exits, and no call allocates or frees anything. Grids of up to
-   131072 cells are accepted in any precision mode; larger grids return FLD_ERR_ARG
-   with a message on stderr.
-   Arguments and results are those of fld_diffuse plus the grid and options a handle
-   would hold (o may be NULL for the defaults); D, E_bc and E are caller-owned device
-   arrays as above. The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress) with that device current; make that first call before any
-   stream capture. Every call reuses the same array, which keeps the previous call's
-   contents (the call clears what must start at zero), so calls must not overlap on
-   the GPU: two calls in flight at once on different streams race. Host threads are
-   serialised by a lock inside the call. */
+   __device__ variable: every GPU on which the library is loaded keeps those 16 MiB until
+   the process exits, and no call allocates or frees device or pinned host memory. Grids
+   of up to 131072 cells are accepted in any precision mode; larger grids return
+   FLD_ERR_ARG with a message on stderr.
+   Arguments and results are those of fld_diffuse plus the grid and options a handle would
+   hold (o may be NULL for the defaults; its graph option is ignored, every kernel is
+   launched directly); D, E_bc and E are caller-owned device arrays as above. The first
+   call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+   device current; make that first call before any stream capture. The call reads the
+   residual back to the host once per V-cycle, each time synchronising `stream`, and
+   synchronises `stream` once more before it returns: it returns after all of its GPU work
+   has finished. Every call reuses the same array, which keeps the previous call's contents
+   (the call clears what must start at zero). Two calls in flight on the GPU at once would
+   race on the array; a lock held for the whole call, together with that final
+   synchronisation, keeps calls from several host threads from overlapping. */
 fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, double dt, const double* D,
                               const double* E_bc, double* E, fld_stats* stats, void* stream);
 

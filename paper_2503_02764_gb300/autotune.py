@@ -36,12 +36,51 @@ def gpu_name():
     return torch.cuda.get_device_name(0)
 
 
-def signature(kind, problems):
-    """Workload key: kind plus a hash of the shapes and boundary kinds."""
+PRECISION_NAMES = {0: "fp64", 1: "mixed", 2: "mixed_df"}
+
+# options of a single grid when nothing is cached: V(2,2), in-place half sweeps, one FP32
+# V-cycle per refinement step
+DEFAULT_GRID = {"nu1": 2, "nu2": 2, "smoother": 0, "inner": 1}
+
+
+def signature(kind, problems, precision=None):
+    """Workload key: kind (with the precision mode when given) plus a hash of the shapes
+    and boundary kinds."""
     h = hashlib.sha256()
     for p in problems:
         h.update(repr((p.shape, p.bc)).encode())
-    return "%s:%d:%s" % (kind, len(problems), h.hexdigest()[:16])
+    key = kind if precision is None else "%s-%s" % (kind, PRECISION_NAMES[int(precision)])
+    return "%s:%d:%s" % (key, len(problems), h.hexdigest()[:16])
+
+
+def grid_options(problem, precision, gpu=None):
+    """Options a single grid runs with in the benchmark: the cached best for this GPU,
+    workload and precision mode (else the entry cached without a precision), else the
+    defaults. Returns (options, tuned)."""
+    try:
+        c = (cached("grid", signature("grid", [problem], precision), gpu)
+             or cached("grid", signature("grid", [problem]), gpu))
+    except Exception:
+        c = None
+    if not c:
+        return dict(DEFAULT_GRID), False
+    b = c["best"]
+    return {"nu1": b["nu1"], "nu2": b["nu2"], "smoother": b["smoother"],
+            "inner": b.get("inner", 1)}, True
+
+
+def batch_options(problems, gpu=None):
+    """Options of the batched substep in the benchmark: the cached best for this GPU and
+    batch (block, cluster, nu1, nu2, inner), else None."""
+    try:
+        c = cached("batch", signature("batch", problems), gpu)
+    except Exception:
+        c = None
+    if not c:
+        return None
+    b = c["best"]
+    return {"block": b["block"], "cluster": b["cluster"], "nu1": b["nu1"], "nu2": b["nu2"],
+            "inner": b.get("inner", 1)}
 
 
 def _load():
@@ -159,7 +198,7 @@ def tune_grid(problem, precision=2, sweeps=((2, 2), (1, 1), (2, 1), (1, 2), (3, 
     good = [r for r in results if r["converged"]]
     best = min(good, key=lambda r: r["seconds"]) if good else None
     if store and best:
-        _store(signature("grid", [P]), {"best": best, "candidates": results,
+        _store(signature("grid", [P], precision), {"best": best, "candidates": results,
                                         "when": time.strftime("%Y-%m-%dT%H:%M:%SZ",
                                                               time.gmtime())}, gpu_name())
     return best, results
@@ -173,5 +212,6 @@ if __name__ == "__main__":
         best, _ = tune_batch(I.batch(512))
         print("batch", best)
     if what in ("grid", "all"):
-        best, _ = tune_grid(I.stratified_3d(256))
-        print("grid", best)
+        for prec in (1, 2, 0):
+            best, _ = tune_grid(I.stratified_3d(256), precision=prec)
+            print("grid", PRECISION_NAMES[prec], best)

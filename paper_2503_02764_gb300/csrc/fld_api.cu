@@ -19,7 +19,7 @@ namespace {
 
 constexpr int MAX_LEVELS = 24;
 constexpr long long COARSE_TARGET = 8;    // stop coarsening at or below this many cells
-constexpr int NORM_BLOCKS = 152 * 8;      // fixed grid of the residual-norm kernels
+constexpr int NORM_BLOCKS_PER_SM = 8;    // residual-norm grid: 8 blocks per SM
 constexpr int NORM_THREADS = 256;
 
 template <typename T>
@@ -92,6 +92,23 @@ int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl) {
     }
     return nl;
 }
+int num_sms() {
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cache[MAXDEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int n = (dev >= 0 && dev < MAXDEV) ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < MAXDEV) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 // launches made outside this file's launch wrapper (the wave step's kernels)
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace fld
@@ -111,6 +128,7 @@ struct fld_handle {
     float* dfK[2] = {nullptr, nullptr};                            // coefficient K (hi, lo)
     double* Dscratch = nullptr;
     double* partials = nullptr;
+    int norm_blocks = 0;              // blocks (and partial sums) of the norm kernels
     DevScalars* scal = nullptr;       // device
     DevScalars* hscal = nullptr;      // pinned host
     std::vector<void*> allocs;
@@ -397,10 +415,10 @@ fld_status residual(fld_handle* h, double* x, float* r32, cudaStream_t s, double
                     unsigned* err) {
     const Lvl& L = h->lv[0];
     run(h, "resid64", 0, L.ncell, s, [&] {
-        launch_resid64(L, x, h->d64[0].b, h->d64[0].K, r32, h->partials, NORM_BLOCKS, NORM_THREADS, s);
+        launch_resid64(L, x, h->d64[0].b, h->d64[0].K, r32, h->partials, h->norm_blocks, NORM_THREADS, s);
     });
-    run(h, "finish_sum", 0, NORM_BLOCKS, s,
-        [&] { launch_finish_sum(h->partials, NORM_BLOCKS, &h->scal->sum, s); });
+    run(h, "finish_sum", 0, h->norm_blocks, s,
+        [&] { launch_finish_sum(h->partials, h->norm_blocks, &h->scal->sum, s); });
     FLD_CK(cudaGetLastError());
     return read_scalars(h, s, rr, err);
 }
@@ -486,11 +504,11 @@ fld_status diffuse_df(fld_handle* h, double* E, double bsum, fld_stats* st, cuda
     auto resid = [&](const float* e, double* rr) -> fld_status {
         float* oh = e ? h->dfx[cur ^ 1][0] : nullptr;
         float* ol = e ? h->dfx[cur ^ 1][1] : nullptr;
-        int nparts = NORM_BLOCKS;
+        int nparts = h->norm_blocks;
         run(h, "resid_df", 0, n, s, [&] {
             nparts = launch_df_resid(L0, wd, h->dfx[cur][0], h->dfx[cur][1], e, h->dfb[0],
                                      h->dfb[1], h->dfK[0], h->dfK[1], oh, ol, h->d32[0].b,
-                                     h->partials, NORM_BLOCKS, NORM_THREADS, s);
+                                     h->partials, h->norm_blocks, NORM_THREADS, s);
         });
         if (e) cur ^= 1;
         run(h, "finish_sum", 0, nparts, s,
@@ -543,9 +561,9 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     if (mixed) restrict_pyramid<float>(h, h->d32, s);
     else restrict_pyramid<double>(h, h->d64, s);
     run(h, "sumsq", 0, L0.ncell, s,
-        [&] { launch_sumsq(L0.ncell, h->d64[0].b, h->partials, NORM_BLOCKS, s); });
-    run(h, "finish_sum", 0, NORM_BLOCKS, s,
-        [&] { launch_finish_sum(h->partials, NORM_BLOCKS, &h->scal->sum, s); });
+        [&] { launch_sumsq(L0.ncell, h->d64[0].b, h->partials, h->norm_blocks, s); });
+    run(h, "finish_sum", 0, h->norm_blocks, s,
+        [&] { launch_finish_sum(h->partials, h->norm_blocks, &h->scal->sum, s); });
     FLD_CK(cudaGetLastError());
     double bsum;
     unsigned err;
@@ -665,7 +683,8 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
         rc = rc ? rc : dalloc(h, &h->dfK[q], n0);
     }
     rc = rc ? rc : dalloc(h, &h->Dscratch, n0);
-    rc = rc ? rc : dalloc(h, &h->partials, NORM_BLOCKS);
+    h->norm_blocks = NORM_BLOCKS_PER_SM * num_sms();
+    rc = rc ? rc : dalloc(h, &h->partials, h->norm_blocks);
     rc = rc ? rc : dalloc(h, &h->scal, 1);
     if (!rc && cudaMallocHost(&h->hscal, sizeof(DevScalars)) != cudaSuccess) {
         cudaGetLastError();
@@ -955,7 +974,8 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
         h.dfb[q] = (float*)take(4 * n0);
         h.dfK[q] = (float*)take(4 * n0);
     }
-    h.partials = (double*)take(8 * NORM_BLOCKS);
+    h.norm_blocks = NORM_BLOCKS_PER_SM * num_sms();
+    h.partials = (double*)take(8 * (size_t)h.norm_blocks);
     h.scal = (DevScalars*)take(sizeof(DevScalars));
     if (!fits) return FLD_ERR_ARG;
     h.Dscratch = nullptr;
@@ -963,5 +983,10 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: clear the status word and sums
     FLD_CK(cudaMemsetAsync(h.scal, 0, sizeof(DevScalars), s));
-    return diffuse_impl(&h, dt, D, E_bc, E, stats, s);
+    const fld_status rc = diffuse_impl(&h, dt, D, E_bc, E, stats, s);
+    // the write-back of the double-FP32 iterate is enqueued after the last read-back: wait
+    // for it, so that no kernel of this call still uses the array once the lock is released
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return rc;
 }

@@ -127,6 +127,9 @@ inline void split_host(double v, float& h, float& l) {
 }
 
 // ----------------------------------------------------------------- host helpers
+// Streaming multiprocessors of the current device, queried once per device; grid caps
+// and the residual-norm grid are sized from it.
+int num_sms();
 int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl);
 bool grid_valid(const fld_grid* g);
 void note_launches(long long n);   // adds to fld_launch_count

@@ -357,14 +357,14 @@ void launch_df_setup(long long n, double S, const double* E, const double* b, co
                      float* xh, float* xl, float* bh, float* bl, float* Kh, float* Kl,
                      cudaStream_t s) {
     long long nb = (n + 255) / 256;
-    if (nb > 152 * 32) nb = 152 * 32;
+    if (nb > num_sms() * 32) nb = num_sms() * 32;
     k_df_setup<<<(int)nb, 256, 0, s>>>(n, std::ilogb(S), E, b, K, xh, xl, bh, bl, Kh, Kl);
 }
 
 void launch_df_finish(long long n, double invS, const float* xh, const float* xl, double* E,
                       cudaStream_t s) {
     long long nb = (n + 255) / 256;
-    if (nb > 152 * 32) nb = 152 * 32;
+    if (nb > num_sms() * 32) nb = num_sms() * 32;
     k_df_finish<<<(int)nb, 256, 0, s>>>(n, std::ilogb(invS), xh, xl, E);
 }
 

@@ -5,7 +5,8 @@
 // w_d = (H_x/H_d)^2:
 //   (A x)_p = x_p + sum_{faces p|q} 0.5 (K_p + K_q) w_d (x_p - x_q) + sum_{Dirichlet} 2 K_p w_d x_p.
 // Coarse levels average K over the (up to 2^d) children and rescale it to the coarse
-// spacing; restriction averages residuals; prolongation is piecewise constant.
+// spacing; restriction averages residuals; prolongation is cell-centred linear (weights
+// 3/4 and 1/4 per coarsened axis, tensor product over the axes).
 // Every kernel here is templated on the storage/arithmetic type (double or float).
 #include <algorithm>
 
@@ -13,7 +14,8 @@
 
 namespace fld {
 
-static inline int grid_for(long long n, int block, int cap = 152 * 32) {
+static inline int grid_for(long long n, int block, int cap = 0) {
+    if (cap <= 0) cap = num_sms() * 32;
     long long nb = (n + block - 1) / block;
     if (nb > cap) nb = cap;
     if (nb < 1) nb = 1;
@@ -22,7 +24,8 @@ static inline int grid_for(long long n, int block, int cap = 152 * 32) {
 
 // Row mapping: a block walks rows r = (j, k) (grid-stride over ny*nz rows) and its
 // threads walk i along the row, so no per-cell integer division is needed.
-static inline int rows_grid(const Lvl& L, int cap = 152 * 64) {
+static inline int rows_grid(const Lvl& L, int cap = 0) {
+    if (cap <= 0) cap = num_sms() * 64;
     long long nr = (long long)L.n[1] * L.n[2];
     return (int)std::min<long long>(std::max<long long>(nr, 1), cap);
 }

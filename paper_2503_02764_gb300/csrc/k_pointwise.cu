@@ -58,7 +58,7 @@ void launch_exchange(long long n, const double* rho, double* T, double* E, Opaci
     if (n <= 0) return;
     const int block = 256;
     long long nb = (n + block - 1) / block;
-    if (nb > 152 * 32) nb = 152 * 32;
+    if (nb > num_sms() * 32) nb = num_sms() * 32;
     const DfConst K = make_dfconst(0.0, op.kappa0, dtc, a_r, cv);
     k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, op, dtc, a_r, cv, use_df, K, err);
 }
@@ -204,13 +204,13 @@ void launch_coupling(const Lvl& L, const double* h, const double* E, const doubl
     for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
     const double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
                                     L.ndim > 2 ? 1.0 / (12.0 * h[2]) : 0.0);
-    const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
+    const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], num_sms() * 64);
     k_coupling<<<nb, 256, 0, s>>>(L, ih, ih, E, rho, T, E_bc, bo, op, c, mode, v, F, fr, fe, vfr,
                                   pt, err);
 }
 
 void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStream_t s) {
-    const long long nb = std::min<long long>((n + 255) / 256, 152 * 32);
+    const long long nb = std::min<long long>((n + 255) / 256, num_sms() * 32);
     k_split_df<<<(int)nb, 256, 0, s>>>(n, v, hi, lo);
 }
 
@@ -223,7 +223,7 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
                               L.ndim > 2 ? 1.0 / (12.0 * h[2]) : 0.0);
     const int block = 256;
-    const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], 152 * 64);
+    const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], num_sms() * 64);
     const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
     if (!(use_df && mode != FLD_LIMITER_DIFFUSION)) Eh = El = nullptr;
     k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, Eh, El, D,

@@ -27,6 +27,7 @@
 // Periodic axes wrap. Same-colour cells must never meet across a periodic wrap, so odd
 // periodic extents are left to the other smoothers, as for the in-place half sweeps.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "fld_internal.cuh"
@@ -305,14 +306,23 @@ namespace {
 constexpr int ZM_TX = 32, ZM_TY = 16, ZM_MINB = 3;
 using ZmMain = ZmShape<ZM_TX, ZM_TY>;
 
-int g_zm_slots = 0;   // resident blocks of the sweep kernel on the whole GPU
+constexpr int ZM_MAXDEV = 64;
+// resident blocks of the sweep kernel on the whole GPU, per device (0: not prepared yet)
+std::atomic<int> g_zm_slots[ZM_MAXDEV];
+std::mutex g_zm_mutex;
+
+int zm_slots() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ZM_MAXDEV) return 1;
+    return std::max(1, g_zm_slots[dev].load(std::memory_order_relaxed));
+}
 
 // z-chunk length: about three waves of blocks over the SMs (the tiles times the chunks),
 // chunks of at least 8 planes so the 2-plane overlap stays small (32 planes at 256^3,
 // the fastest measured there).
 int zm_chunk(const Lvl& L) {
     const int tiles = ((L.n[0] + ZM_TX - 1) / ZM_TX) * ((L.n[1] + ZM_TY - 1) / ZM_TY);
-    const int nch = std::max(1, 2 * std::max(g_zm_slots, 1) / std::max(1, tiles));
+    const int nch = std::max(1, 2 * zm_slots() / std::max(1, tiles));
     const int cz = (L.n[2] + nch - 1) / nch;
     return std::min(L.n[2], std::max(8, cz));
 }
@@ -345,20 +355,23 @@ void launch_rb_sweep(const Lvl& L, const T* xin, T* xout, const T* b, const T* K
     }
 }
 
-// Opt the kernel into its shared-memory size and count its resident blocks: once per
-// process, outside any stream capture (called when a handle is created).
+// Opt the kernel into its shared-memory size and count its resident blocks, once per
+// device (the attribute is a per-device setting), with that device current and outside
+// any stream capture (called when a handle is created).
 void prepare_rb_sweep() {
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZmMain::SMEM);
-        int dev = 0, nsm = 0, occ = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>,
-                                                      ZmMain::NT, ZmMain::SMEM);
-        g_zm_slots = std::max(1, nsm) * std::max(1, occ);
-    });
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ZM_MAXDEV) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_zm_mutex);
+    if (g_zm_slots[dev].load() > 0) return;
+    cudaFuncSetAttribute(k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZmMain::SMEM);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rb_zmarch<ZM_TX, ZM_TY, ZM_MINB>,
+                                                  ZmMain::NT, ZmMain::SMEM);
+    g_zm_slots[dev].store(num_sms() * std::max(1, occ));
 }
 
 template bool rb_sweep_supported<float>(const Lvl&);

@@ -11,6 +11,7 @@
 // in-place form), the average of the children's residuals b - A x, cell-centred
 // trilinear prolongation with mirrored walls, and Gauss-Jordan elimination in FP64 on
 // the coarsest level (at most TAIL_MAX_DENSE cells).
+#include <atomic>
 #include <mutex>
 
 #include "fld_device.cuh"
@@ -217,16 +218,25 @@ void launch_vcycle_tail(const TailLevels<T>& t, cudaStream_t s) {
     k_vcycle_tail<T><<<1, TAIL_THREADS, tail_smem_bytes<T>(t.L, t.n), s>>>(t);
 }
 
-// Opt the tail kernels into TAIL_SMEM_MAX bytes of dynamic shared memory: once per process,
-// outside any stream capture (called when a handle is created).
+// Opt the tail kernels into TAIL_SMEM_MAX bytes of dynamic shared memory, once per device
+// (the attribute is a per-device setting), with that device current and outside any stream
+// capture (called when a handle is created).
 void prepare_vcycle_tail() {
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TAIL_SMEM_MAX);
-        cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TAIL_SMEM_MAX);
-    });
+    constexpr int MAXDEV = 64;
+    static std::atomic<bool> done[MAXDEV];
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev].load()) return;
+    cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TAIL_SMEM_MAX);
+    cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TAIL_SMEM_MAX);
+    done[dev].store(true);
 }
 
 template size_t tail_smem_bytes<float>(const Lvl*, int);

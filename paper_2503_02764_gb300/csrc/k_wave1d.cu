@@ -3,6 +3,8 @@
 // update with the explicit coupling sources, the exchange's energy feedback and the
 // CFL signal speed. State arrays are variable-major [8][n]: rho, rho v_x, rho v_y,
 // rho v_z, B_y, B_z, e (total gas energy), E; B_x is a constant.
+#include <math_constants.h>
+
 #include "fld_wave1d.cuh"
 
 namespace fld {
@@ -201,7 +203,10 @@ __global__ void k_w1_speed(Wave1dDev P, const double* __restrict__ U,
         double W[8];
         cell_prim(P, U, i, 0.0, W);
         const double c = fabs(W[1]) + fast_speed(W, P.Bx, P.gamma);
-        s = fmax(s, c);          // fmax drops a NaN: the host checks the result is finite
+        // a cell with rho <= 0, p <= 0 or a non-finite speed makes the maximum +inf, which
+        // the host reports as a domain error (fmax alone would drop a NaN)
+        const bool ok = W[0] > 0.0 && W[6] > 0.0 && c < CUDART_INF;
+        s = ok ? fmax(s, c) : CUDART_INF;
     }
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -240,7 +245,7 @@ void launch_w1_post(const Wave1dDev& P, double* U, const double* rho, const doub
 
 void launch_w1_speed(const Wave1dDev& P, const double* U, unsigned long long* out,
                      cudaStream_t s) {
-    const int nb = std::min(blocks_for(P.n), 152 * 4);
+    const int nb = std::min(blocks_for(P.n), num_sms() * 4);
     k_w1_speed<<<nb, W1_THREADS, 0, s>>>(P, U, out);
 }
 

@@ -183,6 +183,25 @@ def stratified_3d(n=256, seed=None, nz=None, ny=None):
         E_bc=E_bc, tol=1e-10, steps=1)
 
 
+def batch_member_shape(p, seed_base=None, nmin=32, nmax=512):
+    """(ny, nx) of member p of the batched workload without building its fields (the
+    first two draws of the member's generator, as in batch_member)."""
+    base = SEED_BASE + 4 if seed_base is None else seed_base
+    rng = np.random.Generator(np.random.PCG64(base + 1000 * p))
+    nx = int(rng.integers(nmin, nmax + 1))
+    ny = int(rng.integers(nmin, nmax + 1))
+    return (ny, nx)
+
+
+def batch_shapes(nprob=512, seed_base=None, nmin=32, nmax=512):
+    """Shapes and boundary kinds of the batched workload's members (what the autotuner's
+    workload signature reads), without building their fields."""
+    from types import SimpleNamespace
+    bc = ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC))
+    return [SimpleNamespace(shape=batch_member_shape(p, seed_base, nmin, nmax), bc=bc)
+            for p in range(nprob)]
+
+
 def batch_member(p, seed_base=None, nmin=32, nmax=512):
     """Member p of the batched 2D workload: sides U{nmin..nmax}, periodic, h = 1,
     log-normal rho (sigma ~ U[0.5, 2], correlation 8 cells), kappa = 10^U[0,4],

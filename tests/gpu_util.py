@@ -49,3 +49,12 @@ def maxrel(a, b):
 def pertrel(a, b):
     """perturbation-relative difference ||a - b||_inf / ||b - mean(b)||_inf"""
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b - b.mean())), 1e-300))
+
+
+def bench_grid_options(precision):
+    """The options bench.py reads for its 256^3 stratified workload in this precision mode
+    (only the shape and the boundary kinds enter the autotuner's cache key)."""
+    from types import SimpleNamespace
+    from paper_2503_02764_gb300 import autotune
+    key = SimpleNamespace(shape=(256, 256, 256), bc=I.stratified_3d(16, nz=8, ny=8).bc)
+    return autotune.grid_options(key, precision)[0]

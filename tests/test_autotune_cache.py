@@ -66,3 +66,24 @@ def test_committed_cache_entries_are_well_formed():
                 assert best["block"] in (256, 512, 1024) and best["cluster"] in (1, 2, 4, 8)
             else:
                 assert best["smoother"] in (0, 1, 2) and best["inner"] >= 1
+
+
+def test_grid_options_prefer_the_precision_entry(monkeypatch):
+    # the benchmark and the parity tests of the timed configuration read the options
+    # through grid_options: the entry tuned for the precision mode wins, the entry cached
+    # without a precision is the fallback, the defaults come last
+    _cache(monkeypatch, "tune_cache_prec.json")
+    P = I.stratified_3d(16, nz=12, ny=10)
+    assert A.signature("grid", [P], 1) != A.signature("grid", [P], 2)
+    assert A.signature("grid", [P], 1).startswith("grid-mixed:1:")
+    assert A.grid_options(P, 1, gpu="GPU-A") == (A.DEFAULT_GRID, False)
+    A._store(A.signature("grid", [P]), {"best": {"nu1": 1, "nu2": 1, "smoother": 2,
+                                                 "inner": 3}}, "GPU-A")
+    opts, tuned = A.grid_options(P, 1, gpu="GPU-A")
+    assert tuned and opts == {"nu1": 1, "nu2": 1, "smoother": 2, "inner": 3}
+    A._store(A.signature("grid", [P], 1), {"best": {"nu1": 2, "nu2": 1, "smoother": 0,
+                                                    "inner": 2}}, "GPU-A")
+    assert A.grid_options(P, 1, gpu="GPU-A")[0] == {"nu1": 2, "nu2": 1, "smoother": 0,
+                                                   "inner": 2}
+    assert A.grid_options(P, 2, gpu="GPU-A")[0]["inner"] == 3
+    assert A.batch_options([P], gpu="GPU-A") is None

@@ -1,31 +1,45 @@
-"""Checks at the workloads' full sizes, in the configuration bench.py times: properties
-that hold at any size, and outputs the oracle computes cell by cell on samples."""
+"""Checks at the workloads' full sizes: the benchmark's 256^3 workload with the options
+bench.py runs it with, the 2D log-normal workload at 1024^2 and the linear mode at 512^3,
+by properties that hold at any size, by the oracle on every cell where it finishes in
+seconds, and on sampled cells."""
 import numpy as np
 import pytest
 
 from oracle import fld as O
 from oracle import dispersion as Disp
 from paper_2503_02764_gb300 import inputs as I
-from gpu_util import torch_cuda, library, dev, host, handle_for, consts_of, ebc_dev, maxrel
+from gpu_util import (torch_cuda, library, dev, host, handle_for, consts_of, ebc_dev, maxrel,
+                      bench_grid_options)
 
 pytestmark = pytest.mark.gpu
 
 
-def test_stratified_256_full_size():
-    """Bench workload (256^3, MIXED_DF, tol 1e-10): limiter against the oracle on every
-    cell; the solve's true FP64 residual by the oracle's matrix-free operator; the exchange
-    on a sample of cells."""
+_FULL = {}
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_stratified_256_full_size(precision):
+    """The benchmark's workload at 256^3 with the options bench.py runs it with in this
+    precision mode (the tuned choice, tol 1e-10, graphs on): the limiter against the
+    oracle on every cell; the solve's true FP64 residual by the oracle's matrix-free
+    operator; E after the solve against the oracle's own solve of the same system (PCG
+    from E^n to 1e-13), on every cell and plane by plane on sampled z planes; the exchange
+    on sampled cells."""
     torch = torch_cuda()
     fld = library()
     P = I.stratified_3d(256)
-    hd = handle_for(fld, P, precision=fld.PREC_MIXED_DF, tol=1e-10, max_cycles=50)
+    opts = bench_grid_options(precision)
+    hd = handle_for(fld, P, precision=precision, tol=1e-10, max_cycles=50, **opts)
     consts, op = consts_of(fld, P), fld.make_opacity(P.opacity)
     rho, T, E, ebc = dev(torch, P.rho), dev(torch, P.T), dev(torch, P.E), ebc_dev(torch, P)
     D = torch.empty_like(E)
     hd.limiter(consts, op, E, rho, T, ebc, D)
     Dg = host(D).reshape(P.shape)
-    Do, _, _ = O.limiter(P.E, P.rho, P.T, P.h, P.bc, P.E_bc, P.c, P.opacity)
-    assert np.max(np.abs(Dg / Do - 1)) < 1e-12      # double-FP32 limiter (MIXED_DF)
+    if "D" not in _FULL:
+        _FULL["D"] = O.limiter(P.E, P.rho, P.T, P.h, P.bc, P.E_bc, P.c, P.opacity)[0]
+    Do = _FULL["D"]
+    # FP64 limiter (MIXED) to 1e-13, double-FP32 limiter (MIXED_DF) to 1e-12
+    assert np.max(np.abs(Dg / Do - 1)) < (1e-13 if precision == 1 else 1e-12)
     st = hd.diffuse(P.dt, D, ebc, E)
     x = host(E).reshape(P.shape)
     # b - A x with b = E^n + Dirichlet terms: A applied by the oracle's stencil sums
@@ -37,6 +51,13 @@ def test_stratified_256_full_size():
     b = P.E + g
     rel = np.linalg.norm((b - Ax).ravel()) / np.linalg.norm(b.ravel())
     assert rel < 1.05e-10, (rel, st)
+    if "x" not in _FULL:
+        _FULL["x"] = O.diffuse(P.E, Do, P.h, P.bc, P.E_bc, P.dt, method="pcg")
+    xo = _FULL["x"]
+    planes = [0, 1, 37, 128, 200, 254, 255]
+    per_plane = [maxrel(x[k], xo[k]) for k in planes]
+    assert max(per_plane) < 1e-10, (per_plane, st)
+    assert maxrel(x, xo) < 1e-10, (maxrel(x, xo), st)
     # exchange on the solved field, 40000 sampled cells against the oracle
     Tg = T.clone()
     hd.exchange(consts, op, P.dt, rho, Tg, E)

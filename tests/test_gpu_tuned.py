@@ -1,0 +1,160 @@
+"""Parity of the configurations the benchmark and the autotuner actually run, against the
+oracle: several FP32 V-cycles per refinement step (inner 2 and 3) with the z-marching
+smoother, V(1,1) and the CUDA-graph replay of the FP32 V-cycle, in both mixed modes; the
+whole substep on the stratified recipe with the options the benchmark reads for its
+256^3 workload; the batched substep with the tuned launch shape on members of 256 to 512
+cells a side."""
+import numpy as np
+import pytest
+
+from oracle import fld as O
+from paper_2503_02764_gb300 import autotune
+from paper_2503_02764_gb300 import inputs as I
+from gpu_util import (torch_cuda, library, dev, host, maxrel, consts_of, ebc_dev,
+                      bench_grid_options)
+
+pytestmark = pytest.mark.gpu
+
+# 128 x 96 x 64 cells, x and y periodic, z Dirichlet: the levels 128, 64, 32 and 16 cells
+# wide take the z-marching sweep, the coarser ones the half sweeps and the one-block tail
+BOX = ((64, 96, 128), (1 / 128, 1 / 96, 1 / 64), ((0, 0), (0, 0), (2, 2)), 4e-5, 1.0)
+
+_ORACLE = {}
+
+
+def _problem(shape, bc, sigma, seed, ell=4.0):
+    rng = np.random.default_rng(seed)
+    D = I.lognormal(rng, shape, sigma, ell)
+    E = 1.0 + rng.uniform(0, 1, shape)
+    Eb = {}
+    nd = len(shape)
+    for d in range(nd):
+        for s in (0, 1):
+            if bc[d][s] == 2:
+                fs = tuple(n for a, n in enumerate(shape) if a != nd - 1 - d)
+                Eb[(d, s)] = 1.0 + rng.uniform(0, 1, fs)
+    return D, E, Eb
+
+
+def _oracle(key, shape, h, bc, dt, D, E, Eb):
+    if key not in _ORACLE:
+        _ORACLE[key] = O.diffuse(E, D, h, bc, Eb, dt,
+                                 method="lu" if E.size <= 4096 else
+                                 "splu" if E.size <= 20000 else "pcg")
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("inner", [2, 3])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_inner_cycles_zmarch_graph_box(precision, inner):
+    """The solve as the benchmark runs it (smoother 2, V(1,1), `inner` FP32 V-cycles per
+    refinement step, the V-cycle replayed from a CUDA graph) matches the oracle to 1e-10;
+    the replay (second call) and a run without graphs give the same iterate bit for bit."""
+    torch = torch_cuda()
+    fld = library()
+    shape, h, bc, dt, sigma = BOX
+    D, E, Eb = _problem(shape, bc, sigma, 4242)
+    xo = _oracle("box", shape, h, bc, dt, D, E, Eb)
+    packed = dev(torch, I.pack_dirichlet(shape, bc, Eb))
+    Dd = dev(torch, D)
+    res = []
+    for graph in (1, 0):
+        hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-12, max_cycles=30,
+                        smoother=2, nu1=1, nu2=1, inner=inner, graph=graph)
+        Ed = dev(torch, E)
+        st = hd.diffuse(dt, Dd, packed, Ed, raise_on_error=False)
+        assert st["status"] in (0, 3) and st["rel_resid"] < 1e-10, st
+        if graph:                              # the same handle again: the graph is replayed
+            Ed2 = dev(torch, E)
+            st2 = hd.diffuse(dt, Dd, packed, Ed2, raise_on_error=False)
+            assert st2["cycles"] == st["cycles"] and np.array_equal(host(Ed2), host(Ed))
+        res.append((host(Ed).reshape(shape), st["cycles"]))
+        hd.close()
+    for x, _ in res:
+        assert maxrel(x, xo) < 1e-10, maxrel(x, xo)
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
+SMALL = [
+    ((256,), (1 / 256,), ((0, 0),), 0.002, 1.0),
+    ((80, 96), (1.0, 1.0), ((0, 0), (0, 0)), 5.0, 1.0),
+    ((40, 36, 128), (1.0, 1.0, 1.0), ((0, 0), (1, 2), (2, 1)), 0.8, 1.0),
+    ((9, 11, 13), (0.1, 0.1, 0.1), ((1, 2), (0, 0), (2, 1)), 0.004, 1.0),
+]
+
+
+@pytest.mark.parametrize("smoother", [0, 2])
+@pytest.mark.parametrize("inner", [2, 3])
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("shape,h,bc,dt,sigma", SMALL)
+def test_inner_cycles_small_shapes(shape, h, bc, dt, sigma, precision, inner, smoother):
+    """inner > 1 on 1D, 2D and 3D grids with every boundary kind, both smoothers."""
+    torch = torch_cuda()
+    fld = library()
+    D, E, Eb = _problem(shape, bc, sigma, 31 + shape[0])
+    xo = _oracle(("small", shape), shape, h, bc, dt, D, E, Eb)
+    packed = I.pack_dirichlet(shape, bc, Eb)
+    hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-12, max_cycles=40,
+                    smoother=smoother, nu1=1, nu2=1, inner=inner, graph=1)
+    Ed = dev(torch, E)
+    st = hd.diffuse(dt, dev(torch, D), dev(torch, packed) if packed.size else None, Ed,
+                    raise_on_error=False)
+    assert st["status"] in (0, 3) and st["rel_resid"] < 1e-10, st
+    assert maxrel(host(Ed).reshape(shape), xo) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_step_with_bench_options_stratified(precision):
+    """Two whole substeps (limiter, solve, exchange) of the stratified recipe at 64^3 with
+    exactly the benchmark's options (tuned choice, tol 1e-10, graphs on): E and T match
+    the oracle's substeps to 1e-10."""
+    torch = torch_cuda()
+    fld = library()
+    P = I.stratified_3d(64)
+    opts = bench_grid_options(precision)
+    hd = fld.Handle(P.shape, P.h, P.bc, precision=precision, tol=1e-10, max_cycles=50,
+                    **opts)
+    rho, Td, Ed = dev(torch, P.rho), dev(torch, P.T), dev(torch, P.E)
+    ebc = ebc_dev(torch, P)
+    consts, op = consts_of(fld, P), fld.make_opacity(P.opacity)
+    T, E = P.T.copy(), P.E.copy()
+    for _ in range(2):
+        st = hd.step(consts, op, P.dt, rho, Td, Ed, ebc)
+        assert st["rel_resid"] <= 1e-10, st
+        T, E, _ = O.step(P.rho, T, E, P.h, P.bc, P.E_bc, P.dt, P.c, P.a_r, P.gamma, P.R_gas,
+                         P.opacity, P.limiter, method="pcg")
+    err = maxrel(host(Ed).reshape(P.shape), E)
+    assert err < 1e-10, (opts, err)
+    assert maxrel(host(Td).reshape(P.shape), T) < 1e-10
+
+
+def test_batch_tuned_shape_large_members():
+    """The batched substep with the launch shape the benchmark runs (the cached best for
+    the 512-member batch; on a GPU without an entry the GB300 choice: 1024 threads, no
+    cluster, V(1,1), 2 FP32 V-cycles per refinement step), graphs on, tol 1e-10, on three
+    members of 256 to 512 cells a side and three small ones; every problem against the
+    oracle's substep."""
+    torch = torch_cuda()
+    fld = library()
+    kw = autotune.batch_options(I.batch_shapes(512)) or dict(block=1024, cluster=1, nu1=1,
+                                                             nu2=1, inner=2)
+    ps = [I.batch_member(p, nmin=256, nmax=512) for p in range(3)] + \
+        I.batch(3, nmin=32, nmax=64, seed_base=I.SEED_BASE + 17)
+    b = fld.Batch([(p.shape, p.h, p.bc) for p in ps], tol=1e-10, max_cycles=50, graph=1, **kw)
+    cat = lambda xs: np.concatenate([np.ascontiguousarray(x).ravel() for x in xs])
+    rd, Td, Ed = dev(torch, cat([p.rho for p in ps])), dev(torch, cat([p.T for p in ps])), \
+        dev(torch, cat([p.E for p in ps]))
+    consts = fld.make_consts(1.0, 1.0, 5.0 / 3.0, 1.0)
+    ops = [fld.make_opacity(p.opacity) for p in ps]
+    rc, st = b.step(consts, ops, [p.dt for p in ps], rd, Td, Ed)
+    assert rc == 0, st
+    T, E = host(Td), host(Ed)
+    o = 0
+    for p, s in zip(ps, st):
+        assert s["rel_resid"] <= 1e-10, s
+        To, Eo, _ = O.step(p.rho, p.T, p.E, p.h, p.bc, p.E_bc, p.dt, p.c, p.a_r, p.gamma,
+                           p.R_gas, p.opacity, p.limiter, method="pcg")
+        Ep, Tp = E[o:o + p.ncells].reshape(p.shape), T[o:o + p.ncells].reshape(p.shape)
+        o += p.ncells
+        assert maxrel(Ep, Eo) < 1e-10, (p.name, kw, maxrel(Ep, Eo), s)
+        assert maxrel(Tp, To) < 1e-10, (p.name, kw, maxrel(Tp, To))

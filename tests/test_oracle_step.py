@@ -84,3 +84,11 @@ def test_recipes_are_seeded_and_shaped():
     assert all(32 <= s <= 40 for p in m for s in p.shape)
     packed = I.pack_dirichlet(a.shape, a.bc, a.E_bc)
     assert packed.size == 2 * 10 * 16
+
+
+def test_batch_shapes_without_fields_match_the_members():
+    # the autotuner's signature of the 512-member batch is computed from these shapes
+    for p in (0, 1, 7, 300, 511):
+        assert I.batch_member_shape(p) == I.batch_member(p).shape
+    assert [m.shape for m in I.batch_shapes(4, nmin=32, nmax=40)] == \
+        [m.shape for m in I.batch(4, nmin=32, nmax=40)]

@@ -54,6 +54,39 @@ def test_static_solve_matches_handle_solve_twice(precision, tol):
             assert maxrel(host(Es), host(Eref)) < tol, (call, maxrel(host(Es), host(Eref)))
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10), (2, 1e-10)])
+def test_static_solve_at_the_cell_limit_allocates_nothing(precision, tol):
+    """A 1D grid of exactly 131072 cells with Dirichlet faces, the deepest level pyramid
+    the limit admits (15 levels, where the workspace's fit check and the 256-byte
+    alignment of its pieces matter most): the same result as the handle solve on two
+    calls in a row, and the device's free memory is unchanged across repeated calls."""
+    torch = torch_cuda()
+    fld = library()
+    n = 131072
+    shape, h, bc = (n,), (1.0 / n,), ((2, 2),)
+    D, E, packed = _case(shape, bc, 5)
+    dt = 10.0 / n ** 2
+    opts = fld.make_opts(precision=precision, tol=1e-13, max_cycles=80)
+    hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-13, max_cycles=80)
+    Dd, ebc = dev(torch, D), dev(torch, packed)
+    Eref = dev(torch, E)
+    ref = hd.diffuse(dt, Dd, ebc, Eref, raise_on_error=False)
+    assert ref["status"] in (0, 3)
+    grid = fld.make_grid(shape, h, bc)
+    outs = [dev(torch, E) for _ in range(3)]
+    # the first call loads the library's kernels and its array on this device
+    fld.fld_diffuse_static(grid, opts, dt, Dd, ebc, outs[0], raise_on_error=False)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for Es in outs[1:]:
+        st = fld.fld_diffuse_static(grid, opts, dt, Dd, ebc, Es, raise_on_error=False)
+        assert st["status"] == ref["status"] and st["cycles"] == ref["cycles"], (st, ref)
+        assert maxrel(host(Es), host(Eref)) < tol, maxrel(host(Es), host(Eref))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_static_solve_rejects_oversized_grid():
     # the size check runs on the host before any device work
     from paper_2503_02764_gb300 import fld
