@@ -127,6 +127,7 @@ struct fld_handle {
     float* dfb[2] = {nullptr, nullptr};                            // right-hand side (hi, lo)
     float* dfK[2] = {nullptr, nullptr};                            // coefficient K (hi, lo)
     double* Dscratch = nullptr;
+    double* krscratch = nullptr;     // kappa rho of the substep (limiter -> exchange)
     double* partials = nullptr;
     int norm_blocks = 0;              // blocks (and partial sums) of the norm kernels
     DevScalars* scal = nullptr;       // device
@@ -683,6 +684,7 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
         rc = rc ? rc : dalloc(h, &h->dfK[q], n0);
     }
     rc = rc ? rc : dalloc(h, &h->Dscratch, n0);
+    rc = rc ? rc : dalloc(h, &h->krscratch, n0);
     h->norm_blocks = NORM_BLOCKS_PER_SM * num_sms();
     rc = rc ? rc : dalloc(h, &h->partials, h->norm_blocks);
     rc = rc ? rc : dalloc(h, &h->scal, 1);
@@ -723,13 +725,11 @@ fld_status fld_set_opts(fld_handle* h, const fld_opts* o) {
 
 int fld_num_levels(const fld_handle* h) { return h ? h->nlev : 0; }
 
-fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op, const double* E,
-                       const double* rho, const double* T, const double* E_bc, double* D,
-                       double* lambda, void* stream) {
-    if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho || !D) return FLD_ERR_ARG;
-    if (op->kind != FLD_OPACITY_CONST && !T) return FLD_ERR_ARG;
-    if (has_dirichlet(h->g) && !E_bc && h->o.limiter != FLD_LIMITER_DIFFUSION) return FLD_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+namespace {
+// the limiter of a handle; kr (nullable) receives kappa rho for the exchange of the same step
+fld_status limiter_impl(fld_handle* h, const fld_consts* k, const fld_opacity* op, const double* E,
+                        const double* rho, const double* T, const double* E_bc, double* D,
+                        double* lambda, double* kr, cudaStream_t s) {
     // double-FP32 mode: E split once into FP32 pairs (the level-0 FP32 buffers are free
     // until the solve), so the limiter forms the gradient without FP64 arithmetic
     const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF;
@@ -740,10 +740,32 @@ fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op
         run(h, "split_df", 0, h->ncell, s, [&] { launch_split_df(h->ncell, E, Eh, El, s); });
     run(h, "limiter", 0, h->ncell, s, [&] {
         launch_limiter(h->lv[0], h->g.h, E, rho, T, E_bc, h->bc_off, to_op(op), k->c, h->o.limiter,
-                       dfmode, D, lambda, &h->scal->err, s, Eh, El);
+                       dfmode, D, lambda, &h->scal->err, s, Eh, El, kr);
     });
     FLD_CK(cudaGetLastError());
     return FLD_OK;
+}
+
+fld_status exchange_impl(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
+                         const double* rho, double* T, double* E, const double* kr,
+                         cudaStream_t s) {
+    run(h, "exchange", 0, h->ncell, s, [&] {
+        launch_exchange(h->ncell, rho, T, E, to_op(op), dt * k->c, k->a_r,
+                        k->R_gas / (k->gamma - 1.0), h->o.precision == FLD_PREC_MIXED_DF,
+                        &h->scal->err, s, kr);
+    });
+    FLD_CK(cudaGetLastError());
+    return FLD_OK;
+}
+}  // namespace
+
+fld_status fld_limiter(fld_handle* h, const fld_consts* k, const fld_opacity* op, const double* E,
+                       const double* rho, const double* T, const double* E_bc, double* D,
+                       double* lambda, void* stream) {
+    if (!h || !consts_ok(k) || !op_ok(op) || !E || !rho || !D) return FLD_ERR_ARG;
+    if (op->kind != FLD_OPACITY_CONST && !T) return FLD_ERR_ARG;
+    if (has_dirichlet(h->g) && !E_bc && h->o.limiter != FLD_LIMITER_DIFFUSION) return FLD_ERR_ARG;
+    return limiter_impl(h, k, op, E, rho, T, E_bc, D, lambda, nullptr, (cudaStream_t)stream);
 }
 
 fld_status fld_coupling(fld_handle* h, const fld_consts* k, const fld_opacity* op,
@@ -774,13 +796,7 @@ fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* o
                         const double* rho, double* T, double* E, void* stream) {
     if (!h || !consts_ok(k) || !op_ok(op) || !rho || !T || !E || !(dt >= 0) || !std::isfinite(dt))
         return FLD_ERR_ARG;
-    run(h, "exchange", 0, h->ncell, (cudaStream_t)stream, [&] {
-        launch_exchange(h->ncell, rho, T, E, to_op(op), dt * k->c, k->a_r,
-                        k->R_gas / (k->gamma - 1.0), h->o.precision == FLD_PREC_MIXED_DF,
-                        &h->scal->err, (cudaStream_t)stream);
-    });
-    FLD_CK(cudaGetLastError());
-    return FLD_OK;
+    return exchange_impl(h, k, op, dt, rho, T, E, nullptr, (cudaStream_t)stream);
 }
 
 fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
@@ -790,13 +806,15 @@ fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, d
         return FLD_ERR_ARG;
     if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    fld_status rc = fld_limiter(h, k, op, E, rho, T, E_bc, h->Dscratch, nullptr, stream);
+    // the limiter freezes kappa rho at (rho, T^n) for the exchange (one opacity evaluation
+    // per cell and step)
+    fld_status rc = limiter_impl(h, k, op, E, rho, T, E_bc, h->Dscratch, nullptr, h->krscratch, s);
     if (rc) return rc;
     // a solve that stopped at max_cycles still completes the substep from its last iterate
     // (the status reports it); any other failure stops here
     const fld_status rs = diffuse_impl(h, dt, h->Dscratch, E_bc, E, stats, s);
     if (rs != FLD_OK && rs != FLD_ERR_NOT_CONVERGED) return rs;
-    rc = fld_exchange(h, k, op, dt, rho, T, E, stream);
+    rc = exchange_impl(h, k, op, dt, rho, T, E, h->krscratch, s);
     if (rc) return rc;
     rc = fld_get_status(h, stream);
     return rc ? rc : rs;

@@ -207,38 +207,47 @@ __device__ __forceinline__ df fetch_Edf(const Lvl& L, const float* __restrict__ 
 
 __device__ __forceinline__ bool f32_ok(double v) { return v > 1e-30 && v < 1e30; }
 
+// Root of alpha T + beta T^4 = q (alpha, q > 0, beta >= 0): Newton in FP32 on a scaled
+// form of the quartic (all quantities O(1)) from FP32 images of the coefficients, then
+// one FP64 Newton step whose residual is FP64 and whose derivative is the FP32 one (the
+// step is ~1e-7 T, so the derivative's 1e-7 relative error leaves ~1e-14 T). The FP32
+// images and the seed's FP64 value are converted in integer arithmetic. Coefficients
+// outside the FP32 range take a plain FP64 Newton iteration from the upper bound.
 __device__ __forceinline__ double exchange_root(double alpha, double beta, double q) {
-    const float af = (float)alpha, bf = (float)beta, qf = (float)q;
-    const float T1 = qf / af;                       // root if beta were 0
-    const float T1sq = T1 * T1;
-    const float g = (bf * T1sq) * (T1sq / qf);      // beta T1^4 / q
-    const bool fast = f32_ok(alpha) && f32_ok(q) && (beta == 0.0 || f32_ok(beta)) &&
-                      T1 > 1e-9f && T1 < 1e9f && g < 1e30f;
-    if (fast) {
-        float x = 1.f, scale = T1;
-        if (g <= 1.f) {
-            // phi(x) = g x^4 + x - 1, root in (0.72, 1]
+    const bool bzero = (__double_as_longlong(beta) << 1) == 0;
+    if (in_f32_range(alpha) && in_f32_range(q) && (bzero || in_f32_range(beta))) {
+        const float af = f32_near_pos(alpha), qf = f32_near_pos(q);
+        const float bf = bzero ? 0.f : f32_near_pos(beta);
+        const float T1 = qf / af;                       // root if beta were 0
+        const float T1sq = T1 * T1;
+        const float g = (bf * T1sq) * (T1sq / qf);      // beta T1^4 / q
+        if (T1 > 1e-9f && T1 < 1e9f && g < 1e30f) {
+            float x = 1.f, scale = T1;
+            if (g <= 1.f) {
+                // phi(x) = g x^4 + x - 1, root in (0.72, 1]
 #pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const float x2 = x * x;
-                x -= (fmaf(g * x2, x2, x) - 1.f) / fmaf(4.f * g * x2, x, 1.f);
-            }
-        } else {
-            // psi(y) = y^4 + h y - 1 with h = g^(-1/4), T = y T1 h, root in (0.8, 1]
-            const float hh = rsqrtf(sqrtf(g));
-            scale = T1 * hh;
+                for (int it = 0; it < 8; ++it) {
+                    const float x2 = x * x;
+                    x -= (fmaf(g * x2, x2, x) - 1.f) / fmaf(4.f * g * x2, x, 1.f);
+                }
+            } else {
+                // psi(y) = y^4 + h y - 1 with h = g^(-1/4), T = y T1 h, root in (0.8, 1]
+                const float hh = rsqrtf(sqrtf(g));
+                scale = T1 * hh;
 #pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const float x2 = x * x;
-                x -= (fmaf(x2, x2, hh * x) - 1.f) / fmaf(4.f * x2, x, hh);
+                for (int it = 0; it < 8; ++it) {
+                    const float x2 = x * x;
+                    x -= (fmaf(x2, x2, hh * x) - 1.f) / fmaf(4.f * x2, x, hh);
+                }
             }
+            const float Tf = x * scale;
+            const double T = f64_of_pos(Tf);
+            // one FP64 Newton step: FP64 residual, FP32 derivative
+            const double T2 = T * T;
+            const double f = fma(beta * T2, T2, fma(alpha, T, -q));
+            const float fpf = fmaf(4.f * bf * Tf * Tf, Tf, af);
+            return fma(-f, f64_of_pos(__frcp_rn(fpf)), T);
         }
-        const double T = (double)x * (double)scale;
-        // one FP64 Newton step: FP64 residual, FP32 derivative
-        const double T2 = T * T;
-        const double f = fma(beta * T2, T2, fma(alpha, T, -q));
-        const float fpf = fmaf(4.f * bf * (float)T2, (float)T, af);
-        return fma(-f, (double)__frcp_rn(fpf), T);
     }
     // outside the FP32 range: plain FP64 Newton from the upper bound
     double x = q / alpha;
@@ -256,9 +265,13 @@ __device__ __forceinline__ double exchange_root(double alpha, double beta, doubl
 // ----------------------------------------------------------------- limiter, one cell
 // R = |grad E| / (kappa rho E) (Eq. fld_R), lambda = (2 + R)/(6 + 3R + R^2)
 // (Eq. fld_lambda), D = c lambda / (kappa rho) (Eq. fld_F), grad E by the 5-point
-// 4th-order difference. With v = 1/(kappa rho E), D = c lambda E v: two reciprocals and
-// one square root, by FP32-seeded Newton-Raphson where the operands allow it (FP64
-// issues at a small fraction of the FP32 rate). Returns false on a domain error.
+// 4th-order difference. With a = kappa rho E and g = |grad E| (R = g/a), multiplying the
+// limiter's numerator and denominator by a^2 gives
+//   D = c E (2a + g) / (6a^2 + 3ag + g^2),
+// one square root and one division (FP32-seeded Newton-Raphson where the operands allow
+// it): FP64 issues at a small fraction of the FP32 rate here. Minerbo's limiter and
+// operands outside the FP32 range take R itself. kr_out receives kappa rho (the exchange
+// of the same substep reuses it). Returns false on a domain error.
 template <bool kTables = true>
 __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
                                              const double* __restrict__ E,
@@ -266,12 +279,14 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
                                              const double* __restrict__ T,
                                              const double* __restrict__ Ebc, const BcOff& bo,
                                              const Opacity& op, double c, int mode, int i, int j,
-                                             int k, long long p, double& Dout, double& lmout) {
+                                             int k, long long p, double& Dout, double& lmout,
+                                             double* kr_out = nullptr, bool want_lm = true) {
     const double Ec = E[p], r = rho[p];
     const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
     const double kap = opacity_eval<kTables>(op, r, t);
     if (!(pos_finite(Ec) && pos_finite(r) && pos_finite(t) && pos_finite(kap))) return false;
     const double kr = kap * r;
+    if (kr_out) *kr_out = kr;
     double lm = 1.0 / 3.0;
     if (mode != FLD_LIMITER_DIFFUSION) {
         double g2 = 0.0;
@@ -283,10 +298,21 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
             const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
             g2 = fma(g, g, g2);
         }
-        const double m = kr * Ec;
-        if (in_f32_range(m) && (g2 == 0.0 || in_f32_range(g2))) {
-            const double v = rcp_nr(m);
-            const double R = g2 > 0.0 ? g2 * rsqrt_nr(g2, 2) * v : 0.0;
+        const double a = kr * Ec;
+        const bool gzero = __double_as_longlong(g2) == 0;
+        if (mode == FLD_LIMITER_LP && in_f32_range(a) && (gzero || in_f32_range(g2))) {
+            const double g = gzero ? 0.0 : sqrt_nr(g2);
+            const double den = fma(a, fma(6.0, a, 3.0 * g), g2);
+            const double n2 = fma(2.0, a, g);
+            if (in_f32_range(den)) {
+                Dout = div_nr((c * Ec) * n2, den);
+                if (want_lm) lmout = div_nr(a * n2, den);
+                return true;
+            }
+        }
+        if (in_f32_range(a) && (gzero || in_f32_range(g2))) {
+            const double v = rcp_nr(a);
+            const double R = gzero ? 0.0 : sqrt_nr(g2) * v;
             if (mode == FLD_LIMITER_MINERBO) {
                 lmout = minerbo_lambda(R);
             } else {
@@ -297,7 +323,7 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
             Dout = c * lmout * (Ec * v);
             return true;
         }
-        const double R = sqrt(g2) / m;
+        const double R = sqrt(g2) / a;
         lm = mode == FLD_LIMITER_MINERBO ? minerbo_lambda(R) : (2.0 + R) / (6.0 + 3.0 * R + R * R);
     }
     lmout = lm;
@@ -306,26 +332,35 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
 }
 
 // ----------------------------------------------------------------- exchange, one cell
-// Backward Euler on de/dt = +qdot, dE/dt = -qdot (Eqs. heating, qdot) with kappa from
-// (rho, T on entry): solves alpha T' + beta T'^4 = q (exchange_root) and sets
-// E' = (E + chi a_r T'^4)/(1 + chi). Returns false (cell unchanged) on a domain error.
+// Backward Euler on de/dt = +qdot, dE/dt = -qdot (Eqs. heating, qdot), given
+// kr = kappa rho (frozen at the step's start): chi = dt c kr, solves
+// alpha T' + beta T'^4 = q (exchange_root) with alpha = rho c_v, beta = a_r chi/(1+chi),
+// q = alpha T + chi E/(1+chi), and sets E' = (E + chi a_r T'^4)/(1 + chi)
+// = E/(1+chi) + beta T'^4. The caller checks r, t, er and kr.
+__device__ __forceinline__ void exchange_cell_kr(double r, double kr, double& t, double& er,
+                                                 double dtc, double a_r, double cv) {
+    const double chi = dtc * kr;
+    const double alpha = r * cv;
+    const double d1 = 1.0 + chi;
+    const double inv1 = in_f32_range(d1) ? rcp_nr(d1) : 1.0 / d1;
+    const double w = chi * inv1;
+    const double beta = w * a_r;
+    const double q = fma(w, er, alpha * t);
+    const double x = exchange_root(alpha, beta, q);
+    const double x2 = x * x;
+    er = fma(beta, x2 * x2, er * inv1);
+    t = x;
+}
+
+// The same with kappa from (rho, T on entry). Returns false (cell unchanged) on a domain
+// error.
 template <bool kTables = true>
 __device__ __forceinline__ bool exchange_cell(double r, double& t, double& er, const Opacity& op,
                                               double dtc, double a_r, double cv) {
     if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) return false;
     const double kap = opacity_eval<kTables>(op, r, t);
     if (!pos_finite(kap)) return false;
-    const double chi = dtc * kap * r;
-    const double alpha = r * cv;
-    const double d1 = 1.0 + chi;
-    const double inv1 = (d1 < 1e30) ? rcp_nr(d1) : 1.0 / d1;
-    const double w = chi * inv1;
-    const double beta = w * a_r;
-    const double q = fma(w, er, alpha * t);
-    const double x = exchange_root(alpha, beta, q);
-    const double x2 = x * x;
-    er = fma(chi * a_r, x2 * x2, er) * inv1;
-    t = x;
+    exchange_cell_kr(r, kap * r, t, er, dtc, a_r, cv);
     return true;
 }
 
@@ -367,7 +402,8 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
                                                 int i, int j, int k, long long p, double& Dout,
                                                 double& lmout, const float* __restrict__ Eh = nullptr,
                                                 const float* __restrict__ El = nullptr,
-                                                const df* ihd = nullptr) {
+                                                const df* ihd = nullptr,
+                                                double* kr_out = nullptr) {
     const double r = rho[p];
     const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
     df Ed;
@@ -388,6 +424,7 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
     const df kr = df_mul(kap, rd);
     const df m = df_mul(kr, Ed);
     if (!df_safe(m.hi)) return false;
+    if (kr_out) *kr_out = df_to_double_i(kr);
     df lm = {0.33333334f, -9.9341077e-09f};   // 1/3 as a double-FP32 pair
     if (mode != FLD_LIMITER_DIFFUSION) {
         df g2d = {0.f, 0.f};
@@ -449,14 +486,23 @@ __device__ __forceinline__ bool limiter_cell_df(const Lvl& L, const double* ih,
     return true;
 }
 
+// kr > 0: kappa rho given (frozen at the step's start); else kappa from (rho, T).
 __device__ __forceinline__ bool exchange_cell_df(double r, double& t, double& er,
-                                                 const Opacity& op, const DfConst& K) {
+                                                 const Opacity& op, const DfConst& K,
+                                                 double kr = 0.0) {
     if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) return false;
     const df rd = df_from_double_i(r), td = df_from_double_i(t), Ed = df_from_double_i(er);
     if (!(df_safe(rd.hi) && df_safe(td.hi) && df_safe(Ed.hi))) return false;
-    df kap;
-    if (!df_opacity(op, K, rd, td, kap)) return false;
-    const df chi = df_mul(df_mul({K.dtc_h, K.dtc_l}, kap), rd);
+    df chi;
+    if (kr > 0.0) {
+        const df krd = df_from_double_i(kr);
+        if (!df_safe(krd.hi)) return false;
+        chi = df_mul({K.dtc_h, K.dtc_l}, krd);
+    } else {
+        df kap;
+        if (!df_opacity(op, K, rd, td, kap)) return false;
+        chi = df_mul(df_mul({K.dtc_h, K.dtc_l}, kap), rd);
+    }
     if (!(chi.hi < 1e20f)) return false;
     const df d1 = df_add_f(chi, 1.f);
     const df w = df_div(chi, d1);                         // chi/(1+chi)

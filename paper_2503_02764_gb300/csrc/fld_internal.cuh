@@ -46,25 +46,63 @@ __device__ __forceinline__ bool pos_finite(double v) {
     return b > 0 && b < 0x7FF0000000000000LL;
 }
 
-// 1/sqrt(t) for t within the FP32 normal range: FP32 seed refined by Newton-Raphson on
-// f(y) = 1/y^2 - t, y <- y (3/2 - t y^2 / 2); each step squares the relative error
+// Format conversions for FP32 seeds in integer arithmetic (a conversion instruction runs
+// on the FP64 pipe of this GPU, at the FP64 rate):
+// f32_near_pos: the FP32 number nearest to v (ties rounded up), for 2^-126 <= v < 2^127:
+//   the double's exponent rebiased and its significand rounded to 24 bits, a carry moving
+//   it to the next binade;
+// f64_of_pos:   the exact FP64 value of a positive normal FP32 number.
+__device__ __forceinline__ float f32_near_pos(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return __uint_as_float((unsigned)((b + (1ull << 28)) >> 29) - (896u << 23));
+}
+__device__ __forceinline__ double f64_of_pos(float f) {
+    return __longlong_as_double(
+        (long long)(((unsigned long long)__float_as_uint(f) + (896ull << 23)) << 29));
+}
+
+// 1/sqrt(t) for 0 < t within the FP32 normal range: FP32 seed refined by Newton-Raphson
+// on f(y) = 1/y^2 - t, y <- y (3/2 - t y^2 / 2); each step squares the relative error
 // (~2^-22 -> ~2^-44 -> rounding). `steps` = 1 or 2.
 __device__ __forceinline__ double rsqrt_nr(double t, int steps) {
-    double y = (double)rsqrtf((float)t);
+    double y = f64_of_pos(rsqrtf(f32_near_pos(t)));
     const double ht = 0.5 * t;
     y = y * fma(-ht, y * y, 1.5);
     if (steps > 1) y = y * fma(-ht, y * y, 1.5);
     return y;
 }
 
-// 1/a for a within the FP32 normal range: FP32 reciprocal seed refined by Newton-Raphson
-// on f(y) = 1/y - a, y <- y + y (1 - a y); each step squares the relative error.
+// 1/a for 0 < a within the FP32 normal range (and 1/a too): FP32 reciprocal seed refined
+// by Newton-Raphson on f(y) = 1/y - a, y <- y + y (1 - a y); each step squares the
+// relative error.
 __device__ __forceinline__ double rcp_nr(double a) {
-    double y = (double)__frcp_rn((float)a);
+    double y = f64_of_pos(__frcp_rn(f32_near_pos(a)));
     double e = fma(-a, y, 1.0);
     y = fma(y, e, y);
     e = fma(-a, y, 1.0);
     return fma(y, e, y);
+}
+
+// n / d for n >= 0 and 0 < d within the FP32 normal range (and 1/d too): one Newton-
+// Raphson step on the FP32 reciprocal, the quotient, and one correction from its exact
+// remainder n - d q (Markstein's scheme): within a unit of rounding, five FP64 operations.
+__device__ __forceinline__ double div_nr(double n, double d) {
+    double y = f64_of_pos(__frcp_rn(f32_near_pos(d)));
+    y = fma(y, fma(-d, y, 1.0), y);
+    const double q = n * y;
+    return fma(fma(-d, q, n), y, q);
+}
+
+// sqrt(t) for 0 < t within the FP32 normal range: from the FP32 reciprocal square root
+// y0, s = t y0 corrected twice by s <- s + (t - s^2) y0 / 2 (a Newton step for s^2 = t
+// with the derivative's inverse taken from the seed): relative error 1.5 e0^2 after the
+// first, rounding after the second; five FP64 operations.
+__device__ __forceinline__ double sqrt_nr(double t) {
+    const float y0 = rsqrtf(f32_near_pos(t));
+    const double hy = f64_of_pos(0.5f * y0);
+    double s = t * f64_of_pos(y0);
+    s = fma(fma(-s, s, t), hy, s);
+    return fma(fma(-s, s, t), hy, s);
 }
 
 // |v| within [2^-99, 2^99] (safely inside the FP32 normal range), tested on the
@@ -137,12 +175,16 @@ bool opts_valid(const fld_opts* o);
 
 // ----------------------------------------------------------------- launchers
 // pointwise / limiter (k_pointwise.cu)
+// kr (nullable) in the exchange: kappa rho per cell, frozen by the limiter of the same
+// substep (which writes it when its own kr is non-null); without it kappa is evaluated
 void launch_exchange(long long n, const double* rho, double* T, double* E, Opacity op,
-                     double dtc, double a_r, double cv, int use_df, unsigned* err, cudaStream_t s);
+                     double dtc, double a_r, double cv, int use_df, unsigned* err, cudaStream_t s,
+                     const double* kr = nullptr);
 void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
                     double c, int mode, int use_df, double* D, double* lam, unsigned* err,
-                    cudaStream_t s, float* Eh = nullptr, float* El = nullptr);
+                    cudaStream_t s, float* Eh = nullptr, float* El = nullptr,
+                    double* kr = nullptr);
 // explicit coupling terms of the limiter pass (nullable outputs; v, vfr and pt together)
 void launch_coupling(const Lvl& L, const double* h, const double* E, const double* rho,
                      const double* T, const double* E_bc, const long long* bc_off, Opacity op,

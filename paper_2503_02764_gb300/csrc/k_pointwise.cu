@@ -21,20 +21,35 @@ namespace fld {
 // ~1e-14 T). Cells whose coefficients fall outside the FP32 range take a plain FP64
 // Newton iteration instead.
 
+// kr (nullable): kappa rho of every cell, frozen at the step's start by the limiter of the
+// same substep; without it kappa is evaluated from (rho, T).
 __global__ void k_exchange(long long n, const double* __restrict__ rho, double* __restrict__ T,
-                           double* __restrict__ E, Opacity op, double dtc, double a_r, double cv,
-                           int use_df, DfConst K, unsigned* err) {
+                           double* __restrict__ E, const double* __restrict__ kr, Opacity op,
+                           double dtc, double a_r, double cv, int use_df, DfConst K,
+                           unsigned* err) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[i];
         double t = T[i], er = E[i];
-        if (use_df && exchange_cell_df(rho[i], t, er, op, K)) {
+        const double kri = kr ? kr[i] : 0.0;
+        if (kr && !pos_finite(kri)) {
+            atomicOr(err, ERRBIT_DOMAIN);
+            continue;
+        }
+        if (use_df && exchange_cell_df(r, t, er, op, K, kri)) {
             T[i] = t;
             E[i] = er;
             continue;
         }
         t = T[i];
         er = E[i];
-        if (!exchange_cell(rho[i], t, er, op, dtc, a_r, cv)) {
+        if (kr) {
+            if (!(pos_finite(r) && pos_finite(t) && pos_finite(er))) {
+                atomicOr(err, ERRBIT_DOMAIN);
+                continue;
+            }
+            exchange_cell_kr(r, kri, t, er, dtc, a_r, cv);
+        } else if (!exchange_cell(r, t, er, op, dtc, a_r, cv)) {
             atomicOr(err, ERRBIT_DOMAIN);
             continue;
         }
@@ -54,13 +69,14 @@ DfConst make_dfconst(double c, double kappa0, double dtc, double a_r, double cv)
 }
 
 void launch_exchange(long long n, const double* rho, double* T, double* E, Opacity op,
-                     double dtc, double a_r, double cv, int use_df, unsigned* err, cudaStream_t s) {
+                     double dtc, double a_r, double cv, int use_df, unsigned* err, cudaStream_t s,
+                     const double* kr) {
     if (n <= 0) return;
     const int block = 256;
     long long nb = (n + block - 1) / block;
     if (nb > num_sms() * 32) nb = num_sms() * 32;
     const DfConst K = make_dfconst(0.0, op.kappa0, dtc, a_r, cv);
-    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, op, dtc, a_r, cv, use_df, K, err);
+    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, kr, op, dtc, a_r, cv, use_df, K, err);
 }
 
 // ----------------------------------------------------------------- limiter
@@ -75,12 +91,13 @@ __global__ void k_split_df(long long n, const double* __restrict__ v, float* __r
     }
 }
 
+// kr (nullable): receives kappa rho of every cell, for the exchange of the same substep.
 __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           const double* __restrict__ rho, const double* __restrict__ T,
                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
                           int mode, int use_df, DfConst K, const float* __restrict__ Eh,
                           const float* __restrict__ El, double* __restrict__ D,
-                          double* __restrict__ lam, unsigned* err) {
+                          double* __restrict__ lam, double* __restrict__ kr, unsigned* err) {
     const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
     df ihd[3];
     for (int d = 0; d < 3; ++d) ihd[d] = df_from_double(ih[d]);
@@ -89,19 +106,22 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
         for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
             const int j = rw % L.n[1], k = rw / L.n[1];
             const long long p = (long long)rw * L.n[0] + i;
-            double Dv, lm;
+            double Dv, lm, kv;
             if (use_df && limiter_cell_df(L, ih, E, rho, T, Ebc, bo, op, K, mode, i, j, k, p, Dv, lm,
-                                          Eh, El, ihd)) {
+                                          Eh, El, ihd, kr ? &kv : nullptr)) {
                 D[p] = Dv;
                 if (lam) lam[p] = lm;
+                if (kr) kr[p] = kv;
                 continue;
             }
-            if (!limiter_cell(L, ih, E, rho, T, Ebc, bo, op, c, mode, i, j, k, p, Dv, lm)) {
+            if (!limiter_cell(L, ih, E, rho, T, Ebc, bo, op, c, mode, i, j, k, p, Dv, lm,
+                              kr ? &kv : nullptr, lam != nullptr)) {
                 atomicOr(err, ERRBIT_DOMAIN);
                 continue;
             }
             D[p] = Dv;
             if (lam) lam[p] = lm;
+            if (kr) kr[p] = kv;
         }
 }
 
@@ -217,7 +237,7 @@ void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStr
 void launch_limiter(const Lvl& L, const double* h, const double* E, const double* rho,
                     const double* T, const double* E_bc, const long long* bc_off, Opacity op,
                     double c, int mode, int use_df, double* D, double* lam, unsigned* err,
-                    cudaStream_t s, float* Eh, float* El) {
+                    cudaStream_t s, float* Eh, float* El, double* kr) {
     BcOff bo;
     for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
     double3 ih = make_double3(1.0 / (12.0 * h[0]), L.ndim > 1 ? 1.0 / (12.0 * h[1]) : 0.0,
@@ -227,7 +247,7 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
     if (!(use_df && mode != FLD_LIMITER_DIFFUSION)) Eh = El = nullptr;
     k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, Eh, El, D,
-                                   lam, err);
+                                   lam, kr, err);
 }
 
 }  // namespace fld
