@@ -38,13 +38,14 @@ UNIT = "cell-updates/s"
 # algorithmic bytes per cell of each kernel family (FP64 = 8 B, FP32 = 4 B),
 # counting each array once per launch: reads + writes
 BYTES_PER_CELL = {
-    "limiter": 32.0,          # E, rho, T read; D written (power-law opacity)
+    "limiter": 40.0,          # E, rho, T read; D and kappa rho written (power-law opacity)
     "prep": 36.0,             # D, E read; K64, K32, b written
     "split_df": 16.0,         # E read; its FP32 (hi, lo) pair written
     "df_setup": 48.0,         # E, b, K read; their FP32 (hi, lo) pairs written
     "df_finish": 16.0,        # x (hi, lo) read; E written
     "sumsq": 8.0,             # b read
     "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
+    "resid64x": 40.0,         # x, e32, b, K read; x + e, r32 written
     "resid_df": 40.0,         # x (hi, lo), e32, b (hi, lo), K (hi, lo) read; x (hi, lo), r32 written
     "rbhalf32": 10.0,         # one colour: the other colour's x and every K read (faces),
     "rbhalf64": 20.0,         #   this colour's b read and x written
@@ -57,7 +58,7 @@ BYTES_PER_CELL = {
     "resid_restrict64": 24.0,
     "prolong32": 8.0,
     "prolong64": 16.0,
-    "exchange": 40.0,         # rho, T, E read; T, E written (kappa evaluated from rho, T)
+    "exchange": 48.0,         # rho, T, E, kappa rho read; T, E written
 }
 
 
@@ -71,12 +72,16 @@ def load_peaks():
 
 # FP64 operations per cell of the FP64-bound level-0 kernels, counted in their source for
 # an interior cell of the 3D workload (add, multiply = 1 flop, FMA = 2; the FP32 seeds and
-# the format conversions are not counted): the FP64 limiter with the Kramers opacity, the
-# FP64 exchange (FP32 Newton seed, one FP64 Newton step), the FP64 refinement residual.
+# the integer format conversions are not counted): the FP64 limiter with the Kramers
+# opacity (15 for kappa, 23 for the gradient, 29 for D from one square root and one
+# division), the FP64 exchange given kappa rho (FP32 Newton seed, one FP64 Newton step,
+# E'), the FP64 refinement residual with each face flux evaluated once (3D levels), and
+# the same with the correction x + e added in it.
 FP64_FLOPS_PER_CELL = {
-    "limiter": 76.0,
-    "exchange": 47.0,
-    "resid64": 33.0,
+    "limiter": 67.0,
+    "exchange": 29.0,
+    "resid64": 21.0,
+    "resid64x": 22.0,
 }
 
 

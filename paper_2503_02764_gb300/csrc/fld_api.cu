@@ -411,15 +411,26 @@ fld_status read_scalars(fld_handle* h, cudaStream_t s, double* sum, unsigned* er
     return FLD_OK;
 }
 
-// relative residual of x at level 0 (FP64), optional FP32 copy of the residual
-fld_status residual(fld_handle* h, double* x, float* r32, cudaStream_t s, double* rr,
-                    unsigned* err) {
+// relative residual of x at level 0 (FP64), optional FP32 copy of the residual. With e
+// (3D levels, where the z-marching kernel applies) the iterate is first corrected: x + e is
+// written to xo and the residual is that of xo.
+fld_status residual(fld_handle* h, const double* x, const float* e, double* xo, float* r32,
+                    cudaStream_t s, double* rr, unsigned* err) {
     const Lvl& L = h->lv[0];
-    run(h, "resid64", 0, L.ncell, s, [&] {
-        launch_resid64(L, x, h->d64[0].b, h->d64[0].K, r32, h->partials, h->norm_blocks, NORM_THREADS, s);
-    });
-    run(h, "finish_sum", 0, h->norm_blocks, s,
-        [&] { launch_finish_sum(h->partials, h->norm_blocks, &h->scal->sum, s); });
+    int nparts = h->norm_blocks;
+    if (resid64z_ok(L, h->norm_blocks)) {
+        run(h, e ? "resid64x" : "resid64", 0, L.ncell, s, [&] {
+            nparts = launch_resid64z(L, x, e, xo, h->d64[0].b, h->d64[0].K, r32, h->partials,
+                                     h->norm_blocks, s);
+        });
+    } else {
+        run(h, "resid64", 0, L.ncell, s, [&] {
+            launch_resid64(L, x, h->d64[0].b, h->d64[0].K, r32, h->partials, h->norm_blocks,
+                           NORM_THREADS, s);
+        });
+    }
+    run(h, "finish_sum", 0, nparts, s,
+        [&] { launch_finish_sum(h->partials, nparts, &h->scal->sum, s); });
     FLD_CK(cudaGetLastError());
     return read_scalars(h, s, rr, err);
 }
@@ -578,7 +589,7 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     if (dfmode) return diffuse_df(h, E, bsum, st, s);
     h->d64[0].x = E;
     double r2;
-    rc = residual(h, E, mixed ? h->d32[0].b : nullptr, s, &r2, &err);
+    rc = residual(h, E, nullptr, nullptr, mixed ? h->d32[0].b : nullptr, s, &r2, &err);
     if (rc != FLD_OK) return rc;
     double rel = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
     if (st) {
@@ -586,23 +597,41 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         st->resid_hist[0] = rel;
         st->levels = h->nlev;
     }
+    // mixed refinement on 3D levels: the correction is added inside the residual kernel,
+    // out of place, the iterate alternating between E and the level-0 FP64 scratch (free
+    // in this mode); it ends in E
+    const bool fused = mixed && resid64z_ok(L0, h->norm_blocks);
+    double* cur = E;
+    double* oth = h->d64[0].tmp;
     int cyc = 0;
+    rc = FLD_OK;
     while (rel > h->o.tol && cyc < h->o.max_cycles && std::isfinite(rel)) {
-        if (mixed) {
+        if (fused) {
             rc = vcycle32(h, s);
-            if (rc != FLD_OK) return rc;
+            if (rc != FLD_OK) break;
+            rc = residual(h, cur, h->d32[0].x, oth, h->d32[0].b, s, &r2, &err);
+            std::swap(cur, oth);
+        } else if (mixed) {
+            rc = vcycle32(h, s);
+            if (rc != FLD_OK) break;
             run(h, "add_correction", 0, L0.ncell, s,
                 [&] { launch_add_correction(L0.ncell, E, h->d32[0].x, s); });
-            rc = residual(h, E, h->d32[0].b, s, &r2, &err);
+            rc = residual(h, E, nullptr, nullptr, h->d32[0].b, s, &r2, &err);
         } else {
             vcycle<double>(h, h->d64, 0, s);
-            rc = residual(h, E, nullptr, s, &r2, &err);
+            rc = residual(h, E, nullptr, nullptr, nullptr, s, &r2, &err);
         }
-        if (rc != FLD_OK) return rc;
+        if (rc != FLD_OK) break;
         rel = std::sqrt(r2) / bnorm;
         ++cyc;
         if (st && cyc < 64) st->resid_hist[cyc] = rel;
     }
+    if (cur != E) {
+        const cudaError_t ce =
+            cudaMemcpyAsync(E, cur, sizeof(double) * L0.ncell, cudaMemcpyDeviceToDevice, s);
+        if (rc == FLD_OK && ce != cudaSuccess) rc = cuda_fail(ce);
+    }
+    if (rc != FLD_OK) return rc;
     if (st) {
         st->cycles = cyc;
         st->rel_resid = rel;

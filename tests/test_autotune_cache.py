@@ -57,8 +57,10 @@ def test_committed_cache_entries_are_well_formed():
     d = json.load(open(A.DEFAULT_CACHE))
     for gpu, entries in d.items():
         for sig, e in entries.items():
-            kind = sig.split(":")[0]
+            kind = sig.split(":")[0].split("-")[0]
             assert kind in ("grid", "batch"), sig
+            if "-" in sig.split(":")[0]:
+                assert sig.split(":")[0].split("-")[1] in A.PRECISION_NAMES.values(), sig
             best = e["best"]
             assert best["converged"] is True
             assert best["nu1"] + best["nu2"] >= 1
