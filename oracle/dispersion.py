@@ -173,3 +173,40 @@ def substep_amplification(dt, c, kappa, rho, a_r, T0, gamma, R_gas, D, ktilde2):
 def discrete_k2(k, h):
     """Eigenvalue of the 3-point second difference: (4/h^2) sin^2(k h / 2)."""
     return 4.0 / (h * h) * np.sin(0.5 * k * h) ** 2
+
+
+# ----------------------------------------------------------------- code-unit linear mode
+def code_units_background(ratio, B=1.0, angle_deg=45.0, rho0=1.0, T0=1.0, R_gas=1.0,
+                          gamma=5.0 / 3.0, kappa=1.0e4, c=1.0e4, k=2.0 * np.pi):
+    """Uniform radiative-equilibrium background in code units for the 3D linear-mode
+    workload: p0 = rho0 R_gas T0, E0 = a_r T0^4 with a_r set by the radiation-to-gas
+    pressure ratio (E0/3)/p0 = ratio, B of strength B in the x-z plane at angle_deg to
+    k = k x-hat (Heaviside-Lorentz form, as in Appendix B)."""
+    p0 = rho0 * R_gas * T0
+    a_r = 3.0 * ratio * p0 / T0 ** 4
+    th = np.deg2rad(angle_deg)
+    return dict(rho0=rho0, p0=p0, B=np.array([B * np.cos(th), 0.0, B * np.sin(th)]),
+                gamma=gamma, mu=None, kappa=kappa, T0=T0, E0=a_r * T0 ** 4, k=k, c=c,
+                a_r=a_r, R_gas=R_gas)
+
+
+def fast_mode(bg):
+    """The forward fast magnetosonic eigenpair of the Appendix-B system: the eigenvalue
+    with the largest real part, its eigenvector scaled so that the density component is
+    rho0 (a unit relative density amplitude). Returns (omega, u) with u over
+    (rho, v_x, v_y, v_z, p, B_y, B_z, E)."""
+    w, V = np.linalg.eig(mode_matrix(bg))
+    i = int(np.argmax(w.real))
+    u = V[:, i] / V[0, i] * bg["rho0"]
+    return w[i], u
+
+
+def gas_temperature_amplitude(bg, u):
+    """T_g,1 from the linearised ideal-gas law (Eq. ideal_gas_law_lin):
+    T_1 = T0 (p_1/p0 - rho_1/rho0)."""
+    return bg["T0"] * (u[4] / bg["p0"] - u[0] / bg["rho0"])
+
+
+def hydro_frozen_code(bg):
+    """Hydro-frozen (p, E) rates of a code-unit background (see hydro_frozen)."""
+    return hydro_frozen(bg)

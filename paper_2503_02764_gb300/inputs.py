@@ -233,31 +233,54 @@ def batch(nprob=512, seed_base=None, nmin=32, nmax=512):
     return [batch_member(p, seed_base, nmin, nmax) for p in range(nprob)]
 
 
+def linmode_amplitudes(ratio):
+    """Complex amplitudes (T_1, E_1) per unit relative density amplitude of the fast
+    magnetosonic eigenmode for the radiation-to-gas pressure ratio 0.1 or 1, as stored in
+    linmode_eigen.json (written by the oracle's write_linmode_eigen script from the
+    Appendix-B system: B = 1 at 45 degrees to k = 2 pi, rho0 = T0 = 1, kappa = c = 1e4)."""
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                    "linmode_eigen.json")))
+    m = d["modes"]["%g" % ratio]
+    return complex(*m["T1"]), complex(*m["E1"])
+
+
 def linear_mode_3d(n=512, ratio=1.0, amp=1e-4, seed=None, ny=None, nz=None,
-                   steps=100, dt=1e-3):
+                   steps=100, dt=1e-3, mode="eigen"):
     """3D periodic unit box driven by a linear perturbation along x.
 
     rho = 1, T0 = 1, R_gas = 1, gamma = 5/3, a_r = 3 x ratio (so that the
     radiation-to-gas pressure ratio a_r T^4/3 / (rho R_gas T) equals ratio),
     kappa = 1e4, c = 1e4 (D = 1/3 in the diffusion limit, c kappa rho = 1e8).
-    The mode is k = 2 pi x-hat with T1 = amp/2 cos(k x) and
-    E1 = 4 E0 amp cos(k x) (a radiation-temperature excess over the gas, so
-    that both the diffusion and the exchange act on it).
+    The mode is k = 2 pi x-hat with, per cell, X = X0 + amp Re(X_1 exp(i k x)):
+    mode "eigen" (ratio 0.1 or 1): T_1 and E_1 of the fast magnetosonic eigenmode with
+      B = 1 at 45 degrees to k, per unit relative density amplitude (so amp is the
+      relative density amplitude of the wave; the substep keeps rho fixed);
+    mode "excess": T_1 = 1/2, E_1 = 4 E0 (a radiation-temperature excess over the gas,
+      so that both the diffusion and the exchange act on it).
     """
     ny = n if ny is None else ny
     nz = n if nz is None else nz
     nx = n
     a_r = 3.0 * ratio
-    x = _cell_centres(nx)
-    cosx = np.cos(2.0 * np.pi * x)[None, None, :] * np.ones((nz, ny, nx))
-    T = 1.0 + 0.5 * amp * cosx
     E0 = a_r * 1.0
-    E = E0 * (1.0 + 4.0 * amp * cosx)
+    if mode == "eigen":
+        T1, E1 = linmode_amplitudes(ratio)
+    else:
+        T1, E1 = complex(0.5), complex(4.0 * E0)
+    x = _cell_centres(nx)
+    ph = np.exp(1j * 2.0 * np.pi * x)
+    ones = np.ones((nz, ny, 1))
+    T = (1.0 + amp * np.real(T1 * ph))[None, None, :] * ones
+    E = (E0 + amp * np.real(E1 * ph))[None, None, :] * ones
     return Problem(
-        name="linmode3d_%d_r%g" % (n, ratio), shape=(nz, ny, nx), h=(1.0 / nx, 1.0 / ny, 1.0 / nz),
+        name="linmode3d_%d_r%g_%s" % (n, ratio, mode), shape=(nz, ny, nx),
+        h=(1.0 / nx, 1.0 / ny, 1.0 / nz),
         bc=((PERIODIC, PERIODIC),) * 3, c=1.0e4, a_r=a_r, gamma=5.0 / 3.0, R_gas=1.0,
         opacity=(OPACITY_CONST, 1.0e4, 0.0, 0.0), dt=dt,
-        rho=np.ones((nz, ny, nx)), T=T, E=E, tol=1e-10, steps=steps)
+        rho=np.ones((nz, ny, nx)), T=np.ascontiguousarray(T), E=np.ascontiguousarray(E),
+        tol=1e-10, steps=steps)
 
 
 def opacity_table(kappa0, log_rho=(-2.0, 0.3), log_T=(-0.1, 1.05), n_rho=24, n_T=30,

@@ -92,14 +92,18 @@ def test_lognormal_1024_full_size_step(precision, tol):
     assert maxrel(host(Td).reshape(P.shape), To) < tol
 
 
-@pytest.mark.parametrize("n,steps,ratio", [(32, 100, 1.0), (32, 100, 0.1), (512, 100, 1.0)])
+@pytest.mark.parametrize("n,steps,ratio", [(32, 100, 1.0), (32, 100, 0.1), (512, 100, 1.0),
+                                           (512, 100, 0.1)])
 def test_linear_mode_decay(n, steps, ratio):
-    """The 3D linear-mode workload: the (e_1, E_1) amplitudes of the cos(2 pi x) mode after
-    `steps` substeps equal G^steps applied to the initial ones, G the exact per-step matrix
-    of the split substep (backward-Euler diffusion then exchange, lambda = 1/3 + O(R^2))."""
-    # amplitude 1e-4 (the workload's): second-order terms do not project on cos(2 pi x),
+    """The 3D linear-mode workload seeded with the fast magnetosonic eigenmode (B at 45
+    degrees to k, amplitude 1e-4): the complex (e_1, E_1) amplitudes of the k = 2 pi mode
+    after `steps` substeps equal G^steps applied to the initial ones, G the exact per-step
+    matrix of the split substep (backward-Euler diffusion then exchange, lambda = 1/3 +
+    O(R^2)), to 1e-6; and the mode decays as the hydro-frozen (p, E) rate of the
+    dispersion relation, exp(-t |omega_slow|), to the scheme's first-order error."""
+    # amplitude 1e-4 (the workload's): second-order terms do not project on the k mode,
     # so the linear prediction holds to O(amp^2) relative. The solve tolerance must be
-    # small against the perturbation (E_1/E_0 = 4e-4), hence tol 1e-12 with the FP64
+    # small against the perturbation (E_1/E_0 ~ 5e-4), hence tol 1e-12 with the FP64
     # refinement residual.
     torch = torch_cuda()
     fld = library()
@@ -109,14 +113,13 @@ def test_linear_mode_decay(n, steps, ratio):
     hd = handle_for(fld, P, precision=fld.PREC_MIXED, tol=1e-12, max_cycles=60)
     rho, T, E = dev(torch, P.rho), dev(torch, P.T), dev(torch, P.E)
     x = (np.arange(n) + 0.5) / n
-    cosx = np.cos(2 * np.pi * x)
+    ph = np.exp(-2j * np.pi * x)
 
     def modes(Tf, Ef):
-        # average over y, z, then project on cos(2 pi x)
+        # average over y, z, then the complex amplitude of exp(2 pi i x)
         e = (P.rho * P.R_gas * Tf / (P.gamma - 1)).reshape(P.shape).mean(axis=(0, 1))
         Em = Ef.reshape(P.shape).mean(axis=(0, 1))
-        return np.array([2.0 / n * np.sum((e - e.mean()) * cosx),
-                         2.0 / n * np.sum((Em - Em.mean()) * cosx)])
+        return np.array([2.0 / n * np.sum(e * ph), 2.0 / n * np.sum(Em * ph)])
 
     v0 = modes(P.T, P.E)
     consts, op = consts_of(fld, P), fld.make_opacity(P.opacity)
@@ -129,3 +132,11 @@ def test_linear_mode_decay(n, steps, ratio):
                                    Disp.discrete_k2(2 * np.pi, 1.0 / n))
     want = np.linalg.matrix_power(G, steps) @ v0
     assert np.all(np.abs(got - want) <= 1e-6 * np.abs(want).max()), (got, want)
+    # against the continuum: the hydro-frozen slow rate of the Appendix-B system
+    bg = Disp.code_units_background(ratio)
+    lam = -np.max(Disp.hydro_frozen(bg).imag)
+    f = 4 * bg["E0"] / (bg["p0"] / (bg["gamma"] - 1) + 4 * bg["E0"])
+    a = P.dt * D * Disp.discrete_k2(2 * np.pi, 1.0 / n)
+    cont = np.exp(-steps * P.dt * lam)
+    decay = abs(got[1]) / abs(v0[1])
+    assert abs(decay - cont) <= 1.5 * steps * f * a * a * cont + 1e-6, (decay, cont)

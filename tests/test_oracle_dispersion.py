@@ -108,3 +108,87 @@ def test_substep_generator_is_hydro_frozen_block(ratio):
     J = c * kap * np.array([[-beta, 1.0], [beta, -1.0]]) - np.diag([0, D * (2 * np.pi) ** 2])
     # the small rate is a difference of O(1e9) numbers: relative rounding ~1e-8
     assert np.allclose(np.sort(np.linalg.eigvals(J).real), frozen, rtol=1e-7)
+
+
+# ---------------------------------------------------------------- the 3D linear-mode seed
+@pytest.mark.parametrize("case", ["table2_weak", "table3_strong"])
+def test_fast_mode_is_the_printed_fast_eigenvalue(case):
+    # fast_mode picks the forward fast wave: on the paper's two backgrounds its frequency
+    # is the printed fast eigenvalue of Table 2 / Table 3
+    w, u = Disp.fast_mode(_bg(case))
+    re, im = GOLD[case]["fast"]
+    assert w.real == pytest.approx(re, rel=2e-5)
+    assert w.imag == pytest.approx(im, rel=5e-4)
+
+
+@pytest.mark.parametrize("ratio", [0.1, 1.0])
+def test_fast_mode_eigenpair_code_units(ratio):
+    bg = Disp.code_units_background(ratio)
+    M = Disp.mode_matrix(bg)
+    w, u = Disp.fast_mode(bg)
+    # an eigenpair of the Appendix-B matrix, scaled to a unit relative density amplitude
+    # (M spans 1 to 1e9: the eigensolver's backward error is ~1e-12 of its norm)
+    assert np.linalg.norm(M @ u - w * u) <= 1e-10 * np.linalg.norm(M) * np.linalg.norm(u)
+    assert u[0] == bg["rho0"]
+    # the forward fast wave: a root of the octic, the largest real part of all modes
+    r = np.roots(Disp.octic(bg))
+    assert np.min(np.abs(r - w)) <= 1e-6 * abs(w)     # the octic's roots to its conditioning
+    assert w.real >= np.max(Disp.eigenfrequencies(bg).real) * (1 - 1e-12)
+    # slower than light-speed-free ideal MHD would allow and damped
+    assert w.imag < 0
+    # optically thick (kappa rho L = 1e4): radiation locked to the gas, E_1/E0 = 4 T_1/T0
+    # up to the exchange lag O(omega / (c kappa rho)) ~ 1e-7
+    T1 = Disp.gas_temperature_amplitude(bg, u)
+    assert abs(u[7] / bg["E0"] - 4 * T1 / bg["T0"]) <= 1e-5 * abs(u[7] / bg["E0"])
+    # B at 45 degrees to k in the x-z plane: no y components
+    assert abs(u[2]) < 1e-10 and abs(u[5]) < 1e-10
+
+
+@pytest.mark.parametrize("ratio", [0.1, 1.0])
+def test_stored_linmode_amplitudes(ratio):
+    # the recipe's stored eigenmode (linmode_eigen.json) is the oracle's, recomputed
+    from oracle import write_linmode_eigen as W
+    from paper_2503_02764_gb300 import inputs as I
+    a = W.amplitudes(ratio)
+    T1, E1 = I.linmode_amplitudes(ratio)
+    assert T1 == pytest.approx(complex(*a["T1"]), rel=1e-12)
+    assert E1 == pytest.approx(complex(*a["E1"]), rel=1e-12)
+
+
+@pytest.mark.parametrize("ratio", [0.1, 1.0])
+def test_hydro_frozen_slow_rate_is_effective_diffusion(ratio):
+    # with the gas held (rho_1 = v_1 = B_1 = 0) and radiation locked to it, energy diffuses
+    # at D k^2 times the radiation's share of the heat capacity,
+    # f = (4 E0/T0) / (p0/((gamma - 1) T0) + 4 E0/T0), up to O(D k^2 / (c kappa rho))
+    bg = Disp.code_units_background(ratio)
+    slow = Disp.hydro_frozen(bg)
+    slow = slow[np.argmax(slow.imag)]
+    D = bg["c"] / (3 * bg["kappa"] * bg["rho0"])
+    f = 4 * bg["E0"] / (bg["p0"] / (bg["gamma"] - 1) + 4 * bg["E0"])
+    assert abs(slow.real) < 1e-6 * abs(slow)
+    assert -slow.imag == pytest.approx(D * bg["k"] ** 2 * f, rel=1e-6)
+
+
+@pytest.mark.parametrize("ratio", [0.1, 1.0])
+def test_substep_decay_tracks_hydro_frozen_rate(ratio):
+    # the split substep's amplification G (dt = 1e-3, 512 cells) on the radiation-locked
+    # direction: the diffusion removes a / (1 + a) of E_1 (a = dt D ktilde^2), the exchange
+    # shares the loss of total energy back so that the radiation keeps its share f of the
+    # heat capacity, so the slow eigenvalue is 1 - f a / (1 + a) (up to O(a / chi),
+    # chi = dt c kappa rho = 1e5). Over N steps it follows the continuum exp(-N dt f D k^2)
+    # of the hydro-frozen rate to the scheme's first-order error N f a^2 (1 - f/2).
+    bg = Disp.code_units_background(ratio)
+    dt, N, n = 1e-3, 100, 512
+    D = bg["c"] / (3 * bg["kappa"] * bg["rho0"])
+    k2 = Disp.discrete_k2(bg["k"], 1.0 / n)
+    G = Disp.substep_amplification(dt, bg["c"], bg["kappa"], bg["rho0"], bg["a_r"], bg["T0"],
+                                   bg["gamma"], bg["R_gas"], D, k2)
+    g = np.linalg.eigvals(G)
+    gs = g[np.argmax(np.abs(g))].real
+    f = 4 * bg["E0"] / (bg["p0"] / (bg["gamma"] - 1) + 4 * bg["E0"])
+    a = dt * D * k2
+    assert gs == pytest.approx(1.0 - f * a / (1.0 + a), rel=1e-6)
+    lam = -np.max(Disp.hydro_frozen(bg).imag)
+    cont = np.exp(-N * dt * lam)
+    err = N * f * a * a * (1 - f / 2) * cont
+    assert 0.8 * err <= gs ** N - cont <= 1.2 * err

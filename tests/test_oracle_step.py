@@ -22,7 +22,7 @@ def test_linear_mode_amplification(ratio):
     # per-step matrix G = (I - dt J)^-1 diag(1, 1/(1 + dt D ktilde^2)) (exchange after
     # diffusion; lambda = 1/3 + O(R^2) for R ~ 1e-10).
     amp = 1e-7
-    P = I.linear_mode_3d(16, ratio=ratio, amp=amp, ny=2, nz=2, steps=6)
+    P = I.linear_mode_3d(16, ratio=ratio, amp=amp, ny=2, nz=2, steps=6, mode="excess")
     n = 16
     x = (np.arange(n) + 0.5) / n
     cosx = np.cos(2 * np.pi * x)
