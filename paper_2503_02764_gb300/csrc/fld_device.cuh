@@ -280,7 +280,8 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
                                              const double* __restrict__ Ebc, const BcOff& bo,
                                              const Opacity& op, double c, int mode, int i, int j,
                                              int k, long long p, double& Dout, double& lmout,
-                                             double* kr_out = nullptr, bool want_lm = true) {
+                                             double* kr_out = nullptr, bool want_lm = true,
+                                             double one = 1.0) {
     const double Ec = E[p], r = rho[p];
     const double t = (op.kind == FLD_OPACITY_CONST) ? 1.0 : T[p];
     const double kap = opacity_eval<kTables>(op, r, t);
@@ -295,7 +296,9 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
             const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
             const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);
             const double ep2 = fetch_E(L, E, Ebc, bo, i, j, k, d, 2);
-            const double g = ((em2 - 8.0 * em1) + 8.0 * ep1 - ep2) * ih[d];
+            // (E_-2 - 8 E_-1) + 8 E_+1 - E_+2 as three FMAs (`one` = 1.0 from the kernel's
+            // arguments: an FP64 add costs the FP64 pipe twice an FMA's time on this GPU)
+            const double g = fma(ep2, -one, fma(8.0, ep1, fma(-8.0, em1, em2))) * ih[d];
             g2 = fma(g, g, g2);
         }
         const double a = kr * Ec;
@@ -338,10 +341,11 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
 // q = alpha T + chi E/(1+chi), and sets E' = (E + chi a_r T'^4)/(1 + chi)
 // = E/(1+chi) + beta T'^4. The caller checks r, t, er and kr.
 __device__ __forceinline__ void exchange_cell_kr(double r, double kr, double& t, double& er,
-                                                 double dtc, double a_r, double cv) {
+                                                 double dtc, double a_r, double cv,
+                                                 double one = 1.0) {
     const double chi = dtc * kr;
     const double alpha = r * cv;
-    const double d1 = 1.0 + chi;
+    const double d1 = fma(chi, one, 1.0);      // 1 + chi as an FMA (see limiter_cell)
     const double inv1 = in_f32_range(d1) ? rcp_nr(d1) : 1.0 / d1;
     const double w = chi * inv1;
     const double beta = w * a_r;

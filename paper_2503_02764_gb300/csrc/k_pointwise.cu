@@ -26,7 +26,7 @@ namespace fld {
 __global__ void k_exchange(long long n, const double* __restrict__ rho, double* __restrict__ T,
                            double* __restrict__ E, const double* __restrict__ kr, Opacity op,
                            double dtc, double a_r, double cv, int use_df, DfConst K,
-                           unsigned* err) {
+                           unsigned* err, double one) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const double r = rho[i];
@@ -48,7 +48,7 @@ __global__ void k_exchange(long long n, const double* __restrict__ rho, double* 
                 atomicOr(err, ERRBIT_DOMAIN);
                 continue;
             }
-            exchange_cell_kr(r, kri, t, er, dtc, a_r, cv);
+            exchange_cell_kr(r, kri, t, er, dtc, a_r, cv, one);
         } else if (!exchange_cell(r, t, er, op, dtc, a_r, cv)) {
             atomicOr(err, ERRBIT_DOMAIN);
             continue;
@@ -76,7 +76,8 @@ void launch_exchange(long long n, const double* rho, double* T, double* E, Opaci
     long long nb = (n + block - 1) / block;
     if (nb > num_sms() * 32) nb = num_sms() * 32;
     const DfConst K = make_dfconst(0.0, op.kappa0, dtc, a_r, cv);
-    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, kr, op, dtc, a_r, cv, use_df, K, err);
+    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, kr, op, dtc, a_r, cv, use_df, K, err,
+                                         1.0);
 }
 
 // ----------------------------------------------------------------- limiter
@@ -97,7 +98,8 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
                           int mode, int use_df, DfConst K, const float* __restrict__ Eh,
                           const float* __restrict__ El, double* __restrict__ D,
-                          double* __restrict__ lam, double* __restrict__ kr, unsigned* err) {
+                          double* __restrict__ lam, double* __restrict__ kr, unsigned* err,
+                          double one) {
     const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
     df ihd[3];
     for (int d = 0; d < 3; ++d) ihd[d] = df_from_double(ih[d]);
@@ -115,7 +117,7 @@ __global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                 continue;
             }
             if (!limiter_cell(L, ih, E, rho, T, Ebc, bo, op, c, mode, i, j, k, p, Dv, lm,
-                              kr ? &kv : nullptr, lam != nullptr)) {
+                              kr ? &kv : nullptr, lam != nullptr, one)) {
                 atomicOr(err, ERRBIT_DOMAIN);
                 continue;
             }
@@ -247,7 +249,7 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
     if (!(use_df && mode != FLD_LIMITER_DIFFUSION)) Eh = El = nullptr;
     k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, Eh, El, D,
-                                   lam, kr, err);
+                                   lam, kr, err, 1.0);
 }
 
 }  // namespace fld

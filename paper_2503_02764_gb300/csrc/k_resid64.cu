@@ -47,6 +47,13 @@ __device__ __forceinline__ double f64_of(float f) {
     return (double)f;
 }
 
+// a + b and a - b as FMAs whose multiplier `one` (1.0) arrives at run time, so the compiler
+// cannot turn them back into adds: the result is the same rounded sum, and on this GPU an
+// FP64 add holds the FP64 pipe about twice as long as an FMA (measured: per-cell FP64 add,
+// multiply and FMA counts against the pipe's busy time in three kernels).
+__device__ __forceinline__ double addf(double a, double b, double one) { return fma(a, one, b); }
+__device__ __forceinline__ double subf(double a, double b, double one) { return fma(b, -one, a); }
+
 // FP32 number nearest to v (ties away from zero) in integer arithmetic where the result is
 // a normal number or zero; the rest through the conversion instruction.
 __device__ __forceinline__ float f32_of(double v) {
@@ -63,7 +70,7 @@ __device__ __forceinline__ float f32_of(double v) {
 __global__ void __launch_bounds__(RZ_NT)
 k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
            double* __restrict__ xo, const double* __restrict__ b, const double* __restrict__ K,
-           float* __restrict__ r32, double* __restrict__ partials, int cz) {
+           float* __restrict__ r32, double* __restrict__ partials, int cz, double one) {
     __shared__ double XS[(RZ_TY + 2) * RZ_PW], KS[(RZ_TY + 2) * RZ_PW];
     __shared__ double FX[RZ_TY * (RZ_TX + 1)], FY[(RZ_TY + 1) * RZ_TX];
     __shared__ double sh[32];
@@ -143,7 +150,7 @@ k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
             }
         }
     };
-    auto xnew = [&](double v, float ev) -> double { return e ? v + f64_of(ev) : v; };
+    auto xnew = [&](double v, float ev) -> double { return e ? addf(v, f64_of(ev), one) : v; };
     // own column's x_new and K at plane m (wrapped), or the wall ghost from Kwall
     auto column = [&](int m, const Raw& R, double Kwall, double& xv, double& kv) {
         if (rz_axis(m, nz, zper) >= 0) {
@@ -182,28 +189,31 @@ k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
         if (k < z1) load_raw(k + 1, nxt);
         __syncthreads();
         // -z face against the plane below (registers); fluxes of the -x, -y faces (shared)
+        // the flux (K_c + K_q)(x_c - x_q) of a face
+        auto flux = [&](double kc, double kq, double xc, double xq) {
+            return addf(kc, kq, one) * subf(xc, xq, one);
+        };
         double gz = 0.0;
-        if (act) gz = (kk + kprev) * (xk - xprev);
+        if (act) gz = flux(kk, kprev, xk, xprev);
         if (inplane && act) {
-            FX[ly * (RZ_TX + 1) + lx] = (KS[so] + KS[so - 1]) * (XS[so] - XS[so - 1]);
+            FX[ly * (RZ_TX + 1) + lx] = flux(KS[so], KS[so - 1], XS[so], XS[so - 1]);
             if (lx == ax - 1)
-                FX[ly * (RZ_TX + 1) + lx + 1] = (KS[so + 1] + KS[so]) * (XS[so + 1] - XS[so]);
-            FY[ly * RZ_TX + lx] = (KS[so] + KS[so - RZ_PW]) * (XS[so] - XS[so - RZ_PW]);
+                FX[ly * (RZ_TX + 1) + lx + 1] = flux(KS[so + 1], KS[so], XS[so + 1], XS[so]);
+            FY[ly * RZ_TX + lx] = flux(KS[so], KS[so - RZ_PW], XS[so], XS[so - RZ_PW]);
             if (ly == ay - 1)
-                FY[(ly + 1) * RZ_TX + lx] =
-                    (KS[so + RZ_PW] + KS[so]) * (XS[so + RZ_PW] - XS[so]);
+                FY[(ly + 1) * RZ_TX + lx] = flux(KS[so + RZ_PW], KS[so], XS[so + RZ_PW], XS[so]);
         }
         // the plane below is complete: its +z face is this plane's -z face
         if (act && k - 1 >= z0) {
-            const double r = fma(-hz, gzprev - gz, part);
+            const double r = fma(-hz, subf(gzprev, gz, one), part);
             if (r32) r32[(long long)(k - 1) * plane + own] = f32_of(r);
             acc2 = fma(r, r, acc2);
         }
         __syncthreads();
         if (inplane && act) {
             const int fx = ly * (RZ_TX + 1) + lx, fy = ly * RZ_TX + lx;
-            const double r = fma(-hx, FX[fx] - FX[fx + 1], cur.b - xk);
-            part = fma(-hy, FY[fy] - FY[fy + RZ_TX], r);
+            const double r = fma(-hx, subf(FX[fx], FX[fx + 1], one), subf(cur.b, xk, one));
+            part = fma(-hy, subf(FY[fy], FY[fy + RZ_TX], one), r);
         }
         xprev = xk;
         kprev = kk;
@@ -253,7 +263,7 @@ int launch_resid64z(const Lvl& L, const double* x, const float* e, double* xo, c
     }
     const int cz = (L.n[2] + best - 1) / best;
     const int nch = (L.n[2] + cz - 1) / cz;
-    k_resid64z<<<tiles * nch, RZ_NT, 0, s>>>(L, x, e, xo, b, K, r32, partials, cz);
+    k_resid64z<<<tiles * nch, RZ_NT, 0, s>>>(L, x, e, xo, b, K, r32, partials, cz, 1.0);
     return tiles * nch;
 }
 
