@@ -20,8 +20,9 @@
  *
  * Around the substep: its explicit coupling terms (fld_coupling), a batched
  * substep over many independent grids in one launch (fld_step_batched), an
- * allocation-free solve (fld_diffuse_static) and a 1D radiation-MHD step that
- * runs the substep inside a hyperbolic update (fld_wave1d_*).
+ * allocation-free solve (fld_diffuse_static), a 1D radiation-MHD step that
+ * runs the substep inside a hyperbolic update (fld_wave1d_*) and the diffusion
+ * solve on a coarse block with a refined box (fld_amr_*).
  *
  * Layout: every field is a contiguous float64 array of n[0]*n[1]*n[2] cells,
  * x fastest: index = (k * n[1] + j) * n[0] + i. Absent axes have n = 1.
@@ -29,8 +30,8 @@
  * Memory: field pointers are DEVICE pointers owned by the caller. The handle
  * owns its workspace (the multigrid level pyramid, scratch and reduction
  * buffers), allocated once in fld_create and freed in fld_destroy; only the
- * create calls (fld_create, fld_batch_create, fld_wave1d_create) allocate device
- * memory.
+ * create calls (fld_create, fld_batch_create, fld_wave1d_create, fld_amr_create)
+ * allocate device memory.
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream). Work is enqueued on it. fld_diffuse and fld_step read the residual
@@ -386,6 +387,52 @@ fld_status fld_wave1d_max_dt(fld_wave1d* w, const double* U, double cfl, double*
    stopped at max_cycles: the step is still completed; FLD_ERR_DOMAIN when a cell left
    the physical domain: U holds the stage where it happened). stats may be NULL. */
 fld_status fld_wave1d_step(fld_wave1d* w, double* U, double t, double dt, fld_stats* stats,
+                           void* stream);
+
+/* ---------------------------------------------------------------- composite grid
+   Backward-Euler diffusion (the solve of fld_diffuse) on a block-structured composite grid:
+   a coarse block (the fld_grid, cells h[d]) with one box of it refined by 2 in every axis
+   (cells h[d]/2), the smallest case of the block-adaptive hierarchy whose implicit div F
+   the paper solves with its octree multigrid library (Sect. 3; AMR by Loehner's criterion).
+   The unknowns are the coarse cells outside the box and every fine cell; for each, of
+   volume V_p,
+     (A x)_p = x_p + (dt/V_p) sum_faces a_f (x_p - x_q) + Dirichlet walls at half a cell,
+     a_f = (D_p + D_q)/2 * area_f / dist_f,
+   dist_f the distance of the two cell centres along the face normal: h between coarse
+   cells, h/2 between fine cells, 3h/4 between a fine cell and the coarse cell across the
+   box's edge (one coarse face meets 2^(ndim-1) fine faces). Each face flux enters both
+   its cells with opposite signs: the step conserves sum V E on periodic and Neumann blocks.
+   Along each axis the box lies at least one coarse cell inside the walls or spans the
+   axis (the axis's walls then bound the fine cells; a fine Dirichlet face takes the value
+   of the coarse face it lies in). Periodic extents of the coarse block must be even.
+   The solve: red-black Gauss-Seidel on the composite grid, and the composite residual
+   restricted to the whole block (a covered coarse cell takes the mean of its fine cells')
+   as the right-hand side of a correction solved by the block's own multigrid (covered
+   cells carrying the mean of their fine cells' D), prolonged piecewise constant; repeated
+   until ||b - A x||_2 <= tol ||b||_2 over the unknowns (o->tol, o->max_cycles; the other
+   options go to the block's solver). FP64 composite arithmetic. */
+typedef struct {
+    int lo[3], hi[3];       /* the refined box in coarse cell indices (hi exclusive);
+                               lo = 0, hi = 1 on absent axes */
+} fld_patch;
+
+typedef struct fld_amr fld_amr;
+
+/* Allocates the composite workspace and a handle for the coarse block. FLD_ERR_ARG for an
+   invalid grid, options or box (a box touching one wall without spanning the axis, odd
+   periodic extents). */
+fld_status fld_amr_create(fld_amr** a, const fld_grid* coarse, const fld_patch* patch,
+                          const fld_opts* o);
+fld_status fld_amr_destroy(fld_amr* a);
+/* One step. In: dt > 0; Dc (device, the coarse block's cells, float64, layout of
+   fld_limiter) and Df (device, the box's fine cells: 2 (hi - lo) per axis, same layout):
+   cell diffusion coefficients (> 0); E_bc: the coarse block's Dirichlet face values as
+   for fld_limiter (may be NULL without Dirichlet sides). In/out: Ec, Ef (device, same
+   layouts): E^n on entry (covered coarse cells ignored), E^{n+1} on return, covered coarse
+   cells set to the mean of their fine cells. stats may be NULL (cycles = two-level
+   iterations). Returns after the solve has finished on `stream`. */
+fld_status fld_amr_diffuse(fld_amr* a, double dt, const double* Dc, const double* Df,
+                           const double* E_bc, double* Ec, double* Ef, fld_stats* stats,
                            void* stream);
 
 /* Static string for a status code. */

@@ -70,6 +70,10 @@ class fld_wave1d_params(C.Structure):
                 ("opts", fld_opts)]
 
 
+class fld_patch(C.Structure):
+    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3)]
+
+
 _lib = None
 P = C.c_void_p
 H = C.c_void_p
@@ -117,6 +121,10 @@ def lib():
         "fld_wave1d_destroy": (C.c_int, [H]),
         "fld_wave1d_max_dt": (C.c_int, [H, P, C.c_double, C.POINTER(C.c_double), P]),
         "fld_wave1d_step": (C.c_int, [H, P, C.c_double, C.c_double, C.POINTER(fld_stats), P]),
+        "fld_amr_create": (C.c_int, [C.POINTER(H), C.POINTER(fld_grid), C.POINTER(fld_patch),
+                                     C.POINTER(fld_opts)]),
+        "fld_amr_destroy": (C.c_int, [H]),
+        "fld_amr_diffuse": (C.c_int, [H, C.c_double, P, P, P, P, P, C.POINTER(fld_stats), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -482,6 +490,61 @@ class Wave1D:
         if self.w:
             fld_wave1d_destroy(self.w)
             self.w = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------ composite grid (coarse block + refined box)
+def make_patch(lo, hi):
+    """fld_patch from (x, y, z)-ordered coarse-index bounds (absent axes: 0, 1)."""
+    p = fld_patch()
+    for d in range(3):
+        p.lo[d] = int(lo[d]) if d < len(lo) else 0
+        p.hi[d] = int(hi[d]) if d < len(hi) else 1
+    return p
+
+
+def fld_amr_create(grid, patch, opts):
+    a = H()
+    _check(lib().fld_amr_create(C.byref(a), C.byref(grid), C.byref(patch), C.byref(opts)),
+           "fld_amr_create")
+    return a
+
+
+def fld_amr_destroy(a):
+    _check(lib().fld_amr_destroy(a), "fld_amr_destroy")
+
+
+def fld_amr_diffuse(a, dt, Dc, Df, E_bc, Ec, Ef, stream=None, raise_on_error=True):
+    st = fld_stats()
+    rc = lib().fld_amr_diffuse(a, float(dt), _ptr(Dc), _ptr(Df), _ptr(E_bc), _ptr(Ec), _ptr(Ef),
+                               C.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(rc, "fld_amr_diffuse")
+    return stats_dict(st) | {"status": rc}
+
+
+class Amr:
+    """Owns an fld_amr: the diffusion solve on a coarse block (numpy shape `shape`, cell
+    sizes h and boundary kinds bc in (x, y, z) order) with the box [lo, hi) refined by 2."""
+
+    def __init__(self, shape, h, bc, lo, hi, **opts):
+        self.grid = make_grid(shape, h, bc)
+        self.patch = make_patch(lo, hi)
+        self.opts = make_opts(**opts)
+        self.a = fld_amr_create(self.grid, self.patch, self.opts)
+
+    def diffuse(self, dt, Dc, Df, E_bc, Ec, Ef, stream=None, raise_on_error=True):
+        return fld_amr_diffuse(self.a, dt, Dc, Df, E_bc, Ec, Ef, stream, raise_on_error)
+
+    def close(self):
+        if self.a:
+            fld_amr_destroy(self.a)
+            self.a = None
 
     def __del__(self):
         try:

@@ -55,7 +55,8 @@ def test_binding_structs_match_header_layout():
     if cc is None:
         pytest.skip("no host C compiler")
     structs = [fld.fld_consts, fld.fld_grid, fld.fld_opacity, fld.fld_opts, fld.fld_stats,
-               fld.fld_prof_entry, fld.fld_batch_stat, fld.fld_wave1d_params]
+               fld.fld_prof_entry, fld.fld_batch_stat, fld.fld_wave1d_params,
+               fld.fld_patch]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fld.h"', "int main(void) {"]
     for s in structs:
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s.__name__, s.__name__))
@@ -101,3 +102,20 @@ def test_wave1d_parameter_checks_without_gpu():
     p.hat[0] = 2.0 * p.W0[0]                               # the drive would make rho < 0
     assert L.fld_wave1d_create(ctypes.byref(w), ctypes.byref(p)) == fld.FLD_ERR_ARG
     assert L.fld_wave1d_create(None, ctypes.byref(p)) == fld.FLD_ERR_ARG
+
+
+def test_amr_box_checks_without_gpu():
+    # fld_amr_create rejects boxes touching one wall without spanning the axis, empty or
+    # out-of-range boxes and odd periodic extents on the host, before any device work
+    from paper_2503_02764_gb300 import fld
+    L = fld.lib()
+    g = fld.make_grid((16, 16), (1.0, 1.0), ((1, 1), (1, 1)))
+    for lo, hi in (((0, 4), (8, 10)), ((4, 4), (16, 10)), ((4, 4), (4, 10)), ((3, 2), (9, 17))):
+        a = fld.H()
+        rc = L.fld_amr_create(ctypes.byref(a), ctypes.byref(g),
+                              ctypes.byref(fld.make_patch(lo, hi)), None)
+        assert rc == fld.FLD_ERR_ARG, (lo, hi)
+    g = fld.make_grid((16, 15), (1.0, 1.0), ((0, 0), (1, 1)))      # odd periodic extent
+    a = fld.H()
+    assert L.fld_amr_create(ctypes.byref(a), ctypes.byref(g),
+                            ctypes.byref(fld.make_patch((3, 3), (9, 9))), None) == fld.FLD_ERR_ARG
