@@ -46,6 +46,7 @@ BYTES_PER_CELL = {
     "sumsq": 8.0,             # b read
     "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
     "resid64x": 40.0,         # x, e32, b, K read; x + e, r32 written
+    "resid32": 24.0,          # x, b (FP64), K32 read; r32 written (FP32 arithmetic)
     "resid_df": 40.0,         # x (hi, lo), e32, b (hi, lo), K (hi, lo) read; x (hi, lo), r32 written
     "rbhalf32": 10.0,         # one colour: the other colour's x and every K read (faces),
     "rbhalf64": 20.0,         #   this colour's b read and x written
@@ -351,8 +352,9 @@ def run_reference(args):
 
 DTYPE = {
     "mixed": "f32 V-cycles (smoothing, restriction, prolongation) inside f64 iterative "
-             "refinement (f64 residual and correction); f64 coarsest solve; f64 limiter; "
-             "f64 exchange (f32 Newton seed, f64 Newton polish)",
+             "refinement (f64 residuals and corrections; the first correction from the f32 "
+             "residual of E^n, an f32 initial solve); f64 coarsest solve; f64 limiter; f64 "
+             "exchange (f32 Newton seed, f64 Newton polish)",
     "mixed_df": "f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
                 "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
                 "exponent window)",

@@ -389,6 +389,32 @@ fld_status fld_wave1d_max_dt(fld_wave1d* w, const double* U, double cfl, double*
 fld_status fld_wave1d_step(fld_wave1d* w, double* U, double t, double dt, fld_stats* stats,
                            void* stream);
 
+/* ---------------------------------------------------------------- IMEX stages
+   The paper advances the explicit terms (hyperbolic fluxes, the coupling terms of
+   fld_coupling) and the implicit ones (this substep) together with the ARS3 IMEX Runge-
+   Kutta scheme (Sect. 3): ARS(2,3,3) of Ascher, Ruuth and Spiteri (1997), with
+   gamma = (3 + sqrt 3)/6,
+     explicit  A_ex = [[0, 0, 0], [gamma, 0, 0], [gamma - 1, 2 (1 - gamma), 0]],
+     implicit  A_im = [[0, 0, 0], [0, gamma, 0], [0, 1 - 2 gamma, gamma]],
+     b = [0, 1/2, 1/2] (both), c = [0, gamma, 1 - gamma]  (row-major 3 x 3 arrays).
+   For dU/dt = F_ex(U) + F_im(U) the stages are U_1 = U^n and, for s = 1, 2,
+     U_{s+1} = P_s + gamma dt F_im(U_{s+1}),
+     P_s = U^n + dt sum_{j<=s} A_ex[s][j] F_ex(U_j) + dt sum_{1<=j<=s} A_im[s][j] F_im(U_j),
+   then U^{n+1} = U^n + dt sum_j b[j] (F_ex(U_j) + F_im(U_j)). A host code forms F_ex and the
+   predictors P_s; fld_ars3_stage makes the implicit solve of stage s: the substep
+   (fld_step) over gamma dt from the predictor, F_im being the substep's diffusion and
+   exchange. */
+void fld_ars3_tableau(double a_ex[9], double a_im[9], double b[3], double c[3]);
+/* Stage s (1 or 2) of ARS3 on the handle's grid. In: rho; T, E hold the predictor P_s (gas
+   temperature and radiation energy density; device float64). Out: T, E the stage value
+   U_{s+1}; F_E, F_e (device float64, ncell, each may be NULL) the implicit increments
+   F_im(U_{s+1}) of E and of the gas energy rho c_v T, (U_{s+1} - P_s)/(gamma dt). dt is
+   the full step (the substep runs over gamma dt). Returns fld_step's status. */
+fld_status fld_ars3_stage(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
+                          int stage, const double* rho, double* T, double* E,
+                          const double* E_bc, double* F_E, double* F_e, fld_stats* stats,
+                          void* stream);
+
 /* ---------------------------------------------------------------- composite grid
    Backward-Euler diffusion (the solve of fld_diffuse) on a block-structured composite grid:
    a coarse block (the fld_grid, cells h[d]) with one box of it refined by 2 in every axis

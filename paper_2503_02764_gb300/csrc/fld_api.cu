@@ -589,7 +589,25 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     if (dfmode) return diffuse_df(h, E, bsum, st, s);
     h->d64[0].x = E;
     double r2;
-    rc = residual(h, E, nullptr, nullptr, mixed ? h->d32[0].b : nullptr, s, &r2, &err);
+    if (mixed) {
+        // the first correction's right-hand side: the FP32 residual of E^n (the refinement
+        // starts from an FP32 solve); every later residual, which decides convergence, is
+        // FP64
+        const int nparts = (int)std::min<long long>((long long)L0.n[1] * L0.n[2], h->norm_blocks);
+        run(h, "resid32", 0, L0.ncell, s, [&] {
+            launch_resid32_init(L0, E, h->d64[0].b, h->d32[0].K, h->d32[0].b, h->partials,
+                                h->norm_blocks, s);
+        });
+        run(h, "finish_sum", 0, nparts, s,
+            [&] { launch_finish_sum(h->partials, nparts, &h->scal->sum, s); });
+        FLD_CK(cudaGetLastError());
+        rc = read_scalars(h, s, &r2, &err);
+        // an FP32 residual at the tolerance is confirmed in FP64 before the solve stops
+        if (rc == FLD_OK && !(bnorm > 0 && std::sqrt(r2) / bnorm > h->o.tol))
+            rc = residual(h, E, nullptr, nullptr, h->d32[0].b, s, &r2, &err);
+    } else {
+        rc = residual(h, E, nullptr, nullptr, nullptr, s, &r2, &err);
+    }
     if (rc != FLD_OK) return rc;
     double rel = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
     if (st) {
@@ -848,6 +866,12 @@ fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, d
     rc = fld_get_status(h, stream);
     return rc ? rc : rs;
 }
+
+}  // extern "C"
+
+long long fld::fld_handle_cells(const fld_handle* h) { return h ? h->ncell : 0; }
+
+extern "C" {
 
 fld_status fld_get_status(fld_handle* h, void* stream) {
     if (!h) return FLD_ERR_ARG;

@@ -172,6 +172,7 @@ int make_levels(const fld_grid& g, Lvl* lv, double* kdown, int maxl);
 bool grid_valid(const fld_grid* g);
 void note_launches(long long n);   // adds to fld_launch_count
 bool opts_valid(const fld_opts* o);
+long long fld_handle_cells(const fld_handle* h);   // cells of the handle's grid
 
 // ----------------------------------------------------------------- launchers
 // pointwise / limiter (k_pointwise.cu)
@@ -260,6 +261,11 @@ void launch_add_correction(long long n, double* x, const float* e, cudaStream_t 
 // of r^2; returns the partials written (<= nblocks). resid64z_ok: the level is 3D and its
 // tiles fit the partial-sum slots.
 bool resid64z_ok(const Lvl& L, int nblocks);
+// FP32 residual of the FP64 iterate (the mixed refinement's first correction): r32 and
+// partial sums of r^2; one block per row, at most nblocks (returns nothing: nblocks or the
+// row count partials are written, the smaller)
+void launch_resid32_init(const Lvl& L, const double* x, const double* b, const float* K,
+                         float* r32, double* partials, int nblocks, cudaStream_t s);
 int launch_resid64z(const Lvl& L, const double* x, const float* e, double* xo, const double* b,
                     const double* K, float* r32, double* partials, int nblocks, cudaStream_t s);
 

@@ -267,4 +267,78 @@ int launch_resid64z(const Lvl& L, const double* x, const float* e, double* xo, c
     return tiles * nch;
 }
 
+
+// ----------------------------------------------------------------- FP32 initial residual
+// The right-hand side of the mixed refinement's first correction: r = b - A x in FP32
+// arithmetic from the FP64 iterate x and right-hand side b (their FP32 images, formed in
+// integer arithmetic) and the FP32 coefficients K, with per-block partial sums of r^2 (the
+// first entry of the residual history). The first FP32 V-cycles then start the iterate from
+// an FP32 solve, as mixed-precision iterative refinement does; every later residual, which
+// decides convergence, is the FP64 one above.
+namespace {
+
+__global__ void k_resid32_init(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
+                               const float* __restrict__ K, float* __restrict__ r32,
+                               double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double acc2 = 0.0;
+    const int nx = L.n[0], ny = L.n[1];
+    const int nrows = ny * L.n[2];
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int j = r % ny, k = r / ny;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const long long p = (long long)r * nx + i;
+            float sw, acc;
+            // the level operator's stencil on the FP32 images of x
+            const float Kc = K[p];
+            const int c[3] = {i, j, k};
+            long long stride = 1;
+            sw = 0.f;
+            acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < L.ndim) {
+                    const int n = L.n[d];
+                    const float wd = L.wf[d];
+                    long long q = -1;
+                    if (c[d] > 0) q = p - stride;
+                    else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
+                    if (q >= 0) {
+                        const float w = 0.5f * (Kc + K[q]) * wd;
+                        sw += w;
+                        acc = fmaf(w, f32_of(x[q]), acc);
+                    } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
+                        sw += 2.f * Kc * wd;
+                    }
+                    q = -1;
+                    if (c[d] < n - 1) q = p + stride;
+                    else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
+                    if (q >= 0) {
+                        const float w = 0.5f * (Kc + K[q]) * wd;
+                        sw += w;
+                        acc = fmaf(w, f32_of(x[q]), acc);
+                    } else if (L.bchi[d] == FLD_BC_DIRICHLET) {
+                        sw += 2.f * Kc * wd;
+                    }
+                    stride *= n;
+                }
+            }
+            const float rv = f32_of(b[p]) - fmaf(1.f + sw, f32_of(x[p]), -acc);
+            r32[p] = rv;
+            acc2 = fma((double)rv, (double)rv, acc2);
+        }
+    }
+    acc2 = block_sum(acc2, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc2;
+}
+
+}  // namespace
+
+void launch_resid32_init(const Lvl& L, const double* x, const double* b, const float* K,
+                         float* r32, double* partials, int nblocks, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>((long long)L.n[1] * L.n[2],
+                                                                      nblocks));
+    k_resid32_init<<<nb, 256, 0, s>>>(L, x, b, K, r32, partials);
+}
+
 }  // namespace fld
