@@ -294,25 +294,32 @@ def next_rows(hd, P, prec, gkw, consts, op, rho, T, E, ebc, peak_hbm):
         }
         del Tc, Ec
     out["tabulated_opacity"] = tab
-    wp = I.wave1d(I.WAVE_BACKGROUNDS["strong"], 280, 7, "fast")
-    wv = fld.Wave1D(wp, precision=fld.PREC_FP64, tol=1e-13, max_cycles=200)
-    W = np.repeat(np.asarray(wp.W0, dtype=float)[:, None], wp.n, axis=1)
-    U = np.stack([W[0], W[0] * W[1], W[0] * W[2], W[0] * W[3], W[4], W[5],
-                  W[6] / (wp.gamma - 1.0) + 0.5 * (wp.Bx ** 2 + W[4] ** 2 + W[5] ** 2), W[7]])
-    Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
-    state = {"t": 0.0}
+    waves = {}
+    for n_cells, nw in ((280, 7), (3200, 40)):
+        wp = I.wave1d(I.WAVE_BACKGROUNDS["strong"], n_cells, nw, "fast")
+        W = np.repeat(np.asarray(wp.W0, dtype=float)[:, None], wp.n, axis=1)
+        U = np.stack([W[0], W[0] * W[1], W[0] * W[2], W[0] * W[3], W[4], W[5],
+                      W[6] / (wp.gamma - 1.0) + 0.5 * (wp.Bx ** 2 + W[4] ** 2 + W[5] ** 2),
+                      W[7]])
+        for scheme, sname in ((1, "ars3"), (0, "split")):
+            wv = fld.Wave1D(wp, scheme=scheme, precision=fld.PREC_FP64, tol=1e-13,
+                            max_cycles=200)
+            Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+            state = {"t": 0.0}
 
-    def wave_step():
-        dt = wv.max_dt(Ud, 0.8)
-        wv.step(Ud, state["t"], dt)
-        state["t"] += dt
+            def wave_step():
+                dt = wv.max_dt(Ud, 0.8)
+                wv.step(Ud, state["t"], dt)
+                state["t"] += dt
 
-    ms = timed(wave_step, reps=50, warm=5)
-    out["wave1d"] = {"cells": wp.n, "ms_per_step": ms, "cell_updates_per_s": wp.n / (ms * 1e-3),
-                     "note": "launch- and synchronisation-bound on 280 cells: three Runge-Kutta "
-                             "stages of four launches, the substep's FP64 multigrid cycles and "
-                             "several host synchronisations per step"}
-    wv.close()
+            ms = timed(wave_step, reps=50, warm=5)
+            waves["%s_%d" % (sname, n_cells)] = {"cells": wp.n, "ms_per_step": ms,
+                                                 "cell_updates_per_s": wp.n / (ms * 1e-3)}
+            wv.close()
+    waves["note"] = ("launch- and synchronisation-bound: per step three explicit evaluations "
+                     "of a few launches each and one (split) or two (ARS3) substeps with the "
+                     "direct 1D solve and their read-backs")
+    out["wave1d"] = waves
     return out
 
 
@@ -577,20 +584,24 @@ def config_workloads(fld, I, torch, peak_hbm, nprob=512, big=512):
     out = {}
     consts_of = lambda P: fld.make_consts(P.c, P.a_r, P.gamma, P.R_gas)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    # 1: pulse1d, FP64 plain method, one step + exchange, tol 1e-12
+    # 1: pulse1d, FP64 plain method, one step + exchange, tol 1e-12: the direct 1D solve
+    # (parallel cyclic reduction) and FP64 V-cycles
     P = I.gaussian_pulse_1d(256)
-    hd = fld.Handle(P.shape, P.h, P.bc, precision=fld.PREC_FP64, tol=1e-12, max_cycles=50)
-    first = hd.step(consts_of(P), fld.make_opacity(P.opacity), P.dt, dev(P.rho), dev(P.T),
-                    dev(P.E), None, raise_on_error=False)
-    rho, T, E = dev(P.rho), dev(P.T), dev(P.E)
-    ms, cyc, st = step_series(hd, consts_of(P), fld.make_opacity(P.opacity), P, rho, T, E, None,
-                              20, 3, torch)
-    out["pulse1d_256"] = {"cells": P.ncells, "precision": "fp64", "tol": 1e-12,
-                          "first_step_cycles": first["cycles"], "ms_per_step": ms,
-                          "cycles_per_step": cyc[-1], "cell_updates_per_s": P.ncells / (ms * 1e-3),
-                          "note": "256 cells: latency-bound (launches and the per-cycle "
-                                  "residual read-back), no HBM roofline"}
-    hd.close()
+    res = {"cells": P.ncells, "precision": "fp64", "tol": 1e-12,
+           "note": "256 cells: latency-bound (launches and read-backs), no HBM roofline"}
+    for name, direct in (("direct", 1), ("vcycles", 0)):
+        hd = fld.Handle(P.shape, P.h, P.bc, precision=fld.PREC_FP64, tol=1e-12, max_cycles=50,
+                        direct1d=direct)
+        first = hd.step(consts_of(P), fld.make_opacity(P.opacity), P.dt, dev(P.rho), dev(P.T),
+                        dev(P.E), None, raise_on_error=False)
+        rho, T, E = dev(P.rho), dev(P.T), dev(P.E)
+        ms, cyc, st = step_series(hd, consts_of(P), fld.make_opacity(P.opacity), P, rho, T, E,
+                                  None, 20, 3, torch)
+        res[name] = {"first_step_cycles": first["cycles"], "ms_per_step": ms,
+                     "cycles_per_step": cyc[-1], "rel_resid_last": st["rel_resid"],
+                     "cell_updates_per_s": P.ncells / (ms * 1e-3)}
+        hd.close()
+    out["pulse1d_256"] = res
     # 2: lognormal2d 1024^2, FP64 plain GMG, 10 implicit steps, tol 1e-10
     P = I.lognormal_2d(1024)
     for name, prec in (("fp64", fld.PREC_FP64), ("mixed", fld.PREC_MIXED)):

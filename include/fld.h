@@ -150,6 +150,9 @@ typedef struct {
                            cluster when > 1); 0 = chosen from the largest problem      */
     int inner;          /* MIXED/MIXED_DF: FP32 V-cycles per refinement step (the later
                            ones continue from the previous correction); 0 means 1      */
+    int direct1d;       /* 1D grids: 1 solves the tridiagonal system directly (parallel
+                           cyclic reduction in FP64, a dozen launches; stats report one
+                           cycle), 0 runs V-cycles as in 2D and 3D                      */
 } fld_opts;
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative
@@ -164,7 +167,7 @@ typedef struct {
 typedef struct fld_handle fld_handle;
 
 /* Fill *o with defaults: FP64, tol 1e-10, 50 cycles, V(2,2), 32 coarse sweeps,
-   Levermore-Pomraning limiter. */
+   Levermore-Pomraning limiter, direct 1D solves. */
 void fld_default_opts(fld_opts* o);
 
 /* Create a handle bound to grid *g with options *o; allocates the workspace on
@@ -341,6 +344,7 @@ fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, double dt, c
 /* ---------------------------------------------------------------- 1D RMHD wave step
    One step of the one-dimensional radiation-MHD problem of the paper's linear-wave tests
    (Sect. 4.3) with the scheme of Sect. 3, for the travelling radiation-damped waves:
+   With scheme 0 (first-order split):
    1. the hyperbolic terms (left-hand sides of Eqs. mhd_mass, mhd_mom, mhd_energy,
       mhd_mag and the advection term of Eq. mhd_r_e) plus the explicit coupling terms
       (radiation force f_r = -lambda grad E, its work v . f_r, photon tiring P : grad v,
@@ -352,6 +356,10 @@ fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, double dt, c
    2. the FLD substep (as fld_step: limiter, backward-Euler diffusion, implicit exchange)
       on (rho, T_g = p / (rho R_gas), E); the exchange's change of T_g is added to the
       total gas energy.
+   With scheme 1 the same explicit right-hand side (hyperbolic terms and coupling terms)
+   and the same substep (as the implicit operator) are combined by the ARS3 IMEX scheme,
+   the paper's (Sect. 3): three explicit evaluations and two substeps over gamma dt per
+   step (the stage equations are those of fld_ars3_tableau).
    Units are the caller's; the magnetic field is in Heaviside-Lorentz form (magnetic
    pressure B^2/2) with B_x constant.
    State U: caller-owned device float64 array [8][n] (variable-major): rho, rho v_x,
@@ -372,6 +380,12 @@ typedef struct {
     double W0[8], hat[8];       /* driving wave, primitive variables                    */
     double k, omega;
     fld_opts opts;              /* options of the FLD substep (limiter, precision, tol)  */
+    int scheme;                 /* 0: SSP-RK3 then the FLD substep over dt (first-order
+                                   split); 1: the ARS3 IMEX scheme (fld_ars3_tableau): the
+                                   hyperbolic and coupling terms explicit, the substep as
+                                   its two implicit stages over gamma dt                 */
+    int radiation;              /* 1: as above; 0: ideal MHD (no coupling terms, no
+                                   substep: the scheme's own damping, for reference)       */
 } fld_wave1d_params;
 
 typedef struct fld_wave1d fld_wave1d;

@@ -149,8 +149,9 @@ class Wave:
     problem's W0 + hat sin(k x - omega t) at every stage. With ``problem.radiation``
     False the coupling terms and the FLD substep are off (ideal MHD)."""
 
-    def __init__(self, problem, cfl=0.8, mode=0):
+    def __init__(self, problem, cfl=0.8, mode=0, scheme="split"):
         P = problem
+        self.scheme = scheme
         self.P = P
         self.gamma = P.gamma
         self.R_gas = P.R_gas
@@ -204,7 +205,51 @@ class Wave:
             dU[ER] -= cp["ptire"]
         return dU
 
+    def implicit(self, P, tau, t):
+        """The FLD substep over tau on the state P (the stage solve of the IMEX scheme):
+        limiter, backward-Euler diffusion, exchange; the exchange's change of T_g goes to
+        the gas energy. Returns the new state, its driven cells at time t."""
+        W = primitive(P, self.Bx, self.gamma)
+        T = self.T_gas(W)
+        D, _, _ = F.limiter(W[ER], W[RHO], T, (self.dx,), self.bcE, self.E_bc, self.c,
+                            self.op, self.mode)
+        E1 = diffuse_1d(W[ER], D, self.dx, self.bcE, self.E_bc, tau)
+        T2, E2 = F.exchange(W[RHO], T, E1, tau, self.c, self.a_r, self.gamma, self.R_gas,
+                            self.op)
+        U = P.copy()
+        U[PG] += W[RHO] * self.R_gas * (T2 - T) / (self.gamma - 1.0)
+        U[ER] = E2
+        self.drive(U, t)
+        return U
+
+    def step_ars3(self, U, t, dt):
+        """One step of the ARS(2,3,3) IMEX scheme (Ascher, Ruuth and Spiteri 1997), the
+        ARS3 of Sect. 3: explicit hyperbolic and coupling terms L, implicit FLD substep.
+        gamma = (3 + sqrt 3)/6; stage predictors
+          P1 = U + dt gamma L(U),
+          P2 = U + dt ((gamma - 1) L(U) + 2 (1 - gamma) L(U2)) + dt (1 - 2 gamma) G2,
+        stage values U_{s+1} = the substep over gamma dt from P_s, G = (U_{s+1} - P_s)/(gamma
+        dt) its implicit increment, and U^{n+1} = U + dt/2 (L(U2) + L(U3)) + dt/2 (G2 + G3).
+        Each predictor and stage value takes the driving wave at its stage time."""
+        g = (3.0 + np.sqrt(3.0)) / 6.0
+        L1 = self.rhs(U, t)
+        P1 = U + dt * g * L1
+        self.drive(P1, t + g * dt)
+        U2 = self.implicit(P1, g * dt, t + g * dt)
+        G2 = (U2 - P1) / (g * dt)
+        L2 = self.rhs(U2, t + g * dt)
+        P2 = U + dt * ((g - 1.0) * L1 + 2.0 * (1.0 - g) * L2) + dt * (1.0 - 2.0 * g) * G2
+        self.drive(P2, t + (1.0 - g) * dt)
+        U3 = self.implicit(P2, g * dt, t + (1.0 - g) * dt)
+        G3 = (U3 - P2) / (g * dt)
+        L3 = self.rhs(U3, t + (1.0 - g) * dt)
+        Un = U + 0.5 * dt * (L2 + L3) + 0.5 * dt * (G2 + G3)
+        self.drive(Un, t + dt)
+        return Un
+
     def step(self, U, t, dt):
+        if self.scheme == "ars3" and self.radiation:
+            return self.step_ars3(U, t, dt)
         U1 = U + dt * self.rhs(U, t)
         self.drive(U1, t + dt)
         U2 = 0.75 * U + 0.25 * (U1 + dt * self.rhs(U1, t + dt))

@@ -128,6 +128,7 @@ struct fld_handle {
     float* dfK[2] = {nullptr, nullptr};                            // coefficient K (hi, lo)
     double* Dscratch = nullptr;
     double* krscratch = nullptr;     // kappa rho of the substep (limiter -> exchange)
+    double* triw = nullptr;          // 1D grids: the direct solve's workspace (10 n + 1)
     double* partials = nullptr;
     int norm_blocks = 0;              // blocks (and partial sums) of the norm kernels
     DevScalars* scal = nullptr;       // device
@@ -198,7 +199,7 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->smoother >= 0 && o->smoother <= 2) &&
            (o->cluster == 0 || o->cluster == 1 || o->cluster == 2 || o->cluster == 4 ||
             o->cluster == 8) &&
-           (o->inner >= 0 && o->inner <= 8);
+           (o->inner >= 0 && o->inner <= 8) && (o->direct1d == 0 || o->direct1d == 1);
 }
 
 namespace {
@@ -570,8 +571,12 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         launch_prep_level0(L0, kscale, D, E, E_bc, h->bc_off, h->d64[0].K,
                            mixed ? h->d32[0].K : nullptr, h->d64[0].b, &h->scal->err, s);
     });
-    if (mixed) restrict_pyramid<float>(h, h->d32, s);
-    else restrict_pyramid<double>(h, h->d64, s);
+    // 1D grids with direct1d: the tridiagonal system solved directly (no pyramid needed)
+    const bool direct = h->g.ndim == 1 && h->o.direct1d && h->triw;
+    if (!direct) {
+        if (mixed) restrict_pyramid<float>(h, h->d32, s);
+        else restrict_pyramid<double>(h, h->d64, s);
+    }
     run(h, "sumsq", 0, L0.ncell, s,
         [&] { launch_sumsq(L0.ncell, h->d64[0].b, h->partials, h->norm_blocks, s); });
     run(h, "finish_sum", 0, h->norm_blocks, s,
@@ -586,6 +591,26 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         return FLD_ERR_DOMAIN;
     }
     const double bnorm = std::sqrt(bsum);
+    if (direct) {
+        int nl = 0;
+        run(h, "tridiag", 0, L0.ncell, s,
+            [&] { nl = launch_tridiag_solve(L0, h->d64[0].K, h->d64[0].b, E, h->triw, s); });
+        g_launches.fetch_add(nl - 1, std::memory_order_relaxed);
+        double r2;
+        rc = residual(h, E, nullptr, nullptr, nullptr, s, &r2, &err);
+        if (rc != FLD_OK) return rc;
+        const double rel = bnorm > 0 ? std::sqrt(r2) / bnorm : 0.0;
+        if (st) {
+            memset(st, 0, sizeof(*st));
+            st->resid_hist[0] = rel;
+            st->resid_hist[1] = rel;
+            st->cycles = 1;
+            st->rel_resid = rel;
+            st->levels = 1;
+        }
+        if (!std::isfinite(rel)) return FLD_ERR_DOMAIN;
+        return rel <= h->o.tol ? FLD_OK : FLD_ERR_NOT_CONVERGED;
+    }
     if (dfmode) return diffuse_df(h, E, bsum, st, s);
     h->d64[0].x = E;
     double r2;
@@ -677,6 +702,7 @@ void fld_default_opts(fld_opts* o) {
     o->graph = 1;
     o->cluster = 0;
     o->inner = 1;
+    o->direct1d = 1;
 }
 
 fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
@@ -732,6 +758,7 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
     }
     rc = rc ? rc : dalloc(h, &h->Dscratch, n0);
     rc = rc ? rc : dalloc(h, &h->krscratch, n0);
+    if (g->ndim == 1) rc = rc ? rc : dalloc(h, &h->triw, 10 * n0 + 1);
     h->norm_blocks = NORM_BLOCKS_PER_SM * num_sms();
     rc = rc ? rc : dalloc(h, &h->partials, h->norm_blocks);
     rc = rc ? rc : dalloc(h, &h->scal, 1);
@@ -994,6 +1021,7 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
     h.g = *g;
     h.o = *o;
     h.o.graph = 0;        // graph capture and instantiation allocate: launch directly
+    h.o.direct1d = 0;     // V-cycles in every dimension (the workspace holds no direct solver)
     prepare_rb_sweep();   // kernel attributes only (no device memory)
     prepare_vcycle_tail();
     build_levels(&h);

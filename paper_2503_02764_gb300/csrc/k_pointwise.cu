@@ -93,7 +93,7 @@ __global__ void k_split_df(long long n, const double* __restrict__ v, float* __r
 }
 
 // kr (nullable): receives kappa rho of every cell, for the exchange of the same substep.
-__global__ void k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
+__global__ void __launch_bounds__(256, 5) k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           const double* __restrict__ rho, const double* __restrict__ T,
                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
                           int mode, int use_df, DfConst K, const float* __restrict__ Eh,

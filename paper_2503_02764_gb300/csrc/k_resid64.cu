@@ -67,7 +67,7 @@ __device__ __forceinline__ float f32_of(double v) {
     return (float)v;
 }
 
-__global__ void __launch_bounds__(RZ_NT)
+__global__ void __launch_bounds__(RZ_NT, 5)
 k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
            double* __restrict__ xo, const double* __restrict__ b, const double* __restrict__ K,
            float* __restrict__ r32, double* __restrict__ partials, int cz, double one) {

@@ -175,6 +175,67 @@ __global__ void k_w1_stage(Wave1dDev P, const double* U0, const double* __restri
     }
 }
 
+// L(Uin) = -dF/dx + (0, f_r, 0, 0, 0, 0, v.f_r, -P:grad v), every cell (the driven ones are
+// reset by whatever combines it)
+__global__ void k_w1_rhs(Wave1dDev P, const double* __restrict__ Fi, const double* __restrict__ fr,
+                         const double* __restrict__ vfr, const double* __restrict__ pt,
+                         double* __restrict__ Lout) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long n = P.n, m = P.n + 1;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        double dU = -(Fi[v * m + i + 1] - Fi[v * m + i]) / P.dx;
+        if (v == 1) dU += fr[i];
+        if (v == 6) dU += vfr[i];
+        if (v == 7) dU -= pt[i];
+        Lout[v * n + i] = dU;
+    }
+}
+
+// Uout = U0 + dt (c1 L1 + c2 L2 + c3 L3) + dt (d2 G2 + d3 G3), the G's ([2][n]: gas energy,
+// E) entering variables 6 and 7; null operands have zero weight. Driven cells take the
+// driving wave at t_stage. Uout may alias U0.
+__global__ void k_w1_comb(Wave1dDev P, const double* U0, const double* __restrict__ L1,
+                          const double* __restrict__ L2, const double* __restrict__ L3,
+                          double c1, double c2, double c3, const double* __restrict__ G2,
+                          const double* __restrict__ G3, double d2, double d3, double dt,
+                          double* Uout, double t_stage) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long n = P.n;
+    if (i < P.nd) {
+        double W[8], u[8];
+        drive_prim(P, (i + 0.5) * P.dx, t_stage, W);
+        to_cons(W, P.Bx, P.gamma, u);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) Uout[v * n + i] = u[v];
+        return;
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        double inc = 0.0;
+        if (L1) inc += c1 * L1[v * n + i];
+        if (L2) inc += c2 * L2[v * n + i];
+        if (L3) inc += c3 * L3[v * n + i];
+        if (v >= 6) {
+            if (G2) inc += d2 * G2[(v - 6) * n + i];
+            if (G3) inc += d3 * G3[(v - 6) * n + i];
+        }
+        Uout[v * n + i] = U0[v * n + i] + dt * inc;
+    }
+}
+
+// the implicit increment of a stage: G = (Uafter - Ubefore) / tau for variables 6, 7
+__global__ void k_w1_incr(Wave1dDev P, const double* __restrict__ Ua,
+                          const double* __restrict__ Ub, double inv_tau, double* __restrict__ G) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const long long n = P.n;
+    G[i] = (Ua[6 * n + i] - Ub[6 * n + i]) * inv_tau;
+    G[n + i] = (Ua[7 * n + i] - Ub[7 * n + i]) * inv_tau;
+}
+
 // after the FLD substep: e += rho R_gas (T' - T) / (gamma - 1), E = E'; driven cells reset
 __global__ void k_w1_post(Wave1dDev P, double* __restrict__ U, const double* __restrict__ rho,
                           const double* __restrict__ T0, const double* __restrict__ T,
@@ -241,6 +302,24 @@ void launch_w1_stage(const Wave1dDev& P, const double* U0, const double* Uin, do
 void launch_w1_post(const Wave1dDev& P, double* U, const double* rho, const double* T0,
                     const double* T, const double* E, double t, cudaStream_t s) {
     k_w1_post<<<blocks_for(P.n), W1_THREADS, 0, s>>>(P, U, rho, T0, T, E, t);
+}
+
+void launch_w1_rhs(const Wave1dDev& P, const double* Fi, const double* fr, const double* vfr,
+                   const double* pt, double* Lout, cudaStream_t s) {
+    k_w1_rhs<<<blocks_for(P.n), W1_THREADS, 0, s>>>(P, Fi, fr, vfr, pt, Lout);
+}
+
+void launch_w1_comb(const Wave1dDev& P, const double* U0, const double* L1, const double* L2,
+                    const double* L3, double c1, double c2, double c3, const double* G2,
+                    const double* G3, double d2, double d3, double dt, double* Uout,
+                    double t_stage, cudaStream_t s) {
+    k_w1_comb<<<blocks_for(P.n), W1_THREADS, 0, s>>>(P, U0, L1, L2, L3, c1, c2, c3, G2, G3, d2,
+                                                      d3, dt, Uout, t_stage);
+}
+
+void launch_w1_incr(const Wave1dDev& P, const double* Ua, const double* Ub, double inv_tau,
+                    double* G, cudaStream_t s) {
+    k_w1_incr<<<blocks_for(P.n), W1_THREADS, 0, s>>>(P, Ua, Ub, inv_tau, G);
 }
 
 void launch_w1_speed(const Wave1dDev& P, const double* U, unsigned long long* out,

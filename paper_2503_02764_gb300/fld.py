@@ -45,7 +45,8 @@ class fld_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
                 ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
-                ("graph", C.c_int), ("cluster", C.c_int), ("inner", C.c_int)]
+                ("graph", C.c_int), ("cluster", C.c_int), ("inner", C.c_int),
+                ("direct1d", C.c_int)]
 
 
 class fld_stats(C.Structure):
@@ -67,7 +68,7 @@ class fld_wave1d_params(C.Structure):
                 ("Bx", C.c_double), ("R_gas", C.c_double), ("consts", fld_consts),
                 ("opacity", fld_opacity), ("E_right", C.c_double), ("W0", C.c_double * 8),
                 ("hat", C.c_double * 8), ("k", C.c_double), ("omega", C.c_double),
-                ("opts", fld_opts)]
+                ("opts", fld_opts), ("scheme", C.c_int), ("radiation", C.c_int)]
 
 
 class fld_patch(C.Structure):
@@ -121,6 +122,9 @@ def lib():
         "fld_wave1d_destroy": (C.c_int, [H]),
         "fld_wave1d_max_dt": (C.c_int, [H, P, C.c_double, C.POINTER(C.c_double), P]),
         "fld_wave1d_step": (C.c_int, [H, P, C.c_double, C.c_double, C.POINTER(fld_stats), P]),
+        "fld_ars3_tableau": (None, [C.POINTER(C.c_double)] * 4),
+        "fld_ars3_stage": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), C.c_double,
+                                     C.c_int, P, P, P, P, P, P, C.POINTER(fld_stats), P]),
         "fld_amr_create": (C.c_int, [C.POINTER(H), C.POINTER(fld_grid), C.POINTER(fld_patch),
                                      C.POINTER(fld_opts)]),
         "fld_amr_destroy": (C.c_int, [H]),
@@ -177,7 +181,7 @@ def make_grid(shape, h, bc):
 
 
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
-              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1):
+              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1, direct1d=1):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
@@ -186,6 +190,7 @@ def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coars
     o.graph = graph
     o.cluster = cluster
     o.inner = inner
+    o.direct1d = direct1d
     return o
 
 
@@ -448,10 +453,13 @@ def fld_wave1d_step(w, U, t, dt, stream=None, raise_on_error=True):
     return stats_dict(st) | {"status": rc}
 
 
-def make_wave1d_params(problem, **opts):
+def make_wave1d_params(problem, scheme=0, **opts):
     """fld_wave1d_params from a 1D wave problem (attributes n, n_driven, dx, gamma, Bx,
-    R_gas, c, a_r, kappa, E0, W0, hat, k, omega) and the FLD substep's options."""
+    R_gas, c, a_r, kappa, E0, W0, hat, k, omega), the time scheme (0 split, 1 ARS3) and the
+    FLD substep's options."""
     p = fld_wave1d_params()
+    p.scheme = int(scheme)
+    p.radiation = 1 if getattr(problem, "radiation", True) else 0
     p.n, p.n_driven = int(problem.n), int(problem.n_driven)
     p.dx, p.gamma, p.Bx, p.R_gas = (float(problem.dx), float(problem.gamma), float(problem.Bx),
                                     float(problem.R_gas))
@@ -470,8 +478,8 @@ class Wave1D:
     """Owns an fld_wave1d: the 1D radiation-MHD step on a caller's state U (device
     float64 [8][n])."""
 
-    def __init__(self, problem, **opts):
-        self.params = make_wave1d_params(problem, **opts)
+    def __init__(self, problem, scheme=0, **opts):
+        self.params = make_wave1d_params(problem, scheme, **opts)
         self.n = self.params.n
         self.w = fld_wave1d_create(self.params)
 
@@ -496,6 +504,27 @@ class Wave1D:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------ ARS3 IMEX stages
+def fld_ars3_tableau():
+    """(A_ex, A_im, b, c) of ARS(2,3,3) as numpy arrays (3 x 3, 3 x 3, 3, 3)."""
+    import numpy as np
+    ae, ai, b, c = (C.c_double * 9)(), (C.c_double * 9)(), (C.c_double * 3)(), (C.c_double * 3)()
+    lib().fld_ars3_tableau(ae, ai, b, c)
+    return (np.array(ae[:]).reshape(3, 3), np.array(ai[:]).reshape(3, 3), np.array(b[:]),
+            np.array(c[:]))
+
+
+def fld_ars3_stage(h, consts, opacity, dt, stage, rho, T, E, E_bc, F_E=None, F_e=None,
+                   stream=None, raise_on_error=True):
+    st = fld_stats()
+    rc = lib().fld_ars3_stage(h, C.byref(consts), C.byref(opacity), float(dt), int(stage),
+                              _ptr(rho), _ptr(T), _ptr(E), _ptr(E_bc), _ptr(F_E), _ptr(F_e),
+                              C.byref(st), _stream(stream))
+    if raise_on_error and rc not in (FLD_OK, FLD_ERR_NOT_CONVERGED):
+        _check(rc, "fld_ars3_stage")
+    return stats_dict(st) | {"status": rc}
 
 
 # ------------------------------------------------ composite grid (coarse block + refined box)

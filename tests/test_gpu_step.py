@@ -41,3 +41,26 @@ def test_total_energy_conserved_on_periodic_step():
     e1 = (O.internal_energy(P.rho, host(Td).reshape(P.shape), P.gamma, P.R_gas)
           + host(Ed).reshape(P.shape)).sum()
     assert abs(e1 - e0) / e0 < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
+def test_ars3_stage_is_the_substep_over_gamma_dt(precision, tol):
+    # fld_ars3_stage: the substep over gamma dt from the predictor, and the implicit
+    # increments (stage - predictor)/(gamma dt) of E and of the gas energy rho c_v T
+    torch = torch_cuda()
+    fld = library()
+    P = I.make_config(3, small=True)
+    hd = handle_for(fld, P, precision=precision, tol=1e-14, max_cycles=100)
+    g = (3 + np.sqrt(3)) / 6
+    Td, Ed, rd = dev(torch, P.T), dev(torch, P.E), dev(torch, P.rho)
+    FE, Fe = torch.empty_like(Ed), torch.empty_like(Ed)
+    st = fld.fld_ars3_stage(hd.h, consts_of(fld, P), fld.make_opacity(P.opacity), P.dt, 1, rd, Td,
+                            Ed, ebc_dev(torch, P), FE, Fe, raise_on_error=False)
+    assert st["status"] in (0, 3) and st["rel_resid"] < 1e-13, st
+    To, Eo, _ = O.step(P.rho, P.T, P.E, P.h, P.bc, P.E_bc, g * P.dt, P.c, P.a_r, P.gamma,
+                       P.R_gas, P.opacity, P.limiter, method="splu")
+    assert maxrel(host(Ed).reshape(P.shape), Eo) < tol
+    assert maxrel(host(Td).reshape(P.shape), To) < tol
+    cv = P.R_gas / (P.gamma - 1)
+    assert maxrel(host(FE).reshape(P.shape), (Eo - P.E) / (g * P.dt)) < 1e3 * tol
+    assert maxrel(host(Fe).reshape(P.shape), P.rho * cv * (To - P.T) / (g * P.dt)) < 1e3 * tol

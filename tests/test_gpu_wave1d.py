@@ -55,6 +55,57 @@ def test_wave_steps_match_oracle(kind):
     gpu.close()
 
 
+@pytest.mark.parametrize("kind", ["fast", "slow", "alfven"])
+def test_ars3_steps_match_oracle(kind):
+    # the ARS3 IMEX step (explicit hyperbolic and coupling terms, the FLD substep as its two
+    # implicit stages over gamma dt) against the oracle's, as for the split step
+    torch = torch_cuda()
+    fld = library()
+    P = _problem(kind=kind)
+    orc = R.Wave(P, cfl=0.8, scheme="ars3")
+    gpu = fld.Wave1D(P, scheme=1, **OPTS)
+    U = orc.initial()
+    Ud = dev(torch, U)
+    t = 0.0
+    for _ in range(12):
+        dt = orc.dt_max(U)
+        U = orc.step(U, t, dt)
+        st = gpu.step(Ud, t, dt)
+        assert st["status"] in (0, 3)
+        t += dt
+    G = host(Ud).reshape(8, -1)
+    W0 = P.W0[:, None]
+    cf = float(R.fast_speed(W0, P.Bx, P.gamma)[0])
+    e0 = float(R.conserved(W0, P.Bx, P.gamma)[R.PG][0])
+    Bmag = float(np.sqrt(P.Bx ** 2 + P.W0[4] ** 2 + P.W0[5] ** 2))
+    scales = [P.W0[0], P.W0[0] * cf, P.W0[0] * cf, P.W0[0] * cf, Bmag, Bmag, e0, P.E0]
+    for v in range(8):
+        assert np.max(np.abs(G[v] - U[v])) <= 1e-11 * scales[v], v
+    gpu.close()
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_ideal_mhd_steps_match_oracle(scheme):
+    # without radiation (no coupling terms, no substep): the hyperbolic scheme alone, the
+    # reference for the scheme's own damping
+    torch = torch_cuda()
+    fld = library()
+    P = I.wave1d(GOLD["table2_weak"]["background"], 280, 7, "fast", radiation=False)
+    orc = R.Wave(P, cfl=0.8, scheme="ars3" if scheme else "split")
+    gpu = fld.Wave1D(P, scheme=scheme, **OPTS)
+    U = orc.initial()
+    Ud = dev(torch, U)
+    t = 0.0
+    for _ in range(12):
+        dt = orc.dt_max(U)
+        U = orc.step(U, t, dt)
+        gpu.step(Ud, t, dt)
+        t += dt
+    G = host(Ud).reshape(8, -1)
+    assert np.max(np.abs(G - U) / np.maximum(np.abs(U).max(axis=1, keepdims=True), 1e-300)) < 1e-12
+    gpu.close()
+
+
 def test_radiative_fast_wave_damping_matches_oracle():
     # the strongly radiative fast wave of Table 3 over 5.5 wavelengths of travel at CFL 0.2:
     # the GPU run's measured spatial damping equals the oracle run's
