@@ -153,15 +153,32 @@ typedef struct {
     int direct1d;       /* 1D grids: 1 solves the tridiagonal system directly (parallel
                            cyclic reduction in FP64, a dozen launches; stats report one
                            cycle), 0 runs V-cycles as in 2D and 3D                      */
+    int diag;           /* diagnostics filled into fld_stats by fld_diffuse and fld_step
+                           when a stats pointer is given: FLD_DIAG_ENERGY adds the total
+                           energy before and after (two reductions), FLD_DIAG_TIMES the
+                           per-phase times (CUDA events on the stream); 0 = none        */
 } fld_opts;
 
+enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };
+
 /* Per-solve statistics (optional output). resid_hist[i] is the relative
-   residual after i cycles (resid_hist[0] before the first), for i < 64. */
+   residual after i cycles (resid_hist[0] before the first), for i < 64.
+   With FLD_DIAG_ENERGY in the handle's diag option: energy_before / energy_after are the
+   sums over the block of the energy per cell times the cell volume (prod h[d], d < ndim),
+   before the call and after it: E for fld_diffuse, rho c_v T + E (c_v = R_gas/(gamma-1),
+   the gas internal energy of Eq. energy_density plus the radiation energy) for fld_step.
+   With periodic and Neumann walls the two agree to the solve's tolerance (the discrete
+   diffusion operator and the exchange conserve energy); Dirichlet walls let energy in or
+   out. With FLD_DIAG_TIMES: t_ms = {limiter, diffusion solve, exchange, whole call} in
+   milliseconds between CUDA events on the call's stream (fld_diffuse fills the solve and
+   the whole call). Unrequested fields are zero. */
 typedef struct {
     int cycles;
     double rel_resid;
     double resid_hist[64];
     int levels;
+    double energy_before, energy_after;
+    double t_ms[4];
 } fld_stats;
 
 typedef struct fld_handle fld_handle;

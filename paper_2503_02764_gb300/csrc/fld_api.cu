@@ -34,6 +34,7 @@ struct DevScalars {       // read back together after each cycle
     double sum;
     unsigned err;
     unsigned pad;
+    double energy[2];     // diagnostics: total energy before and after a call
 };
 
 std::atomic<long long> g_launches{0};
@@ -143,6 +144,7 @@ struct fld_handle {
     long long vgraph_nodes = 0;
     // first level of the single-launch V-cycle tail (-1: none); set when the levels are built
     int tail_start = -1;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};   // per-phase times (diag)
 };
 
 namespace {
@@ -199,7 +201,8 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->smoother >= 0 && o->smoother <= 2) &&
            (o->cluster == 0 || o->cluster == 1 || o->cluster == 2 || o->cluster == 4 ||
             o->cluster == 8) &&
-           (o->inner >= 0 && o->inner <= 8) && (o->direct1d == 0 || o->direct1d == 1);
+           (o->inner >= 0 && o->inner <= 8) && (o->direct1d == 0 || o->direct1d == 1) &&
+           (o->diag >= 0 && o->diag <= (FLD_DIAG_ENERGY | FLD_DIAG_TIMES));
 }
 
 namespace {
@@ -282,6 +285,10 @@ fld_status dalloc(fld_handle* h, T** p, long long n) {
 }
 
 void free_all(fld_handle* h) {
+    for (cudaEvent_t& e : h->tev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->hscal) cudaFreeHost(h->hscal);
@@ -767,6 +774,11 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
         rc = FLD_ERR_NOMEM;
     }
     if (!rc && cudaMemset(h->scal, 0, sizeof(DevScalars)) != cudaSuccess) rc = FLD_ERR_CUDA;
+    for (int q = 0; q < 4 && !rc; ++q)
+        if (cudaEventCreate(&h->tev[q]) != cudaSuccess) {
+            h->tev[q] = nullptr;
+            rc = FLD_ERR_CUDA;
+        }
     if (!rc) {
         prepare_rb_sweep();
         prepare_vcycle_tail();
@@ -800,6 +812,49 @@ fld_status fld_set_opts(fld_handle* h, const fld_opts* o) {
 int fld_num_levels(const fld_handle* h) { return h ? h->nlev : 0; }
 
 namespace {
+// diagnostics: the energy sum of the block into energy[slot] (device), cell volume applied on
+// the host when read
+void energy_sum(fld_handle* h, const double* rho, const double* T, const double* E, double cv,
+                int slot, cudaStream_t s) {
+    run(h, "energy_sum", 0, h->ncell, s, [&] {
+        launch_energy_sum(h->ncell, rho, T, E, cv, h->partials, h->norm_blocks, s);
+    });
+    run(h, "finish_sum", 0, h->norm_blocks, s, [&] {
+        launch_finish_sum(h->partials, h->norm_blocks, &h->scal->energy[slot], s);
+    });
+}
+
+double cell_volume(const fld_handle* h) {
+    double v = 1.0;
+    for (int d = 0; d < h->g.ndim; ++d) v *= h->g.h[d];
+    return v;
+}
+
+bool want(const fld_handle* h, const fld_stats* st, int bit) { return st && (h->o.diag & bit); }
+
+// copies the diagnostics out of the scalars read back last (the stream is synchronised)
+void fill_diag(fld_handle* h, fld_stats* st, int phases) {
+    if (want(h, st, FLD_DIAG_ENERGY)) {
+        const double v = cell_volume(h);
+        st->energy_before = h->hscal->energy[0] * v;
+        st->energy_after = h->hscal->energy[1] * v;
+    }
+    if (want(h, st, FLD_DIAG_TIMES)) {
+        float ms = 0.f;
+        // phases: 3 = limiter, solve, exchange (events 0..3); 1 = solve (events 0, 3)
+        if (phases == 3) {
+            for (int q = 0; q < 3; ++q)
+                if (cudaEventElapsedTime(&ms, h->tev[q], h->tev[q + 1]) == cudaSuccess)
+                    st->t_ms[q] = ms;
+        }
+        if (cudaEventElapsedTime(&ms, h->tev[0], h->tev[3]) == cudaSuccess) {
+            st->t_ms[3] = ms;
+            if (phases == 1) st->t_ms[1] = ms;
+        }
+        cudaGetLastError();
+    }
+}
+
 // the limiter of a handle; kr (nullable) receives kappa rho for the exchange of the same step
 fld_status limiter_impl(fld_handle* h, const fld_consts* k, const fld_opacity* op, const double* E,
                         const double* rho, const double* T, const double* E_bc, double* D,
@@ -863,7 +918,21 @@ fld_status fld_diffuse(fld_handle* h, double dt, const double* D, const double* 
                        fld_stats* stats, void* stream) {
     if (!h || !D || !E || !(dt > 0) || !std::isfinite(dt)) return FLD_ERR_ARG;
     if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
-    return diffuse_impl(h, dt, D, E_bc, E, stats, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool en = want(h, stats, FLD_DIAG_ENERGY), tm = want(h, stats, FLD_DIAG_TIMES);
+    if (!en && !tm) return diffuse_impl(h, dt, D, E_bc, E, stats, s);
+    if (tm) FLD_CK(cudaEventRecord(h->tev[0], s));
+    if (en) energy_sum(h, nullptr, nullptr, E, 0.0, 0, s);
+    const fld_status rs = diffuse_impl(h, dt, D, E_bc, E, stats, s);
+    if (rs != FLD_OK && rs != FLD_ERR_NOT_CONVERGED) return rs;
+    if (en) energy_sum(h, nullptr, nullptr, E, 0.0, 1, s);
+    if (tm) FLD_CK(cudaEventRecord(h->tev[3], s));
+    double sum;
+    unsigned err;
+    const fld_status rc = read_scalars(h, s, &sum, &err);
+    if (rc) return rc;
+    fill_diag(h, stats, 1);
+    return rs;
 }
 
 fld_status fld_exchange(fld_handle* h, const fld_consts* k, const fld_opacity* op, double dt,
@@ -880,17 +949,26 @@ fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, d
         return FLD_ERR_ARG;
     if (has_dirichlet(h->g) && !E_bc) return FLD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool en = want(h, stats, FLD_DIAG_ENERGY), tm = want(h, stats, FLD_DIAG_TIMES);
+    const double cv = k->R_gas / (k->gamma - 1.0);
+    if (tm) FLD_CK(cudaEventRecord(h->tev[0], s));
+    if (en) energy_sum(h, rho, T, E, cv, 0, s);
     // the limiter freezes kappa rho at (rho, T^n) for the exchange (one opacity evaluation
     // per cell and step)
     fld_status rc = limiter_impl(h, k, op, E, rho, T, E_bc, h->Dscratch, nullptr, h->krscratch, s);
     if (rc) return rc;
+    if (tm) FLD_CK(cudaEventRecord(h->tev[1], s));
     // a solve that stopped at max_cycles still completes the substep from its last iterate
     // (the status reports it); any other failure stops here
     const fld_status rs = diffuse_impl(h, dt, h->Dscratch, E_bc, E, stats, s);
     if (rs != FLD_OK && rs != FLD_ERR_NOT_CONVERGED) return rs;
+    if (tm) FLD_CK(cudaEventRecord(h->tev[2], s));
     rc = exchange_impl(h, k, op, dt, rho, T, E, h->krscratch, s);
     if (rc) return rc;
+    if (en) energy_sum(h, rho, T, E, cv, 1, s);
+    if (tm) FLD_CK(cudaEventRecord(h->tev[3], s));
     rc = fld_get_status(h, stream);
+    if (!rc) fill_diag(h, stats, 3);
     return rc ? rc : rs;
 }
 

@@ -288,5 +288,8 @@ int launch_df_resid(const Lvl& L, const DfW& wd, const float* xh, const float* x
                      cudaStream_t s);
 void launch_sumsq(long long n, const double* v, double* partials, int nblocks, cudaStream_t s);
 void launch_finish_sum(const double* partials, int nparts, double* out, cudaStream_t s);
+// partial sums of c_v rho T + E over n cells (E alone when rho is null), nblocks partials
+void launch_energy_sum(long long n, const double* rho, const double* T, const double* E, double cv,
+                       double* partials, int nblocks, cudaStream_t s);
 
 }  // namespace fld

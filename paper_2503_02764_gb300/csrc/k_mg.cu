@@ -497,6 +497,26 @@ void launch_finish_sum(const double* partials, int nparts, double* out, cudaStre
     k_finish_sum<<<1, 1024, 0, s>>>(partials, nparts, out);
 }
 
+// partial sums of the energy density per cell, c_v rho T + E (E alone when rho is null)
+__global__ void k_energy_sum(long long n, const double* __restrict__ rho,
+                             const double* __restrict__ T, const double* __restrict__ E,
+                             double cv, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        a += E[p];
+        if (rho) a = fma(cv * rho[p], T[p], a);
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+}
+
+void launch_energy_sum(long long n, const double* rho, const double* T, const double* E, double cv,
+                       double* partials, int nblocks, cudaStream_t s) {
+    k_energy_sum<<<nblocks, 256, 0, s>>>(n, rho, T, E, cv, partials);
+}
+
 // explicit instantiations
 #define FLD_INST(T)                                                                              \
     template void launch_restrict_K<T>(const Lvl&, const Lvl&, double, const T*, T*, cudaStream_t); \

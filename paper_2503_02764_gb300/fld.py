@@ -15,6 +15,7 @@ LIBPATH = os.path.join(HERE, "libfld_gb300.so")
 FLD_OK, FLD_ERR_ARG, FLD_ERR_DOMAIN, FLD_ERR_NOT_CONVERGED, FLD_ERR_TIMEOUT, FLD_ERR_CUDA, \
     FLD_ERR_NOMEM = range(7)
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
+DIAG_ENERGY, DIAG_TIMES = 1, 2
 LIMITER_LP, LIMITER_DIFFUSION, LIMITER_MINERBO = 0, 1, 2
 OPACITY_CONST, OPACITY_POWER, OPACITY_TABLE = 0, 1, 2
 
@@ -46,12 +47,13 @@ class fld_opts(C.Structure):
                 ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
                 ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
                 ("graph", C.c_int), ("cluster", C.c_int), ("inner", C.c_int),
-                ("direct1d", C.c_int)]
+                ("direct1d", C.c_int), ("diag", C.c_int)]
 
 
 class fld_stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("rel_resid", C.c_double), ("resid_hist", C.c_double * 64),
-                ("levels", C.c_int)]
+                ("levels", C.c_int), ("energy_before", C.c_double), ("energy_after", C.c_double),
+                ("t_ms", C.c_double * 4)]
 
 
 class fld_prof_entry(C.Structure):
@@ -181,7 +183,8 @@ def make_grid(shape, h, bc):
 
 
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
-              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1, direct1d=1):
+              limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1, direct1d=1,
+              diag=0):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
@@ -191,6 +194,7 @@ def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coars
     o.cluster = cluster
     o.inner = inner
     o.direct1d = direct1d
+    o.diag = diag
     return o
 
 
@@ -221,7 +225,9 @@ def make_opacity(op, table=None):
 def stats_dict(st):
     n = min(st.cycles, 63)
     return {"cycles": st.cycles, "rel_resid": st.rel_resid, "levels": st.levels,
-            "resid_hist": [st.resid_hist[i] for i in range(n + 1)]}
+            "resid_hist": [st.resid_hist[i] for i in range(n + 1)],
+            "energy_before": st.energy_before, "energy_after": st.energy_after,
+            "t_ms": [st.t_ms[i] for i in range(4)]}
 
 
 # ------------------------------------------------ C entry points, same names

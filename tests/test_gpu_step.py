@@ -64,3 +64,45 @@ def test_ars3_stage_is_the_substep_over_gamma_dt(precision, tol):
     cv = P.R_gas / (P.gamma - 1)
     assert maxrel(host(FE).reshape(P.shape), (Eo - P.E) / (g * P.dt)) < 1e3 * tol
     assert maxrel(host(Fe).reshape(P.shape), P.rho * cv * (To - P.T) / (g * P.dt)) < 1e3 * tol
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_step_diagnostics_energy_and_phase_times(cfg):
+    # diag = energy | times: the energy sums are those of the fields before and after the
+    # step (rho c_v T + E times the cell volume, summed in numpy), equal to each other on the
+    # periodic config 2; Dirichlet walls (config 3) let energy through. Phase times are
+    # positive and the whole call covers the three phases
+    torch = torch_cuda()
+    fld = library()
+    P = I.make_config(cfg, small=True)
+    hd = handle_for(fld, P, precision=1, tol=1e-12, diag=fld.DIAG_ENERGY | fld.DIAG_TIMES)
+    Td, Ed, rd = dev(torch, P.T), dev(torch, P.E), dev(torch, P.rho)
+    vol = float(np.prod(P.h))
+
+    def total(T, E):
+        return float((O.internal_energy(P.rho, T, P.gamma, P.R_gas) + E).sum()) * vol
+
+    e0 = total(P.T, P.E)
+    st = hd.step(consts_of(fld, P), fld.make_opacity(P.opacity), P.dt, rd, Td, Ed,
+                 ebc_dev(torch, P))
+    e1 = total(host(Td).reshape(P.shape), host(Ed).reshape(P.shape))
+    assert st["energy_before"] == pytest.approx(e0, rel=1e-13)
+    assert st["energy_after"] == pytest.approx(e1, rel=1e-13)
+    if cfg == 2:
+        assert abs(st["energy_after"] - st["energy_before"]) <= 1e-12 * e0
+    t = st["t_ms"]
+    assert all(x > 0 for x in t), t
+    assert t[3] >= 0.99 * (t[0] + t[1] + t[2]), t
+    # the solve alone through fld_diffuse: E summed before and after
+    Dd = torch.empty_like(Ed)
+    hd.limiter(consts_of(fld, P), fld.make_opacity(P.opacity), Ed, rd, Td, ebc_dev(torch, P), Dd)
+    E0 = host(Ed).reshape(P.shape)
+    st = hd.diffuse(P.dt, Dd, ebc_dev(torch, P), Ed)
+    assert st["energy_before"] == pytest.approx(float(E0.sum()) * vol, rel=1e-13)
+    assert st["energy_after"] == pytest.approx(float(host(Ed).sum()) * vol, rel=1e-13)
+    assert st["t_ms"][1] > 0 and st["t_ms"][0] == 0 and st["t_ms"][2] == 0
+    # without diag the fields stay zero
+    hd.set_opts(precision=1, tol=1e-12)
+    st = hd.step(consts_of(fld, P), fld.make_opacity(P.opacity), P.dt, rd, Td, Ed,
+                 ebc_dev(torch, P))
+    assert st["energy_before"] == 0 and st["t_ms"] == [0.0] * 4
