@@ -157,9 +157,18 @@ typedef struct {
                            when a stats pointer is given: FLD_DIAG_ENERGY adds the total
                            energy before and after (two reductions), FLD_DIAG_TIMES the
                            per-phase times (CUDA events on the stream); 0 = none        */
+    int face_mean;      /* face coefficient w_f of the diffusion operator from the two
+                           cell values D_i, D_j: FLD_FACE_ARITH (D_i + D_j)/2, the
+                           default, or FLD_FACE_HARM 2 D_i D_j/(D_i + D_j), which keeps
+                           the flux through layers of unequal D that of resistances in
+                           series. HARM is taken by FP64 and MIXED handles (their fine
+                           levels then use the generic half-sweep smoother and residual
+                           kernels, not the z-marching ones), not by MIXED_DF, the
+                           batched step or the composite grid (FLD_ERR_ARG)            */
 } fld_opts;
 
 enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };
+enum { FLD_FACE_ARITH = 0, FLD_FACE_HARM = 1 };
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative
    residual after i cycles (resid_hist[0] before the first), for i < 64.
@@ -238,8 +247,8 @@ fld_status fld_coupling(fld_handle* h, const fld_consts* k, const fld_opacity* o
                         double* f_edd, double* vfr, double* ptire, void* stream);
 
 /* Backward-Euler diffusion step: solves A E^{n+1} = E^n + g in place,
-     (A x)_i = x_i + sum_faces (dt/h_d^2) w_f (x_i - x_j),  w_f = (D_i + D_j)/2,
-   a Dirichlet face adding (dt/h_d^2) 2 D_i (x_i - E_b) (g holds the E_b part),
+     (A x)_i = x_i + sum_faces (dt/h_d^2) w_f (x_i - x_j),  w_f = (D_i + D_j)/2
+   (2 D_i D_j/(D_i + D_j) with the face_mean option FLD_FACE_HARM), a Dirichlet face adding (dt/h_d^2) 2 D_i (x_i - E_b) (g holds the E_b part),
    a Neumann face nothing.
    In:  dt > 0; D (device, ncell float64, > 0); E_bc as for fld_limiter.
    In/out: E (device, ncell float64): E^n on entry, E^{n+1} on return (the last

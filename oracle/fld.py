@@ -14,7 +14,8 @@ diffusion and exchange terms):
               Pomraning), D = c lambda / (kappa rho) (Eq. fld_F).
 2. diffuse:   one backward-Euler step of dE/dt = div(D grad E) (the div F
               term of Eq. mhd_r_e with F = -D grad E), cell-centred finite
-              volumes, face D = arithmetic mean of the two cell values;
+              volumes, face D = arithmetic mean of the two cell values (the
+              harmonic mean 2 D_i D_j / (D_i + D_j) as an option);
               the linear system A x = b is solved directly (dense LU) or by
               Jacobi-preconditioned CG to a relative residual of 1e-14.
 3. exchange:  backward Euler on de/dt = +qdot, dE/dt = -qdot with
@@ -214,11 +215,22 @@ def coupling(E, rho, T, h, bc, E_bc, c, op, v=None, mode=0):
 
 
 # ----------------------------------------------------------------- diffusion
-def assemble(D, h, bc, E_bc, dt):
+def face_coefficient(Di, Dj, face_mean="arith"):
+    """Face D between two cells: the arithmetic mean (D_i + D_j)/2, or the harmonic mean
+    2 D_i D_j / (D_i + D_j), the face value for which the flux through cells of unequal
+    D equals that of resistances h/D in series."""
+    if face_mean == "arith":
+        return 0.5 * (Di + Dj)
+    if face_mean == "harm":
+        return 2.0 * Di * Dj / (Di + Dj)
+    raise ValueError(face_mean)
+
+
+def assemble(D, h, bc, E_bc, dt, face_mean="arith"):
     """Backward-Euler matrix A and the Dirichlet right-hand-side term g.
 
     (A x)_i = x_i + sum over faces f of i of (dt/h_d^2) w_f (x_i - x_j),
-    w_f = (D_i + D_j)/2 for interior/periodic faces; a Dirichlet face adds
+    w_f = face_coefficient(D_i, D_j) for interior/periodic faces; a Dirichlet face adds
     (dt/h_d^2) 2 D_i (x_i - E_b), i.e. 2 dt D_i/h_d^2 to A_ii and
     2 dt D_i E_b/h_d^2 to g_i. Neumann faces carry no flux.
     """
@@ -239,7 +251,7 @@ def assemble(D, h, bc, E_bc, dt):
         for f in range(nfaces):
             i = np.take(idx, f, axis=a).ravel()
             j = np.take(idx, (f + 1) % n, axis=a).ravel()
-            w = s * 0.5 * (Df[i] + Df[j])
+            w = s * face_coefficient(Df[i], Df[j], face_mean)
             np.add.at(diag, i, w)
             np.add.at(diag, j, w)
             rows += [i, j]
@@ -283,9 +295,9 @@ def pcg(A, b, x0, rtol=1e-14, maxiter=100000):
     return x, it
 
 
-def diffuse(E, D, h, bc, E_bc, dt, method="auto"):
+def diffuse(E, D, h, bc, E_bc, dt, method="auto", face_mean="arith"):
     """E^{n+1} = A^{-1}(E^n + g) for the backward-Euler diffusion step."""
-    A, g = assemble(D, h, bc, E_bc, dt)
+    A, g = assemble(D, h, bc, E_bc, dt, face_mean)
     b = E.ravel() + g
     if method == "auto":
         method = "lu" if E.size <= 4096 else "pcg"
@@ -299,14 +311,14 @@ def diffuse(E, D, h, bc, E_bc, dt, method="auto"):
     return x.reshape(E.shape)
 
 
-def relative_residual(x, E, D, h, bc, E_bc, dt):
+def relative_residual(x, E, D, h, bc, E_bc, dt, face_mean="arith"):
     """||b - A x||_2 / ||b||_2 with b = E^n + g (plain sparse matvec)."""
-    A, g = assemble(D, h, bc, E_bc, dt)
+    A, g = assemble(D, h, bc, E_bc, dt, face_mean)
     b = E.ravel() + g
     return np.linalg.norm(b - A @ x.ravel()) / np.linalg.norm(b)
 
 
-def apply_operator(x, D, h, bc, dt):
+def apply_operator(x, D, h, bc, dt, face_mean="arith"):
     """A x without boundary data (homogeneous Dirichlet), by direct stencil sums.
 
     A second, matrix-free statement of the same operator, used to check any
@@ -321,7 +333,7 @@ def apply_operator(x, D, h, bc, dt):
         for off in (-1, 1):
             xn = np.roll(x, -off, axis=a)
             Dn = np.roll(D, -off, axis=a)
-            w = s * 0.5 * (D + Dn)
+            w = s * face_coefficient(D, Dn, face_mean)
             contrib = w * (x - xn)
             edge = [slice(None)] * ndim
             edge[a] = (n - 1) if off == 1 else 0
@@ -391,14 +403,15 @@ def internal_energy(rho, T, gamma, R_gas):
 
 
 # ----------------------------------------------------------------- substep
-def step(rho, T, E, h, bc, E_bc, dt, c, a_r, gamma, R_gas, op, mode=0, method="auto"):
+def step(rho, T, E, h, bc, E_bc, dt, c, a_r, gamma, R_gas, op, mode=0, method="auto",
+         face_mean="arith"):
     """limiter -> backward-Euler diffusion -> exchange (opacity frozen at T^n).
 
     Returns (T', E', D). The exchange uses kappa(rho, T^n), the same value the
     limiter used.
     """
     D, _, _ = limiter(E, rho, T, h, bc, E_bc, c, op, mode)
-    E1 = diffuse(E, D, h, bc, E_bc, dt, method)
+    E1 = diffuse(E, D, h, bc, E_bc, dt, method, face_mean)
     kappa = opacity(op, rho, T)
     T2, E2 = exchange(rho, T, E1, dt, c, a_r, gamma, R_gas, ("field", kappa))
     return T2, E2, D

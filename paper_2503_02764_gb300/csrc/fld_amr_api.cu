@@ -78,7 +78,8 @@ fld_status fld_amr_create(fld_amr** out, const fld_grid* g, const fld_patch* pat
     fld_opts def;
     fld_default_opts(&def);
     if (!o) o = &def;
-    if (!opts_valid(o)) return FLD_ERR_ARG;
+    // the composite operator uses the arithmetic face mean
+    if (!opts_valid(o) || o->face_mean != FLD_FACE_ARITH) return FLD_ERR_ARG;
     AmrGeom G;
     memset(&G, 0, sizeof(G));
     G.nd = g->ndim;

@@ -202,7 +202,9 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->cluster == 0 || o->cluster == 1 || o->cluster == 2 || o->cluster == 4 ||
             o->cluster == 8) &&
            (o->inner >= 0 && o->inner <= 8) && (o->direct1d == 0 || o->direct1d == 1) &&
-           (o->diag >= 0 && o->diag <= (FLD_DIAG_ENERGY | FLD_DIAG_TIMES));
+           (o->diag >= 0 && o->diag <= (FLD_DIAG_ENERGY | FLD_DIAG_TIMES)) &&
+           (o->face_mean == FLD_FACE_ARITH ||
+            (o->face_mean == FLD_FACE_HARM && o->precision != FLD_PREC_MIXED_DF));
 }
 
 namespace {
@@ -258,6 +260,7 @@ bool has_dirichlet(const fld_grid& g) {
 
 void build_levels(fld_handle* h) {
     h->nlev = fld::make_levels(h->g, h->lv, h->kscale_down, MAX_LEVELS);
+    for (int l = 0; l < h->nlev; ++l) h->lv[l].fm = h->o.face_mean;
     // the tail starts at the first level small enough for one block (cells, and all its
     // levels in shared memory even in FP64), if the coarsest level takes the dense solve
     // and at least two levels remain
@@ -805,7 +808,14 @@ fld_status fld_destroy(fld_handle* h) {
 
 fld_status fld_set_opts(fld_handle* h, const fld_opts* o) {
     if (!h || !opts_ok(o)) return FLD_ERR_ARG;
+    const bool fm_changed = o->face_mean != h->o.face_mean;
     h->o = *o;
+    if (fm_changed) {
+        // the levels carry the face mean, and a captured V-cycle holds them by value
+        FLD_CK(cudaDeviceSynchronize());
+        graph_free(h);
+        for (int l = 0; l < h->nlev; ++l) h->lv[l].fm = o->face_mean;
+    }
     return FLD_OK;
 }
 

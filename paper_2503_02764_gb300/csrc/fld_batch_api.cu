@@ -66,7 +66,9 @@ void batch_free(fld_batch* b) {
 int block_threads(const fld_opts& o) { return o.block ? o.block : 512; }
 
 bool batch_opts_ok(const fld_opts* o) {
-    return fld::opts_valid(o) && (o->block == 0 || batch_threads_supported(o->block));
+    // the batched kernels use the arithmetic face mean
+    return fld::opts_valid(o) && o->face_mean == FLD_FACE_ARITH &&
+           (o->block == 0 || batch_threads_supported(o->block));
 }
 
 // blocks per problem: the option, or the smallest cluster giving the largest problem

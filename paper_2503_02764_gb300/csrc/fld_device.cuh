@@ -39,7 +39,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
             if (c[d] > 0) q = p - stride;
             else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
             if (q >= 0) {
-                const T w = T(0.5) * (Kc + K[q]) * wd;
+                const T w = fmean(Kc, K[q], L.fm) * wd;
                 sw += w;
                 acc += w * x[q];
             } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
             if (c[d] < n - 1) q = p + stride;
             else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
             if (q >= 0) {
-                const T w = T(0.5) * (Kc + K[q]) * wd;
+                const T w = fmean(Kc, K[q], L.fm) * wd;
                 sw += w;
                 acc += w * x[q];
             } else if (L.bchi[d] == FLD_BC_DIRICHLET) {

@@ -21,7 +21,21 @@ struct Lvl {
     double w[3];    // axis weights (H_x / H_d)^2
     float wf[3];    // the same in FP32 (FP32 kernels never touch FP64 values)
     long long ncell;
+    int fm;         // face coefficient from the two cell values: 0 arithmetic, 1 harmonic mean
 };
+
+// Twice the face coefficient between two cells with cell coefficients a and b: a + b
+// (arithmetic mean, fm = 0) or 4ab/(a + b) (harmonic mean, fm = 1; zero when a + b is not
+// positive). The flag is uniform over a launch.
+template <typename T>
+__host__ __device__ __forceinline__ T fsum2(T a, T b, int fm) {
+    const T s = a + b;
+    if (fm == 0) return s;
+    return s > T(0) ? T(4) * a * b / s : T(0);
+}
+// the face coefficient itself: (a + b)/2 or 2ab/(a + b)
+template <typename T>
+__host__ __device__ __forceinline__ T fmean(T a, T b, int fm) { return T(0.5) * fsum2(a, b, fm); }
 
 // Axis weight in the kernel's arithmetic type.
 template <typename T>

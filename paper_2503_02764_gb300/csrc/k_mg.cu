@@ -159,27 +159,27 @@ __device__ __forceinline__ void rb_cell(const Lvl& L, int i, int j, int k, T* __
     T sw = T(0), acc = T(0);
     const T wx = wgt<T>(L, 0);
     int q = i > 0 ? p - 1 : (L.bclo[0] == FLD_BC_PERIODIC ? p + nx - 1 : -1);
-    if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wx; sw += w; acc += w * x[q]; }
+    if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wx; sw += w; acc += w * x[q]; }
     else if (L.bclo[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
     q = i < nx - 1 ? p + 1 : (L.bchi[0] == FLD_BC_PERIODIC ? p - nx + 1 : -1);
-    if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wx; sw += w; acc += w * x[q]; }
+    if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wx; sw += w; acc += w * x[q]; }
     else if (L.bchi[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
     if (L.ndim >= 2) {
         const T wy = wgt<T>(L, 1);
         q = j > 0 ? p - sy : (L.bclo[1] == FLD_BC_PERIODIC ? p + (ny - 1) * sy : -1);
-        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wy; sw += w; acc += w * x[q]; }
+        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wy; sw += w; acc += w * x[q]; }
         else if (L.bclo[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
         q = j < ny - 1 ? p + sy : (L.bchi[1] == FLD_BC_PERIODIC ? p - (ny - 1) * sy : -1);
-        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wy; sw += w; acc += w * x[q]; }
+        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wy; sw += w; acc += w * x[q]; }
         else if (L.bchi[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
     }
     if (L.ndim >= 3) {
         const T wz = wgt<T>(L, 2);
         q = k > 0 ? p - sz : (L.bclo[2] == FLD_BC_PERIODIC ? p + (nz - 1) * sz : -1);
-        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wz; sw += w; acc += w * x[q]; }
+        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wz; sw += w; acc += w * x[q]; }
         else if (L.bclo[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
         q = k < nz - 1 ? p + sz : (L.bchi[2] == FLD_BC_PERIODIC ? p - (nz - 1) * sz : -1);
-        if (q >= 0) { const T w = T(0.5) * (kc + K[q]) * wz; sw += w; acc += w * x[q]; }
+        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wz; sw += w; acc += w * x[q]; }
         else if (L.bchi[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
     }
     x[p] = div_fast<T>(b[p] + acc, T(1) + sw);
@@ -256,7 +256,7 @@ __global__ void k_resid_restrict(Lvl F, Lvl C, const T* __restrict__ x, const T*
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
                            int block, cudaStream_t s) {
-    if (transfer3_ok(F, C)) return launch_resid_restrict3<T>(F, C, x, b, K, bc, s);
+    if (transfer3_ok(F, C) && !F.fm) return launch_resid_restrict3<T>(F, C, x, b, K, bc, s);
     k_resid_restrict<T><<<grid_for(C.ncell, block), block, 0, s>>>(F, C, x, b, K, bc);
 }
 
@@ -363,7 +363,7 @@ __global__ void k_coarse_dense(Lvl L, T* __restrict__ x, const T* __restrict__ b
                     else if (kind == FLD_BC_PERIODIC) q = r - (nd - 1) * stride;
                 }
                 if (q >= 0) {
-                    const double w = 0.5 * (kc + (double)K[q]) * wd;
+                    const double w = fmean(kc, (double)K[q], L.fm) * wd;
                     diag += w;
                     A[r][q] -= w;
                 } else if (kind == FLD_BC_DIRICHLET) {
@@ -427,21 +427,21 @@ __global__ void k_resid64(Lvl L, const double* __restrict__ x, const double* __r
             double ax = 0.0, ay = 0.0, az = 0.0, dir = 0.0;
             // x faces
             int q = i > 0 ? p - 1 : (L.bclo[0] == FLD_BC_PERIODIC ? p + nx - 1 : -1);
-            if (q >= 0) ax = fma(kc + K[q], xc - x[q], ax);
+            if (q >= 0) ax = fma(fsum2(kc, K[q], L.fm), xc - x[q], ax);
             else if (L.bclo[0] == FLD_BC_DIRICHLET) dir += L.w[0];
             q = i < nx - 1 ? p + 1 : (L.bchi[0] == FLD_BC_PERIODIC ? p - nx + 1 : -1);
-            if (q >= 0) ax = fma(kc + K[q], xc - x[q], ax);
+            if (q >= 0) ax = fma(fsum2(kc, K[q], L.fm), xc - x[q], ax);
             else if (L.bchi[0] == FLD_BC_DIRICHLET) dir += L.w[0];
             if (L.ndim >= 2) {
-                if (oym != -1) ay = fma(kc + K[p + oym], xc - x[p + oym], ay);
+                if (oym != -1) ay = fma(fsum2(kc, K[p + oym], L.fm), xc - x[p + oym], ay);
                 else if (L.bclo[1] == FLD_BC_DIRICHLET) dir += L.w[1];
-                if (oyp != -1) ay = fma(kc + K[p + oyp], xc - x[p + oyp], ay);
+                if (oyp != -1) ay = fma(fsum2(kc, K[p + oyp], L.fm), xc - x[p + oyp], ay);
                 else if (L.bchi[1] == FLD_BC_DIRICHLET) dir += L.w[1];
             }
             if (L.ndim >= 3) {
-                if (ozm != -1) az = fma(kc + K[p + ozm], xc - x[p + ozm], az);
+                if (ozm != -1) az = fma(fsum2(kc, K[p + ozm], L.fm), xc - x[p + ozm], az);
                 else if (L.bclo[2] == FLD_BC_DIRICHLET) dir += L.w[2];
-                if (ozp != -1) az = fma(kc + K[p + ozp], xc - x[p + ozp], az);
+                if (ozp != -1) az = fma(fsum2(kc, K[p + ozp], L.fm), xc - x[p + ozp], az);
                 else if (L.bchi[2] == FLD_BC_DIRICHLET) dir += L.w[2];
             }
             double res = fma(-hx, ax, b[p] - xc);

@@ -336,7 +336,8 @@ bool rb_sweep_supported(const Lvl& L) {
     if constexpr (sizeof(T) != 4) {
         return false;
     } else {
-        if (L.ndim != 3 || L.n[0] % 4 != 0 || L.n[0] < 16) return false;
+        // the arithmetic face mean only (the harmonic one takes the half sweeps)
+        if (L.fm || L.ndim != 3 || L.n[0] % 4 != 0 || L.n[0] < 16) return false;
         for (int d = 0; d < 3; ++d)
             if (L.bclo[d] == FLD_BC_PERIODIC && (L.n[d] & 1)) return false;
         return true;

@@ -229,7 +229,7 @@ int g_rz_slots[64];        // resident blocks of the kernel on the whole GPU, pe
 }  // namespace
 
 bool resid64z_ok(const Lvl& L, int nblocks) {
-    if (L.ndim != 3) return false;
+    if (L.ndim != 3 || L.fm) return false;     // arithmetic face mean only
     const int tiles = ((L.n[0] + RZ_TX - 1) / RZ_TX) * ((L.n[1] + RZ_TY - 1) / RZ_TY);
     return tiles <= nblocks;
 }
@@ -304,7 +304,7 @@ __global__ void k_resid32_init(Lvl L, const double* __restrict__ x, const double
                     if (c[d] > 0) q = p - stride;
                     else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
                     if (q >= 0) {
-                        const float w = 0.5f * (Kc + K[q]) * wd;
+                        const float w = fmean(Kc, K[q], L.fm) * wd;
                         sw += w;
                         acc = fmaf(w, f32_of(x[q]), acc);
                     } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
@@ -314,7 +314,7 @@ __global__ void k_resid32_init(Lvl L, const double* __restrict__ x, const double
                     if (c[d] < n - 1) q = p + stride;
                     else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
                     if (q >= 0) {
-                        const float w = 0.5f * (Kc + K[q]) * wd;
+                        const float w = fmean(Kc, K[q], L.fm) * wd;
                         sw += w;
                         acc = fmaf(w, f32_of(x[q]), acc);
                     } else if (L.bchi[d] == FLD_BC_DIRICHLET) {

@@ -133,7 +133,7 @@ __device__ void tail_dense(const Lvl& L, T* __restrict__ x, const T* __restrict_
                     else if (kind == FLD_BC_PERIODIC) q = r - (nd - 1) * stride;
                 }
                 if (q >= 0) {
-                    const double w = 0.5 * (kc + (double)K[q]) * wd;
+                    const double w = fmean(kc, (double)K[q], L.fm) * wd;
                     diag += w;
                     A[r][q] -= w;
                 } else if (kind == FLD_BC_DIRICHLET) {

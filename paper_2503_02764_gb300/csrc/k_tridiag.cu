@@ -1,6 +1,7 @@
 // Direct solve of a 1D level's backward-Euler system (the 3-point operator of k_mg.cu,
 //   -w_{i-1} x_{i-1} + (1 + w_{i-1} + w_i + Dirichlet) x_i - w_i x_{i+1} = b_i,
-//   w_i = (K_i + K_{i+1})/2, a Dirichlet wall adding 2 K_i to the diagonal)
+//   w_i the arithmetic or harmonic mean of K_i and K_{i+1}, a Dirichlet wall adding 2 K_i
+//   to the diagonal)
 // by parallel cyclic reduction: at stride s every row eliminates its neighbours i - s and
 // i + s with their own rows, coupling it to i - 2s and i + 2s; after ceil(log2 n) steps each
 // row holds one unknown. One launch per step over all cells (a 1D grid of a few thousand
@@ -21,7 +22,7 @@ namespace {
 constexpr int TRI_T = 256;
 
 // rows of T and the right-hand sides b (d) and u (e, periodic only); sc[0] = a_0 / gamma
-__global__ void k_tri_setup(int n, int lo_bc, int hi_bc, const double* __restrict__ K,
+__global__ void k_tri_setup(int n, int lo_bc, int hi_bc, int fm, const double* __restrict__ K,
                             const double* __restrict__ rhs, double* __restrict__ a,
                             double* __restrict__ b, double* __restrict__ c, double* __restrict__ d,
                             double* __restrict__ e, double* __restrict__ sc) {
@@ -29,11 +30,11 @@ __global__ void k_tri_setup(int n, int lo_bc, int hi_bc, const double* __restric
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double Ki = K[i];
         double wl = 0.0, wr = 0.0, dg = 1.0;
-        if (i > 0) wl = 0.5 * (Ki + K[i - 1]);
-        else if (per) wl = 0.5 * (Ki + K[n - 1]);
+        if (i > 0) wl = fmean(Ki, K[i - 1], fm);
+        else if (per) wl = fmean(Ki, K[n - 1], fm);
         else if (lo_bc == FLD_BC_DIRICHLET) dg += 2.0 * Ki;
-        if (i < n - 1) wr = 0.5 * (Ki + K[i + 1]);
-        else if (per) wr = 0.5 * (Ki + K[0]);
+        if (i < n - 1) wr = fmean(Ki, K[i + 1], fm);
+        else if (per) wr = fmean(Ki, K[0], fm);
         else if (hi_bc == FLD_BC_DIRICHLET) dg += 2.0 * Ki;
         dg += wl + wr;
         double ai = -wl, ci = -wr;
@@ -41,8 +42,8 @@ __global__ void k_tri_setup(int n, int lo_bc, int hi_bc, const double* __restric
         if (per) {
             // corners a_0 (couples x_{n-1}) and c_{n-1} (couples x_0) into u v^T
             const double K0 = K[0], Kn = K[n - 1];
-            const double wc = 0.5 * (K0 + Kn);
-            double dg0 = 1.0 + wc + (n > 1 ? 0.5 * (K0 + K[1]) : 0.0);
+            const double wc = fmean(K0, Kn, fm);
+            double dg0 = 1.0 + wc + (n > 1 ? fmean(K0, K[1], fm) : 0.0);
             const double gamma = -dg0;
             const double a0 = -wc, cn = -wc;
             e[i] = 0.0;
@@ -116,7 +117,7 @@ int launch_tridiag_solve(const Lvl& L, const double* K, const double* rhs, doubl
     double* sc = w + 10LL * n;
     const int two = L.bclo[0] == FLD_BC_PERIODIC ? 1 : 0;
     const int nb = tri_blocks(n);
-    k_tri_setup<<<nb, TRI_T, 0, s>>>(n, L.bclo[0], L.bchi[0], K, rhs, A[0][0], A[0][1], A[0][2],
+    k_tri_setup<<<nb, TRI_T, 0, s>>>(n, L.bclo[0], L.bchi[0], L.fm, K, rhs, A[0][0], A[0][1], A[0][2],
                                      A[0][3], A[0][4], sc);
     int launches = 1, cur = 0;
     for (int st = 1; st < n; st *= 2) {
