@@ -165,10 +165,18 @@ typedef struct {
                            levels then use the generic half-sweep smoother and residual
                            kernels, not the z-marching ones), not by MIXED_DF, the
                            batched step or the composite grid (FLD_ERR_ARG)            */
+    int prolong;        /* V-cycle prolongation of the coarse correction:
+                           FLD_PROLONG_LINEAR (bi/trilinear, cell-centred: 3/4 parent +
+                           1/4 neighbour per coarsened axis, walls mirrored), the
+                           default, or FLD_PROLONG_CONSTANT (the parent's value). The
+                           choice changes the convergence rate, not the solution.
+                           CONSTANT runs the generic prolongation kernel; the batched
+                           step takes LINEAR only                                      */
 } fld_opts;
 
 enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };
 enum { FLD_FACE_ARITH = 0, FLD_FACE_HARM = 1 };
+enum { FLD_PROLONG_LINEAR = 0, FLD_PROLONG_CONSTANT = 1 };
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative
    residual after i cycles (resid_hist[0] before the first), for i < 64.

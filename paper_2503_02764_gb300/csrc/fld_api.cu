@@ -204,7 +204,8 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->inner >= 0 && o->inner <= 8) && (o->direct1d == 0 || o->direct1d == 1) &&
            (o->diag >= 0 && o->diag <= (FLD_DIAG_ENERGY | FLD_DIAG_TIMES)) &&
            (o->face_mean == FLD_FACE_ARITH ||
-            (o->face_mean == FLD_FACE_HARM && o->precision != FLD_PREC_MIXED_DF));
+            (o->face_mean == FLD_FACE_HARM && o->precision != FLD_PREC_MIXED_DF)) &&
+           (o->prolong == FLD_PROLONG_LINEAR || o->prolong == FLD_PROLONG_CONSTANT);
 }
 
 namespace {
@@ -260,7 +261,10 @@ bool has_dirichlet(const fld_grid& g) {
 
 void build_levels(fld_handle* h) {
     h->nlev = fld::make_levels(h->g, h->lv, h->kscale_down, MAX_LEVELS);
-    for (int l = 0; l < h->nlev; ++l) h->lv[l].fm = h->o.face_mean;
+    for (int l = 0; l < h->nlev; ++l) {
+        h->lv[l].fm = h->o.face_mean;
+        h->lv[l].pk = h->o.prolong;
+    }
     // the tail starts at the first level small enough for one block (cells, and all its
     // levels in shared memory even in FP64), if the coarsest level takes the dense solve
     // and at least two levels remain
@@ -808,13 +812,17 @@ fld_status fld_destroy(fld_handle* h) {
 
 fld_status fld_set_opts(fld_handle* h, const fld_opts* o) {
     if (!h || !opts_ok(o)) return FLD_ERR_ARG;
-    const bool fm_changed = o->face_mean != h->o.face_mean;
+    const bool lv_changed = o->face_mean != h->o.face_mean || o->prolong != h->o.prolong;
     h->o = *o;
-    if (fm_changed) {
-        // the levels carry the face mean, and a captured V-cycle holds them by value
+    if (lv_changed) {
+        // the levels carry the face mean and the prolongation kind, and a captured V-cycle
+        // holds them by value
         FLD_CK(cudaDeviceSynchronize());
         graph_free(h);
-        for (int l = 0; l < h->nlev; ++l) h->lv[l].fm = o->face_mean;
+        for (int l = 0; l < h->nlev; ++l) {
+            h->lv[l].fm = o->face_mean;
+            h->lv[l].pk = o->prolong;
+        }
     }
     return FLD_OK;
 }

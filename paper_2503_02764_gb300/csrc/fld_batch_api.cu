@@ -66,8 +66,9 @@ void batch_free(fld_batch* b) {
 int block_threads(const fld_opts& o) { return o.block ? o.block : 512; }
 
 bool batch_opts_ok(const fld_opts* o) {
-    // the batched kernels use the arithmetic face mean
+    // the batched kernels use the arithmetic face mean and linear prolongation
     return fld::opts_valid(o) && o->face_mean == FLD_FACE_ARITH &&
+           o->prolong == FLD_PROLONG_LINEAR &&
            (o->block == 0 || batch_threads_supported(o->block));
 }
 

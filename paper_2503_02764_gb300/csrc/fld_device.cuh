@@ -75,8 +75,15 @@ struct Interp {
     float wt[2];
 };
 
-__device__ __forceinline__ Interp interp1(int i, int nf, int nc, int lo_bc, int hi_bc) {
+__device__ __forceinline__ Interp interp1(int i, int nf, int nc, int lo_bc, int hi_bc,
+                                          int constant = 0) {
     Interp r;
+    if (constant && nc != nf) {   // piecewise constant: the parent's value
+        r.idx[0] = r.idx[1] = i >> 1;
+        r.wt[0] = 1.f;
+        r.wt[1] = 0.f;
+        return r;
+    }
     if (nc == nf) {           // axis not coarsened
         r.idx[0] = r.idx[1] = i;
         r.wt[0] = 1.f;

@@ -22,6 +22,7 @@ struct Lvl {
     float wf[3];    // the same in FP32 (FP32 kernels never touch FP64 values)
     long long ncell;
     int fm;         // face coefficient from the two cell values: 0 arithmetic, 1 harmonic mean
+    int pk;         // prolongation onto this level: 0 (bi/tri)linear, 1 piecewise constant
 };
 
 // Twice the face coefficient between two cells with cell coefficients a and b: a + b

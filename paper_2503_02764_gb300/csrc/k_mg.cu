@@ -1,12 +1,13 @@
 // Geometric multigrid kernels for the backward-Euler diffusion solve
 //   A x = x - dt div(D grad x) = b
-// on cell-centred finite volumes (face D = mean of the two cell values).
-// Per level the operator is stored as K = dt D / H_x^2 per cell with axis weights
-// w_d = (H_x/H_d)^2:
-//   (A x)_p = x_p + sum_{faces p|q} 0.5 (K_p + K_q) w_d (x_p - x_q) + sum_{Dirichlet} 2 K_p w_d x_p.
+// on cell-centred finite volumes (face D = arithmetic or harmonic mean of the two cell
+// values, the level's fm). Per level the operator is stored as K = dt D / H_x^2 per cell
+// with axis weights w_d = (H_x/H_d)^2:
+//   (A x)_p = x_p + sum_{faces p|q} mean(K_p, K_q) w_d (x_p - x_q) + sum_{Dirichlet} 2 K_p w_d x_p.
 // Coarse levels average K over the (up to 2^d) children and rescale it to the coarse
 // spacing; restriction averages residuals; prolongation is cell-centred linear (weights
-// 3/4 and 1/4 per coarsened axis, tensor product over the axes).
+// 3/4 and 1/4 per coarsened axis, tensor product over the axes) or, with the level's pk,
+// piecewise constant.
 // Every kernel here is templated on the storage/arithmetic type (double or float).
 #include <algorithm>
 
@@ -266,10 +267,10 @@ __global__ void k_prolong(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict_
     for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
         const int j = r % F.n[1], k = r / F.n[1];
         const long long base = (long long)r * F.n[0];
-        const Interp iy = interp1(j, F.n[1], C.n[1], F.bclo[1], F.bchi[1]);
-        const Interp iz = interp1(k, F.n[2], C.n[2], F.bclo[2], F.bchi[2]);
+        const Interp iy = interp1(j, F.n[1], C.n[1], F.bclo[1], F.bchi[1], F.pk);
+        const Interp iz = interp1(k, F.n[2], C.n[2], F.bclo[2], F.bchi[2], F.pk);
         for (int i = threadIdx.x; i < F.n[0]; i += blockDim.x) {
-            const Interp ix = interp1(i, F.n[0], C.n[0], F.bclo[0], F.bchi[0]);
+            const Interp ix = interp1(i, F.n[0], C.n[0], F.bclo[0], F.bchi[0], F.pk);
             T acc = T(0);
 #pragma unroll
             for (int c = 0; c < 2; ++c)
@@ -288,7 +289,7 @@ __global__ void k_prolong(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict_
 
 template <typename T>
 void launch_prolong(const Lvl& F, const Lvl& C, T* xf, const T* xc, int block, cudaStream_t s) {
-    if (transfer3_ok(F, C)) return launch_prolong3<T>(F, C, xf, xc, s);
+    if (transfer3_ok(F, C) && !F.pk) return launch_prolong3<T>(F, C, xf, xc, s);
     k_prolong<T><<<rows_grid(F), block, 0, s>>>(F, C, xf, xc);
 }
 

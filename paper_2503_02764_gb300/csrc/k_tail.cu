@@ -88,9 +88,9 @@ __device__ void tail_prolong(const Lvl& F, const Lvl& C, T* __restrict__ xf,
     for (int p = threadIdx.x; p < (int)F.ncell; p += blockDim.x) {
         int i, j, k;
         decode(F, p, i, j, k);
-        const Interp ix = interp1(i, F.n[0], C.n[0], F.bclo[0], F.bchi[0]);
-        const Interp iy = interp1(j, F.n[1], C.n[1], F.bclo[1], F.bchi[1]);
-        const Interp iz = interp1(k, F.n[2], C.n[2], F.bclo[2], F.bchi[2]);
+        const Interp ix = interp1(i, F.n[0], C.n[0], F.bclo[0], F.bchi[0], F.pk);
+        const Interp iy = interp1(j, F.n[1], C.n[1], F.bclo[1], F.bchi[1], F.pk);
+        const Interp iz = interp1(k, F.n[2], C.n[2], F.bclo[2], F.bchi[2], F.pk);
         T acc = T(0);
 #pragma unroll
         for (int c = 0; c < 2; ++c)

@@ -17,6 +17,7 @@ FLD_OK, FLD_ERR_ARG, FLD_ERR_DOMAIN, FLD_ERR_NOT_CONVERGED, FLD_ERR_TIMEOUT, FLD
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
 DIAG_ENERGY, DIAG_TIMES = 1, 2
 FACE_ARITH, FACE_HARM = 0, 1
+PROLONG_LINEAR, PROLONG_CONSTANT = 0, 1
 LIMITER_LP, LIMITER_DIFFUSION, LIMITER_MINERBO = 0, 1, 2
 OPACITY_CONST, OPACITY_POWER, OPACITY_TABLE = 0, 1, 2
 
@@ -48,7 +49,8 @@ class fld_opts(C.Structure):
                 ("nu1", C.c_int), ("nu2", C.c_int), ("coarse_sweeps", C.c_int),
                 ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
                 ("graph", C.c_int), ("cluster", C.c_int), ("inner", C.c_int),
-                ("direct1d", C.c_int), ("diag", C.c_int), ("face_mean", C.c_int)]
+                ("direct1d", C.c_int), ("diag", C.c_int), ("face_mean", C.c_int),
+                ("prolong", C.c_int)]
 
 
 class fld_stats(C.Structure):
@@ -185,7 +187,7 @@ def make_grid(shape, h, bc):
 
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
               limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1, direct1d=1,
-              diag=0, face_mean=FACE_ARITH):
+              diag=0, face_mean=FACE_ARITH, prolong=PROLONG_LINEAR):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
@@ -197,6 +199,7 @@ def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coars
     o.direct1d = direct1d
     o.diag = diag
     o.face_mean = face_mean
+    o.prolong = prolong
     return o
 
 

@@ -123,20 +123,23 @@ def test_amr_box_checks_without_gpu():
 
 def test_face_mean_and_diag_checks_without_gpu():
     # the harmonic face mean is refused on the host by MIXED_DF handles, the batched step
-    # and the composite grid; unknown face_mean or diag values by every create call
+    # and the composite grid, constant prolongation by the batched step; unknown
+    # face_mean, prolong or diag values by every create call
     from paper_2503_02764_gb300 import fld
     L = fld.lib()
     g = fld.make_grid((16, 16), (1.0, 1.0), ((1, 1), (1, 1)))
     for kw in (dict(precision=fld.PREC_MIXED_DF, face_mean=fld.FACE_HARM),
-               dict(face_mean=2), dict(face_mean=-1), dict(diag=4), dict(diag=-1)):
+               dict(face_mean=2), dict(face_mean=-1), dict(diag=4), dict(diag=-1),
+               dict(prolong=2), dict(prolong=-1)):
         o = fld.make_opts(**kw)
         h = fld.H()
         assert L.fld_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(o)) == \
             fld.FLD_ERR_ARG, kw
-    o = fld.make_opts(face_mean=fld.FACE_HARM)
     arr = (fld.fld_grid * 2)(g, g)
-    b = fld.H()
-    assert L.fld_batch_create(ctypes.byref(b), 2, arr, ctypes.byref(o)) == fld.FLD_ERR_ARG
+    for o in (fld.make_opts(face_mean=fld.FACE_HARM), fld.make_opts(prolong=fld.PROLONG_CONSTANT)):
+        b = fld.H()
+        assert L.fld_batch_create(ctypes.byref(b), 2, arr, ctypes.byref(o)) == fld.FLD_ERR_ARG
+    o = fld.make_opts(face_mean=fld.FACE_HARM)
     a = fld.H()
     assert L.fld_amr_create(ctypes.byref(a), ctypes.byref(g),
                             ctypes.byref(fld.make_patch((3, 3), (9, 9))),

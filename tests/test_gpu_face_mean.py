@@ -117,3 +117,27 @@ def test_switching_the_face_mean_on_a_handle():
         assert st["status"] == 0, st
         ref = O.diffuse(E, D, h, bc, Eb, dt, method="splu", face_mean=name)
         assert maxrel(host(Ed).reshape(shape), ref) < 1e-10, name
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape,h,bc,dt,sigma", CASES[1:])
+def test_constant_prolongation_reaches_the_same_solution(shape, h, bc, dt, sigma, precision):
+    # the prolongation kind changes the convergence rate, never the answer: piecewise
+    # constant prolongation converges to the oracle's solution (arithmetic mean), in no
+    # fewer cycles than the linear one
+    torch = torch_cuda()
+    fld = library()
+    D, E, Eb = _problem(shape, bc, sigma, 23)
+    packed = I.pack_dirichlet(shape, bc, Eb)
+    ref = O.diffuse(E, D, h, bc, Eb, dt, method="splu")
+    cycles = {}
+    for pk in (fld.PROLONG_LINEAR, fld.PROLONG_CONSTANT):
+        hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-12, max_cycles=200,
+                        prolong=pk, smoother=2)
+        Ed = dev(torch, E)
+        st = hd.diffuse(dt, dev(torch, D), dev(torch, packed) if packed.size else None, Ed,
+                        raise_on_error=False)
+        assert st["status"] == 0, (pk, st)
+        assert maxrel(host(Ed).reshape(shape), ref) < (1e-11 if precision == 0 else 1e-10)
+        cycles[pk] = st["cycles"]
+    assert cycles[fld.PROLONG_CONSTANT] >= cycles[fld.PROLONG_LINEAR], cycles
