@@ -208,7 +208,12 @@ class Wave:
     def implicit(self, P, tau, t):
         """The FLD substep over tau on the state P (the stage solve of the IMEX scheme):
         limiter, backward-Euler diffusion, exchange; the exchange's change of T_g goes to
-        the gas energy. Returns the new state, its driven cells at time t."""
+        the gas energy. Returns the new state, its driven cells at time t. Without radiation
+        there is no implicit term: the stage value is the predictor."""
+        if not self.radiation:
+            U = P.copy()
+            self.drive(U, t)
+            return U
         W = primitive(P, self.Bx, self.gamma)
         T = self.T_gas(W)
         D, _, _ = F.limiter(W[ER], W[RHO], T, (self.dx,), self.bcE, self.E_bc, self.c,
@@ -248,7 +253,7 @@ class Wave:
         return Un
 
     def step(self, U, t, dt):
-        if self.scheme == "ars3" and self.radiation:
+        if self.scheme == "ars3":
             return self.step_ars3(U, t, dt)
         U1 = U + dt * self.rhs(U, t)
         self.drive(U1, t + dt)

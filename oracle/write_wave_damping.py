@@ -4,9 +4,10 @@ runs measure for the driven waves of Sect. 4.3.
 TEST INFRASTRUCTURE (part of the CPU oracle): run by hand, it calls only oracle/ (and the
 seeded input recipes). For each case (background of Table 2 or 3, fast or slow wave,
 cells over 40 wavelengths, CFL 0.8, the ARS3 IMEX scheme), the oracle runs the radiative
-problem and the same grid without radiation (the hyperbolic scheme's own damping) until
-the front has travelled `travel` wavelengths, and fits the damping over the wavelengths
-[1, travel - 3); it also stores Im k from the Appendix-B system at the driving frequency
+problem and the same grid without radiation (the hyperbolic scheme's own damping, the same
+ARS3 explicit stages with no implicit term) until the radiative front has travelled
+`travel` wavelengths (t_end, the same for both runs), and fits the damping over the
+wavelengths [1, travel - 3); it also stores Im k from the Appendix-B system at the driving frequency
 and the printed damping per length. The resolution study is the strongly radiative slow
 wave on 800, 1600, 2400 and 3200 cells. The time-step study is the weakly radiative fast
 wave on 1600 cells at CFL 0.8, 0.4 and 0.2: there the stiff gas-radiation exchange makes
@@ -64,7 +65,8 @@ def run_case(args):
     im_k = R.spatial_damping(bg, P.omega, bg["k"]).imag
     return key_of(*args), {
         "case": case, "kind": kind, "n": n, "wavelengths": NW, "cfl": cfl, "scheme": "ars3",
-        "travel": travel, "fit": [1, last], "steps": steps, "steps_ideal": steps_i,
+        "travel": travel, "t_end": t_end, "fit": [1, last], "steps": steps,
+        "steps_ideal": steps_i,
         "k_meas": k_meas, "k_num": k_num, "im_k": im_k,
         "printed": gold["damping_per_length_" + kind], "seconds": time.time() - t0}
 

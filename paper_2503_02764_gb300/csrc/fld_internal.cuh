@@ -271,10 +271,13 @@ void launch_coarse_solve(const Lvl& L, T* x, const T* b, const T* K, int sweeps,
 void launch_resid64(const Lvl& L, const double* x, const double* b, const double* K,
                     float* r32, double* partials, int nblocks, int block, cudaStream_t s);
 void launch_add_correction(long long n, double* x, const float* e, cudaStream_t s);
-// direct solve of a 1D level's system by parallel cyclic reduction (k_tridiag.cu); w holds
-// 10 n + 1 doubles; returns the kernels launched
+// direct solve of a 1D level's system by parallel cyclic reduction (k_tridiag.cu), and one
+// step of iterative refinement of x with it; w holds 12 n + 1 doubles; both return the
+// kernels launched
 int launch_tridiag_solve(const Lvl& L, const double* K, const double* rhs, double* x, double* w,
                          cudaStream_t s);
+int launch_tridiag_refine(const Lvl& L, const double* K, const double* rhs, double* x, double* w,
+                          cudaStream_t s);
 // FP64 residual on 3D levels with each face flux evaluated once (k_resid64.cu): r = b - A x
 // (x + e written to xo first when e is given), r32 its FP32 image (nullable), partial sums
 // of r^2; returns the partials written (<= nblocks). resid64z_ok: the level is 3D and its

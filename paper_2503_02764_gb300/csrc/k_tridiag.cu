@@ -102,12 +102,35 @@ __global__ void k_tri_finish(int n, int two, const double* __restrict__ b,
     }
 }
 
+// r = b - A x in FP64 (the 3-point operator of k_tri_setup, periodic wrap or walls)
+__global__ void k_tri_resid(int n, int lo_bc, int hi_bc, int fm, const double* __restrict__ K,
+                            const double* __restrict__ b, const double* __restrict__ x,
+                            double* __restrict__ r) {
+    const bool per = lo_bc == FLD_BC_PERIODIC;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double Ki = K[i], xi = x[i];
+        double ax = xi;
+        const int il = i > 0 ? i - 1 : (per ? n - 1 : -1);
+        const int ir = i < n - 1 ? i + 1 : (per ? 0 : -1);
+        if (il >= 0) ax = fma(fmean(Ki, K[il], fm), xi - x[il], ax);
+        else if (lo_bc == FLD_BC_DIRICHLET) ax = fma(2.0 * Ki, xi, ax);
+        if (ir >= 0) ax = fma(fmean(Ki, K[ir], fm), xi - x[ir], ax);
+        else if (hi_bc == FLD_BC_DIRICHLET) ax = fma(2.0 * Ki, xi, ax);
+        r[i] = b[i] - ax;
+    }
+}
+
+__global__ void k_tri_add(int n, double* __restrict__ x, const double* __restrict__ d) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+
 int tri_blocks(int n) { return std::max(1, std::min((n + TRI_T - 1) / TRI_T, num_sms() * 8)); }
 
 }  // namespace
 
-// Buffers: w holds 10 n + 1 doubles (two sets of a, b, c, d, e and one scalar). Returns the
-// number of kernels launched.
+// Buffers: w holds 12 n + 1 doubles (two sets of a, b, c, d, e, one scalar, and the residual
+// and correction of launch_tridiag_refine). Returns the number of kernels launched.
 int launch_tridiag_solve(const Lvl& L, const double* K, const double* rhs, double* x, double* w,
                          cudaStream_t s) {
     const int n = L.n[0];
@@ -129,6 +152,22 @@ int launch_tridiag_solve(const Lvl& L, const double* K, const double* rhs, doubl
     }
     k_tri_finish<<<nb, TRI_T, 0, s>>>(n, two, A[cur][1], A[cur][3], A[cur][4], sc, x);
     return launches + 1;
+}
+
+// One step of iterative refinement of x: r = b - A x (FP64), A d = r by the same reduction,
+// x += d. The reduction's rounding grows with the coupling (dt D / h^2 far above 1 on fine
+// 1D grids) and with the Sherman-Morrison combination of a periodic grid; a step brings
+// the residual back to the rounding of the operator. Returns the kernels launched.
+int launch_tridiag_refine(const Lvl& L, const double* K, const double* rhs, double* x, double* w,
+                          cudaStream_t s) {
+    const int n = L.n[0];
+    double* r = w + 10LL * n + 1;
+    double* d = r + n;
+    const int nb = tri_blocks(n);
+    k_tri_resid<<<nb, TRI_T, 0, s>>>(n, L.bclo[0], L.bchi[0], L.fm, K, rhs, x, r);
+    const int nl = launch_tridiag_solve(L, K, r, d, w, s);
+    k_tri_add<<<nb, TRI_T, 0, s>>>(n, x, d);
+    return nl + 2;
 }
 
 }  // namespace fld

@@ -37,7 +37,7 @@ def _gpu_damping(c, radiation):
     orc = R.Wave(P, cfl=c["cfl"], scheme="ars3")
     gpu = fld.Wave1D(P, scheme=1, **OPTS)
     Ud = dev(torch_cuda(), orc.initial())
-    t_end = c["travel"] * P.lam / P.phase_speed
+    t_end = c["t_end"]          # the radiative front's travel time, for both runs
     t, n = 0.0, 0
     while t < t_end * (1.0 - 1e-12):
         dt = min(gpu.max_dt(Ud, c["cfl"]), t_end - t)

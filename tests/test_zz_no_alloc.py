@@ -39,7 +39,7 @@ def test_static_solve_matches_handle_solve_twice(precision, tol):
     for shape, h, bc, dt in cases:
         D, E, packed = _case(shape, bc, sum(shape))
         opts = fld.make_opts(precision=precision, tol=1e-13, max_cycles=80)
-        hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-13, max_cycles=80)
+        hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-13, max_cycles=80, direct1d=0)
         Eref = dev(torch, E)
         ebc = dev(torch, packed) if packed.size else None
         ref = hd.diffuse(dt, dev(torch, D), ebc, Eref, raise_on_error=False)
@@ -68,7 +68,7 @@ def test_static_solve_at_the_cell_limit_allocates_nothing(precision, tol):
     D, E, packed = _case(shape, bc, 5)
     dt = 10.0 / n ** 2
     opts = fld.make_opts(precision=precision, tol=1e-13, max_cycles=80)
-    hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-13, max_cycles=80)
+    hd = fld.Handle(shape, h, bc, precision=precision, tol=1e-13, max_cycles=80, direct1d=0)
     Dd, ebc = dev(torch, D), dev(torch, packed)
     Eref = dev(torch, E)
     ref = hd.diffuse(dt, Dd, ebc, Eref, raise_on_error=False)
