@@ -367,6 +367,9 @@ DTYPE = {
                 "exponent window)",
     "fp64": "f64 V-cycles; f64 coarsest solve; f64 limiter; f64 exchange (f32 Newton seed, "
             "f64 Newton polish)",
+    "mixed_dflim": "as mixed (f32 V-cycles inside f64 iterative refinement, f64 coarsest solve, "
+                   "f64 exchange), with the double-f32 (48-bit) limiter: gradient from f32 "
+                   "pairs of E, R, lambda, D",
 }
 BATCH_DTYPE = ("f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
                "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
@@ -691,6 +694,8 @@ def main():
                          "half sweeps, 2 single-pass z-marching sweep")
     ap.add_argument("--nu1", type=int, default=-1, help="pre-smoothing sweeps (-1: tuned)")
     ap.add_argument("--nu2", type=int, default=-1, help="post-smoothing sweeps (-1: tuned)")
+    ap.add_argument("--prolong", type=int, default=-1,
+                    help="prolongation: -1 the tuned choice (else linear); 0 linear, 1 constant")
     ap.add_argument("--inner", type=int, default=-1,
                     help="FP32 V-cycles per refinement step (-1: tuned)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the mixed-vs-FP64 solve timing")
@@ -729,7 +734,7 @@ def main():
 
     def options(pr):
         o, t = autotune.grid_options(P, pr)
-        for k in ("smoother", "nu1", "nu2", "inner"):     # explicit choices override the tuner
+        for k in ("smoother", "nu1", "nu2", "inner", "prolong"):   # explicit choices override the tuner
             if getattr(args, k) >= 0:
                 o[k] = getattr(args, k)
                 t = False
@@ -882,11 +887,13 @@ def main():
     # tuned options, from the same state (rank 0)
     variants = {}
     if rank == 0 and not args.no_variants:
-        for name in ("mixed_df", "fp64", "mixed"):
+        for name in ("mixed_df", "fp64", "mixed", "mixed_dflim"):
             if name == args.precision:
                 continue
-            o, t = options(PREC[name])
-            hv = fld.Handle(P.shape, P.h, P.bc, precision=PREC[name], tol=1e-10, max_cycles=50, **o)
+            base = "mixed" if name == "mixed_dflim" else name
+            o, t = options(PREC[base])
+            o = dict(o, limiter_df=1) if name == "mixed_dflim" else o
+            hv = fld.Handle(P.shape, P.h, P.bc, precision=PREC[base], tol=1e-10, max_cycles=50, **o)
             Tv, Ev = T_start.clone(), E_start.clone()
             nst = max(5, args.steps // 4) if name == "fp64" else args.steps
             msv, cyc, stv = step_series(hv, consts, op, P, rho, Tv, Ev, ebc, nst, 2, torch)
@@ -948,7 +955,7 @@ def main():
             "config": {"workload": workload_name(args.n),
                        "cells": P.ncells, "precision": args.precision, "tol": 1e-10,
                        "nu1": gkw["nu1"], "nu2": gkw["nu2"], "smoother": gkw["smoother"],
-                       "inner": gkw.get("inner", 1), "graph": 1,
+                       "inner": gkw.get("inner", 1), "prolong": gkw.get("prolong", 0), "graph": 1,
                        "autotuned": bool(tuned),
                        "l2": "inputs larger than L2 (fields %.0f MB + workspace)" %
                              (3 * P.ncells * 8 / 1e6),

@@ -172,6 +172,11 @@ typedef struct {
                            choice changes the convergence rate, not the solution.
                            CONSTANT runs the generic prolongation kernel; the batched
                            step takes LINEAR only                                      */
+    int limiter_df;     /* 1: the limiter (fld_limiter, and the limiter of fld_step) runs
+                           in double-FP32 as in MIXED_DF (gradient from FP32 pairs of E,
+                           R, lambda, D; relative error ~1e-14) whatever the precision
+                           mode, the solve and the exchange keeping theirs; 0 (default):
+                           the limiter of the precision mode                           */
 } fld_opts;
 
 enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };

@@ -66,7 +66,7 @@ def grid_options(problem, precision, gpu=None):
         return dict(DEFAULT_GRID), False
     b = c["best"]
     return {"nu1": b["nu1"], "nu2": b["nu2"], "smoother": b["smoother"],
-            "inner": b.get("inner", 1)}, True
+            "inner": b.get("inner", 1), "prolong": b.get("prolong", 0)}, True
 
 
 def batch_options(problems, gpu=None):

@@ -205,7 +205,8 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->diag >= 0 && o->diag <= (FLD_DIAG_ENERGY | FLD_DIAG_TIMES)) &&
            (o->face_mean == FLD_FACE_ARITH ||
             (o->face_mean == FLD_FACE_HARM && o->precision != FLD_PREC_MIXED_DF)) &&
-           (o->prolong == FLD_PROLONG_LINEAR || o->prolong == FLD_PROLONG_CONSTANT);
+           (o->prolong == FLD_PROLONG_LINEAR || o->prolong == FLD_PROLONG_CONSTANT) &&
+           (o->limiter_df == 0 || o->limiter_df == 1);
 }
 
 namespace {
@@ -650,10 +651,10 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         // the first correction's right-hand side: the FP32 residual of E^n (the refinement
         // starts from an FP32 solve); every later residual, which decides convergence, is
         // FP64
-        const int nparts = (int)std::min<long long>((long long)L0.n[1] * L0.n[2], h->norm_blocks);
+        int nparts = 0;
         run(h, "resid32", 0, L0.ncell, s, [&] {
-            launch_resid32_init(L0, E, h->d64[0].b, h->d32[0].K, h->d32[0].b, h->partials,
-                                h->norm_blocks, s);
+            nparts = launch_resid32_init(L0, E, h->d64[0].b, h->d32[0].K, h->d32[0].b,
+                                         h->partials, h->norm_blocks, s);
         });
         run(h, "finish_sum", 0, nparts, s,
             [&] { launch_finish_sum(h->partials, nparts, &h->scal->sum, s); });
@@ -895,9 +896,10 @@ void fill_diag(fld_handle* h, fld_stats* st, int phases) {
 fld_status limiter_impl(fld_handle* h, const fld_consts* k, const fld_opacity* op, const double* E,
                         const double* rho, const double* T, const double* E_bc, double* D,
                         double* lambda, double* kr, cudaStream_t s) {
-    // double-FP32 mode: E split once into FP32 pairs (the level-0 FP32 buffers are free
-    // until the solve), so the limiter forms the gradient without FP64 arithmetic
-    const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF;
+    // double-FP32 limiter (MIXED_DF, or the limiter_df option): E split once into FP32
+    // pairs (the level-0 FP32 buffers are free until the solve), so the limiter forms the
+    // gradient without FP64 arithmetic
+    const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF || h->o.limiter_df;
     const bool split = dfmode && h->o.limiter != FLD_LIMITER_DIFFUSION;
     float* Eh = split ? h->d32[0].x : nullptr;
     float* El = split ? h->d32[0].tmp : nullptr;

@@ -17,11 +17,13 @@ __device__ __forceinline__ void decode(const Lvl& L, long long p, int& i, int& j
 
 // Off-diagonal sum and diagonal excess of the level operator at cell p:
 //   sw  = sum of face weights (+ 2 K_p w_d per Dirichlet face),  acc = sum w_f x_q,
-// so (A x)_p = (1 + sw) x_p - acc.
-template <typename T>
+// so (A x)_p = (1 + sw) x_p - acc. FM >= 0 fixes the face mean at compile time (the
+// level's fm otherwise).
+template <typename T, int FM = -1>
 __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
                                         const T* __restrict__ x, int i, int j, int k, long long p64,
                                         T& sw, T& acc) {
+    const int fm = FM < 0 ? L.fm : FM;
     // cell indices fit in 32 bits (the handle rejects grids of 2^31 cells or more)
     const int p = (int)p64;
     const T Kc = K[p];
@@ -39,7 +41,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
             if (c[d] > 0) q = p - stride;
             else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
             if (q >= 0) {
-                const T w = fmean(Kc, K[q], L.fm) * wd;
+                const T w = fmean(Kc, K[q], fm) * wd;
                 sw += w;
                 acc += w * x[q];
             } else if (L.bclo[d] == FLD_BC_DIRICHLET) {
@@ -50,7 +52,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
             if (c[d] < n - 1) q = p + stride;
             else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
             if (q >= 0) {
-                const T w = fmean(Kc, K[q], L.fm) * wd;
+                const T w = fmean(Kc, K[q], fm) * wd;
                 sw += w;
                 acc += w * x[q];
             } else if (L.bchi[d] == FLD_BC_DIRICHLET) {

@@ -284,10 +284,10 @@ int launch_tridiag_refine(const Lvl& L, const double* K, const double* rhs, doub
 // tiles fit the partial-sum slots.
 bool resid64z_ok(const Lvl& L, int nblocks);
 // FP32 residual of the FP64 iterate (the mixed refinement's first correction): r32 and
-// partial sums of r^2; one block per row, at most nblocks (returns nothing: nblocks or the
-// row count partials are written, the smaller)
-void launch_resid32_init(const Lvl& L, const double* x, const double* b, const float* K,
-                         float* r32, double* partials, int nblocks, cudaStream_t s);
+// partial sums of r^2, z-marching tiles on 3D levels (where resid64z_ok holds), else one
+// block per row; returns the number of partial sums written (<= nblocks)
+int launch_resid32_init(const Lvl& L, const double* x, const double* b, const float* K,
+                        float* r32, double* partials, int nblocks, cudaStream_t s);
 int launch_resid64z(const Lvl& L, const double* x, const float* e, double* xo, const double* b,
                     const double* K, float* r32, double* partials, int nblocks, cudaStream_t s);
 

@@ -83,6 +83,7 @@ void launch_prep_level0(const Lvl& L, double kscale, const double* D, const doub
 template <typename T>
 __global__ void k_restrict_K(Lvl F, Lvl C, double scale, const T* __restrict__ Kf,
                              T* __restrict__ Kc) {
+    const T sc = (T)scale;
     for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < C.ncell;
          P += (long long)gridDim.x * blockDim.x) {
         int c[3];
@@ -96,15 +97,18 @@ __global__ void k_restrict_K(Lvl F, Lvl C, double scale, const T* __restrict__ K
                 lo[d] = hi[d] = c[d];
             }
         }
-        double s = 0.0;
+        // the mean in the level's own type (the FP32 pyramid preconditions only; the FP64
+        // one keeps FP64 sums); the child count is a power of two, so its reciprocal is exact
+        T s = T(0);
         int cnt = 0;
         for (int k = lo[2]; k <= hi[2]; ++k)
             for (int j = lo[1]; j <= hi[1]; ++j)
                 for (int i = lo[0]; i <= hi[0]; ++i) {
-                    s += (double)Kf[((long long)k * F.n[1] + j) * F.n[0] + i];
+                    s += Kf[((long long)k * F.n[1] + j) * F.n[0] + i];
                     ++cnt;
                 }
-        Kc[P] = (T)(scale * s / cnt);
+        const T inv = cnt == 8 ? T(0.125) : cnt == 4 ? T(0.25) : cnt == 2 ? T(0.5) : T(1);
+        Kc[P] = (sc * inv) * s;
     }
 }
 

@@ -332,13 +332,171 @@ __global__ void k_resid32_init(Lvl L, const double* __restrict__ x, const double
     if (threadIdx.x == 0) partials[blockIdx.x] = acc2;
 }
 
+// The same residual on 3D levels, marching along z like k_resid64z: a block owns a
+// RZ_TX x RZ_TY tile, the FP32 images of x and K of the current plane (and the one-cell
+// ring: periodic neighbours, or the wall ghosts x = 0, K = 3 K_wall for Dirichlet and
+// -K_wall for Neumann) sit in shared memory, the planes below and above in registers. Each
+// cell evaluates its seven-point stencil in FP32; x and b are read once as FP64 and
+// converted in integer arithmetic.
+__global__ void __launch_bounds__(RZ_NT)
+k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
+           const float* __restrict__ K, float* __restrict__ r32, double* __restrict__ partials,
+           int cz) {
+    __shared__ float XS[(RZ_TY + 2) * RZ_PW], KS[(RZ_TY + 2) * RZ_PW];
+    __shared__ double sh[32];
+
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int tilesx = (nx + RZ_TX - 1) / RZ_TX, tilesy = (ny + RZ_TY - 1) / RZ_TY;
+    int bid = blockIdx.x;
+    const int tx0 = (bid % tilesx) * RZ_TX;
+    bid /= tilesx;
+    const int ty0 = (bid % tilesy) * RZ_TY;
+    bid /= tilesy;
+    const int z0 = bid * cz, z1 = min(z0 + cz, nz);
+    const bool xper = L.bclo[0] == FLD_BC_PERIODIC, yper = L.bclo[1] == FLD_BC_PERIODIC;
+    const bool zper = L.bclo[2] == FLD_BC_PERIODIC;
+    const long long plane = (long long)nx * ny;
+    const float hx = 0.5f * L.wf[0], hy = 0.5f * L.wf[1], hz = 0.5f * L.wf[2];
+
+    const int tid = threadIdx.x;
+    const int lx = tid % RZ_TX, ly = tid / RZ_TX;
+    const int ax = min(RZ_TX, nx - tx0), ay = min(RZ_TY, ny - ty0);
+    const bool act = lx < ax && ly < ay;
+    const long long own = act ? (long long)(ty0 + ly) * nx + tx0 + lx : 0;
+    const int so = (ly + 1) * RZ_PW + lx + 1;
+
+    int rso = -1;
+    long long rsrc = 0;
+    bool rghost = false;
+    float rfac = 0.f;
+    {
+        int qx = 0, qy = 0;
+        bool has = true;
+        if (tid < ay) { qx = -1; qy = tid; }
+        else if (tid < 2 * ay) { qx = ax; qy = tid - ay; }
+        else if (tid < 2 * ay + ax) { qx = tid - 2 * ay; qy = -1; }
+        else if (tid < 2 * ay + 2 * ax) { qx = tid - 2 * ay - ax; qy = ay; }
+        else has = false;
+        if (has) {
+            rso = (qy + 1) * RZ_PW + qx + 1;
+            const int gx = rz_axis(tx0 + qx, nx, xper), gy = rz_axis(ty0 + qy, ny, yper);
+            if (gx >= 0 && gy >= 0) {
+                rsrc = (long long)gy * nx + gx;
+            } else {
+                rghost = true;
+                const int wx = qx < 0 ? 0 : (qx >= ax ? ax - 1 : qx);
+                const int wy = qy < 0 ? 0 : (qy >= ay ? ay - 1 : qy);
+                rsrc = (long long)(ty0 + wy) * nx + tx0 + wx;
+                const int bc = gx < 0 ? (qx < 0 ? L.bclo[0] : L.bchi[0])
+                                      : (qy < 0 ? L.bclo[1] : L.bchi[1]);
+                rfac = (float)rz_factor(bc);
+            }
+        }
+    }
+    // the own column at plane m: the FP32 images, or the z-wall ghost from the wall cell's K
+    auto column = [&](int m, float kwall, float& xv, float& kv) {
+        const int gz = rz_axis(m, nz, zper);
+        if (gz >= 0) {
+            const long long q = gz * plane + own;
+            xv = f32_of(x[q]);
+            kv = K[q];
+        } else {
+            xv = 0.f;
+            kv = kwall * (float)rz_factor(m < 0 ? L.bclo[2] : L.bchi[2]);
+        }
+    };
+    // the words plane k needs besides the planes below: the own column at k + 1, b at k and
+    // the ring at k, loaded one plane ahead (while plane k - 1 is computed)
+    struct Raw {
+        double x, b, rx;
+        float k, rk;
+    };
+    auto fetch = [&](int k, Raw& R) {
+        const int g1 = rz_axis(k + 1, nz, zper);
+        if (act) {
+            if (g1 >= 0) {
+                R.x = x[g1 * plane + own];
+                R.k = K[g1 * plane + own];
+            }
+            R.b = b[(long long)k * plane + own];
+        }
+        if (rso >= 0) {
+            R.rk = K[(long long)k * plane + rsrc];
+            if (!rghost) R.rx = x[(long long)k * plane + rsrc];
+        }
+    };
+
+    double acc2 = 0.0;
+    float xm = 0.f, km = 0.f, xc = 0.f, kc = 0.f, xp = 0.f, kp = 0.f;
+    if (act) {
+        column(z0, 0.f, xc, kc);
+        column(z0 - 1, kc, xm, km);
+    }
+    Raw cur = {}, nxt = {};
+    fetch(z0, cur);
+    for (int k = z0; k < z1; ++k) {
+        const long long pk = (long long)k * plane;
+        if (k + 1 < z1) fetch(k + 1, nxt);
+        float bk = 0.f;
+        if (act) {
+            if (rz_axis(k + 1, nz, zper) >= 0) {
+                xp = f32_of(cur.x);
+                kp = cur.k;
+            } else {
+                xp = 0.f;
+                kp = kc * (float)rz_factor(L.bchi[2]);
+            }
+            bk = f32_of(cur.b);
+            XS[so] = xc;
+            KS[so] = kc;
+        }
+        if (rso >= 0) {
+            XS[rso] = rghost ? 0.f : f32_of(cur.rx);
+            KS[rso] = rghost ? rfac * cur.rk : cur.rk;
+        }
+        __syncthreads();
+        if (act) {
+            float sx = (kc + KS[so - 1]) * (xc - XS[so - 1]);
+            sx = fmaf(kc + KS[so + 1], xc - XS[so + 1], sx);
+            float sy = (kc + KS[so - RZ_PW]) * (xc - XS[so - RZ_PW]);
+            sy = fmaf(kc + KS[so + RZ_PW], xc - XS[so + RZ_PW], sy);
+            float sz = (kc + km) * (xc - xm);
+            sz = fmaf(kc + kp, xc - xp, sz);
+            float rv = fmaf(-hx, sx, bk - xc);
+            rv = fmaf(-hy, sy, rv);
+            rv = fmaf(-hz, sz, rv);
+            r32[pk + own] = rv;
+            acc2 = fma((double)rv, (double)rv, acc2);
+        }
+        __syncthreads();
+        xm = xc;
+        km = kc;
+        xc = xp;
+        kc = kp;
+        cur = nxt;
+    }
+    const double a2 = block_sum(acc2, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a2;
+}
+
 }  // namespace
 
-void launch_resid32_init(const Lvl& L, const double* x, const double* b, const float* K,
-                         float* r32, double* partials, int nblocks, cudaStream_t s) {
+// Returns the number of partial sums written (<= nblocks).
+int launch_resid32_init(const Lvl& L, const double* x, const double* b, const float* K,
+                        float* r32, double* partials, int nblocks, cudaStream_t s) {
+    if (resid64z_ok(L, nblocks)) {
+        const int tiles = ((L.n[0] + RZ_TX - 1) / RZ_TX) * ((L.n[1] + RZ_TY - 1) / RZ_TY);
+        // chunks of at least 16 planes, as many as the partial sums allow
+        int nch = std::max(1, std::min(nblocks / tiles, (L.n[2] + 15) / 16));
+        const int cz = (L.n[2] + nch - 1) / nch;
+        nch = (L.n[2] + cz - 1) / cz;
+        k_resid32z<<<tiles * nch, RZ_NT, 0, s>>>(L, x, b, K, r32, partials, cz);
+        return tiles * nch;
+    }
     const int nb = (int)std::max<long long>(1, std::min<long long>((long long)L.n[1] * L.n[2],
                                                                       nblocks));
     k_resid32_init<<<nb, 256, 0, s>>>(L, x, b, K, r32, partials);
+    return nb;
 }
 
 }  // namespace fld

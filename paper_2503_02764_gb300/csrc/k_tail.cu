@@ -22,7 +22,7 @@ namespace {
 
 constexpr int TAIL_THREADS = 1024;
 
-template <typename T>
+template <typename T, int FM>
 __device__ void tail_colour(const Lvl& L, int color, const T* __restrict__ xin,
                             T* __restrict__ xout, const T* __restrict__ b,
                             const T* __restrict__ K) {
@@ -34,23 +34,23 @@ __device__ void tail_colour(const Lvl& L, int color, const T* __restrict__ xin,
             continue;
         }
         T sw, acc;
-        stencil<T>(L, K, xin, i, j, k, p, sw, acc);
+        stencil<T, FM>(L, K, xin, i, j, k, p, sw, acc);
         xout[p] = div_fast<T>(b[p] + acc, T(1) + sw);
     }
 }
 
-template <typename T>
+template <typename T, int FM>
 __device__ void tail_smooth(const Lvl& L, int n, T* x, T* tmp, const T* b, const T* K) {
     for (int s = 0; s < n; ++s) {
-        tail_colour<T>(L, 0, x, tmp, b, K);
+        tail_colour<T, FM>(L, 0, x, tmp, b, K);
         __syncthreads();
-        tail_colour<T>(L, 1, tmp, x, b, K);
+        tail_colour<T, FM>(L, 1, tmp, x, b, K);
         __syncthreads();
     }
 }
 
 // coarse b = mean over the children of the fine residual b - A x
-template <typename T>
+template <typename T, int FM>
 __device__ void tail_restrict(const Lvl& F, const Lvl& C, const T* __restrict__ x,
                               const T* __restrict__ b, const T* __restrict__ K,
                               T* __restrict__ bc) {
@@ -73,7 +73,7 @@ __device__ void tail_restrict(const Lvl& F, const Lvl& C, const T* __restrict__ 
                 for (int i = lo[0]; i <= hi[0]; ++i) {
                     const long long p = ((long long)k * F.n[1] + j) * F.n[0] + i;
                     T sw, acc;
-                    stencil<T>(F, K, x, i, j, k, p, sw, acc);
+                    stencil<T, FM>(F, K, x, i, j, k, p, sw, acc);
                     s += b[p] - (T(1) + sw) * x[p] + acc;
                     ++cnt;
                 }
@@ -106,7 +106,7 @@ __device__ void tail_prolong(const Lvl& F, const Lvl& C, T* __restrict__ xf,
 }
 
 // exact solve of the coarsest level (n <= TAIL_MAX_DENSE) by Gauss-Jordan in FP64
-template <typename T>
+template <typename T, int FM>
 __device__ void tail_dense(const Lvl& L, T* __restrict__ x, const T* __restrict__ b,
                            const T* __restrict__ K, double (*A)[TAIL_MAX_DENSE + 1]) {
     const int n = (int)L.ncell;
@@ -133,7 +133,7 @@ __device__ void tail_dense(const Lvl& L, T* __restrict__ x, const T* __restrict_
                     else if (kind == FLD_BC_PERIODIC) q = r - (nd - 1) * stride;
                 }
                 if (q >= 0) {
-                    const double w = fmean(kc, (double)K[q], L.fm) * wd;
+                    const double w = fmean(kc, (double)K[q], FM) * wd;
                     diag += w;
                     A[r][q] -= w;
                 } else if (kind == FLD_BC_DIRICHLET) {
@@ -161,7 +161,8 @@ __device__ void tail_dense(const Lvl& L, T* __restrict__ x, const T* __restrict_
 // All tail levels live in shared memory for the whole launch: the first level's x and b
 // and every level's K are read once, the first level's x written back once; every phase
 // in between touches shared memory only.
-template <typename T>
+// FM: the levels' face mean (0 arithmetic, 1 harmonic), fixed per instantiation
+template <typename T, int FM>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailLevels<T> t) {
     __shared__ double A[TAIL_MAX_DENSE][TAIL_MAX_DENSE + 1];
     extern __shared__ __align__(16) unsigned char tail_smem[];
@@ -189,17 +190,17 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(TailLevels<T> t) {
     const int last = t.n - 1;
     // down: pre-smooth, restrict the residual, clear the coarse iterate
     for (int l = 0; l < last; ++l) {
-        tail_smooth<T>(t.L[l], t.nu1, xs[l], ts[l], bs[l], Ks[l]);
-        tail_restrict<T>(t.L[l], t.L[l + 1], xs[l], bs[l], Ks[l], bs[l + 1]);
+        tail_smooth<T, FM>(t.L[l], t.nu1, xs[l], ts[l], bs[l], Ks[l]);
+        tail_restrict<T, FM>(t.L[l], t.L[l + 1], xs[l], bs[l], Ks[l], bs[l + 1]);
         for (int p = threadIdx.x; p < (int)t.L[l + 1].ncell; p += blockDim.x) xs[l + 1][p] = T(0);
         __syncthreads();
     }
-    tail_dense<T>(t.L[last], xs[last], bs[last], Ks[last], A);
+    tail_dense<T, FM>(t.L[last], xs[last], bs[last], Ks[last], A);
     // up: prolong the correction, post-smooth
     for (int l = last - 1; l >= 0; --l) {
         tail_prolong<T>(t.L[l], t.L[l + 1], xs[l], xs[l + 1]);
         __syncthreads();
-        tail_smooth<T>(t.L[l], t.nu2, xs[l], ts[l], bs[l], Ks[l]);
+        tail_smooth<T, FM>(t.L[l], t.nu2, xs[l], ts[l], bs[l], Ks[l]);
     }
     for (int p = threadIdx.x; p < (int)t.L[0].ncell; p += blockDim.x) t.x[0][p] = xs[0][p];
 }
@@ -215,7 +216,11 @@ size_t tail_smem_bytes(const Lvl* lv, int n) {
 
 template <typename T>
 void launch_vcycle_tail(const TailLevels<T>& t, cudaStream_t s) {
-    k_vcycle_tail<T><<<1, TAIL_THREADS, tail_smem_bytes<T>(t.L, t.n), s>>>(t);
+    const size_t sm = tail_smem_bytes<T>(t.L, t.n);
+    if (t.L[0].fm)
+        k_vcycle_tail<T, 1><<<1, TAIL_THREADS, sm, s>>>(t);
+    else
+        k_vcycle_tail<T, 0><<<1, TAIL_THREADS, sm, s>>>(t);
 }
 
 // Opt the tail kernels into TAIL_SMEM_MAX bytes of dynamic shared memory, once per device
@@ -232,9 +237,13 @@ void prepare_vcycle_tail() {
     }
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev].load()) return;
-    cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_vcycle_tail<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)TAIL_SMEM_MAX);
-    cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_vcycle_tail<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TAIL_SMEM_MAX);
+    cudaFuncSetAttribute(k_vcycle_tail<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TAIL_SMEM_MAX);
+    cudaFuncSetAttribute(k_vcycle_tail<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)TAIL_SMEM_MAX);
     done[dev].store(true);
 }

@@ -82,10 +82,10 @@ def test_grid_options_prefer_the_precision_entry(monkeypatch):
     A._store(A.signature("grid", [P]), {"best": {"nu1": 1, "nu2": 1, "smoother": 2,
                                                  "inner": 3}}, "GPU-A")
     opts, tuned = A.grid_options(P, 1, gpu="GPU-A")
-    assert tuned and opts == {"nu1": 1, "nu2": 1, "smoother": 2, "inner": 3}
+    assert tuned and opts == {"nu1": 1, "nu2": 1, "smoother": 2, "inner": 3, "prolong": 0}
     A._store(A.signature("grid", [P], 1), {"best": {"nu1": 2, "nu2": 1, "smoother": 0,
-                                                    "inner": 2}}, "GPU-A")
+                                                    "inner": 2, "prolong": 1}}, "GPU-A")
     assert A.grid_options(P, 1, gpu="GPU-A")[0] == {"nu1": 2, "nu2": 1, "smoother": 0,
-                                                   "inner": 2}
+                                                   "inner": 2, "prolong": 1}
     assert A.grid_options(P, 2, gpu="GPU-A")[0]["inner"] == 3
     assert A.batch_options([P], gpu="GPU-A") is None

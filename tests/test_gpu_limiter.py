@@ -33,16 +33,17 @@ def _fields(shape, bc, seed):
     return E, rho, T, Eb
 
 
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision,limiter_df", [(0, 0), (2, 0), (1, 1)])
 @pytest.mark.parametrize("shape,h,bc", CASES)
 @pytest.mark.parametrize("op", [(0, 2.0, 0.0, 0.0), (1, 5.0, 1.0, -3.5)])
-def test_limiter_matches_oracle(shape, h, bc, op, precision):
-    # precision 2 (MIXED_DF) runs the double-FP32 limiter, the others the FP64 one
+def test_limiter_matches_oracle(shape, h, bc, op, precision, limiter_df):
+    # precision 2 (MIXED_DF) and the limiter_df option run the double-FP32 limiter, the
+    # others the FP64 one
     torch = torch_cuda()
     fld = library()
     E, rho, T, Eb = _fields(shape, bc, len(shape) * 100 + shape[-1])
     for mode in (0, 1, 2):
-        hd = fld.Handle(shape, h, bc, limiter=mode, precision=precision)
+        hd = fld.Handle(shape, h, bc, limiter=mode, precision=precision, limiter_df=limiter_df)
         D = torch.empty(E.size, dtype=torch.float64, device="cuda")
         lam = torch.empty_like(D)
         packed = I.pack_dirichlet(shape, bc, Eb)
@@ -51,7 +52,7 @@ def test_limiter_matches_oracle(shape, h, bc, op, precision):
         assert hd.status() == 0
         Do, lo, _ = O.limiter(E, rho, T, h, bc, Eb, 3.0, op, mode)
         # FP64: rounding-level; double-FP32 (48-bit): a few units of 2^-48
-        tol = 1e-13 if precision == 0 else 1e-12
+        tol = 1e-13 if precision == 0 and not limiter_df else 1e-12
         assert np.max(np.abs(host(D).reshape(shape) / Do - 1)) < tol
         assert np.max(np.abs(host(lam).reshape(shape) / lo - 1)) < tol
 

@@ -11,12 +11,14 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("cfg", [1, 2, 3, 5])
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10), (2, 1e-10)])
-def test_step_matches_oracle(cfg, precision, tol):
+@pytest.mark.parametrize("precision,tol,limiter_df", [(0, 1e-12, 0), (1, 1e-10, 0), (2, 1e-10, 0),
+                                                      (1, 1e-10, 1)])
+def test_step_matches_oracle(cfg, precision, tol, limiter_df):
     torch = torch_cuda()
     fld = library()
     P = I.make_config(cfg, small=True)
-    hd = handle_for(fld, P, precision=precision, tol=1e-14, max_cycles=100)
+    hd = handle_for(fld, P, precision=precision, tol=1e-14, max_cycles=100,
+                    limiter_df=limiter_df)
     Td, Ed, rd = dev(torch, P.T), dev(torch, P.E), dev(torch, P.rho)
     ebc = ebc_dev(torch, P)
     T, E = P.T.copy(), P.E.copy()
