@@ -300,7 +300,11 @@ __device__ __forceinline__ bool limiter_cell(const Lvl& L, const double* ih,
     double lm = 1.0 / 3.0;
     if (mode != FLD_LIMITER_DIFFUSION) {
         double g2 = 0.0;
-        for (int d = 0; d < L.ndim; ++d) {
+        // unrolled over the three axes, so that every index into the level and the
+        // spacings is a constant (no local-memory copy of them)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= L.ndim) break;
             const double em2 = fetch_E(L, E, Ebc, bo, i, j, k, d, -2);
             const double em1 = fetch_E(L, E, Ebc, bo, i, j, k, d, -1);
             const double ep1 = fetch_E(L, E, Ebc, bo, i, j, k, d, 1);

@@ -22,8 +22,9 @@ namespace fld {
 // Newton iteration instead.
 
 // kr (nullable): kappa rho of every cell, frozen at the step's start by the limiter of the
-// same substep; without it kappa is evaluated from (rho, T).
-__global__ void k_exchange(long long n, const double* __restrict__ rho, double* __restrict__ T,
+// same substep; without it kappa is evaluated from (rho, T). DF as for k_limiter.
+template <bool DF>
+__global__ void __launch_bounds__(256, DF ? 5 : 6) k_exchange(long long n, const double* __restrict__ rho, double* __restrict__ T,
                            double* __restrict__ E, const double* __restrict__ kr, Opacity op,
                            double dtc, double a_r, double cv, int use_df, DfConst K,
                            unsigned* err, double one) {
@@ -36,7 +37,7 @@ __global__ void k_exchange(long long n, const double* __restrict__ rho, double* 
             atomicOr(err, ERRBIT_DOMAIN);
             continue;
         }
-        if (use_df && exchange_cell_df(r, t, er, op, K, kri)) {
+        if (DF && use_df && exchange_cell_df(r, t, er, op, K, kri)) {
             T[i] = t;
             E[i] = er;
             continue;
@@ -76,8 +77,12 @@ void launch_exchange(long long n, const double* rho, double* T, double* E, Opaci
     long long nb = (n + block - 1) / block;
     if (nb > num_sms() * 32) nb = num_sms() * 32;
     const DfConst K = make_dfconst(0.0, op.kappa0, dtc, a_r, cv);
-    k_exchange<<<(int)nb, block, 0, s>>>(n, rho, T, E, kr, op, dtc, a_r, cv, use_df, K, err,
-                                         1.0);
+    if (use_df)
+        k_exchange<true><<<(int)nb, block, 0, s>>>(n, rho, T, E, kr, op, dtc, a_r, cv, use_df, K,
+                                                   err, 1.0);
+    else
+        k_exchange<false><<<(int)nb, block, 0, s>>>(n, rho, T, E, kr, op, dtc, a_r, cv, use_df, K,
+                                                    err, 1.0);
 }
 
 // ----------------------------------------------------------------- limiter
@@ -93,7 +98,10 @@ __global__ void k_split_df(long long n, const double* __restrict__ v, float* __r
 }
 
 // kr (nullable): receives kappa rho of every cell, for the exchange of the same substep.
-__global__ void __launch_bounds__(256, 5) k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
+// DF: the double-FP32 cell routine first (FP64 for the cells it declines); the FP64-only
+// instantiation carries none of its registers.
+template <bool DF>
+__global__ void __launch_bounds__(256, DF ? 5 : 6) k_limiter(Lvl L, double3 inv12h, const double* __restrict__ E,
                           const double* __restrict__ rho, const double* __restrict__ T,
                           const double* __restrict__ Ebc, BcOff bo, Opacity op, double c,
                           int mode, int use_df, DfConst K, const float* __restrict__ Eh,
@@ -102,14 +110,15 @@ __global__ void __launch_bounds__(256, 5) k_limiter(Lvl L, double3 inv12h, const
                           double one) {
     const double ih[3] = {inv12h.x, inv12h.y, inv12h.z};
     df ihd[3];
-    for (int d = 0; d < 3; ++d) ihd[d] = df_from_double(ih[d]);
+    if (DF)
+        for (int d = 0; d < 3; ++d) ihd[d] = df_from_double(ih[d]);
     const int nrows = L.n[1] * L.n[2];
     for (int rw = blockIdx.x; rw < nrows; rw += gridDim.x)
         for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
             const int j = rw % L.n[1], k = rw / L.n[1];
             const long long p = (long long)rw * L.n[0] + i;
             double Dv, lm, kv;
-            if (use_df && limiter_cell_df(L, ih, E, rho, T, Ebc, bo, op, K, mode, i, j, k, p, Dv, lm,
+            if (DF && use_df && limiter_cell_df(L, ih, E, rho, T, Ebc, bo, op, K, mode, i, j, k, p, Dv, lm,
                                           Eh, El, ihd, kr ? &kv : nullptr)) {
                 D[p] = Dv;
                 if (lam) lam[p] = lm;
@@ -248,8 +257,12 @@ void launch_limiter(const Lvl& L, const double* h, const double* E, const double
     const int nb = (int)std::min<long long>((long long)L.n[1] * L.n[2], num_sms() * 64);
     const DfConst K = make_dfconst(c, op.kappa0, 0.0, 0.0, 0.0);
     if (!(use_df && mode != FLD_LIMITER_DIFFUSION)) Eh = El = nullptr;
-    k_limiter<<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K, Eh, El, D,
-                                   lam, kr, err, 1.0);
+    if (use_df)
+        k_limiter<true><<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K,
+                                             Eh, El, D, lam, kr, err, 1.0);
+    else
+        k_limiter<false><<<nb, block, 0, s>>>(L, ih, E, rho, T, E_bc, bo, op, c, mode, use_df, K,
+                                              Eh, El, D, lam, kr, err, 1.0);
 }
 
 }  // namespace fld
