@@ -196,6 +196,18 @@ def cpu_baseline(n=256):
     v1, s1, it1 = cpu_oracle_step(Ph, 1)
     vp, sp, itp = cpu_oracle_step(Ph, cores, "pcg")
     vpy, spy, cells_py, _ = cpu_sample_step(64, 1)
+    # the other configurations: the 1D pulse and the 2D log-normal field on all cores and
+    # on one, and a 256^3 sample of the 512^3 linear mode on all cores
+    configs = {}
+    for name, Pc, single in (("pulse1d_256", I.make_config(1), True),
+                             ("lognormal2d_1024", I.make_config(2), True),
+                             ("linmode3d_512_sample_256", I.linear_mode_3d(256, 1.0, steps=1),
+                              False)):
+        va, sa, ia = cpu_oracle_step(Pc, cores, steps=20 if Pc.ncells < 4096 else 1)
+        configs[name] = {"all_cores": va, "seconds": sa, "cycles": ia, "cells": Pc.ncells}
+        if single:
+            configs[name]["single_thread"] = cpu_oracle_step(
+                Pc, 1, steps=20 if Pc.ncells < 4096 else 1)[0]
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "one C-oracle substep (oracle/cfld.c, FP64: limiter, V(2,2) multigrid "
                       "to 1e-10 in %d cycles, exchange) of the stratified recipe at %d^3 = %d "
@@ -208,7 +220,8 @@ def cpu_baseline(n=256):
                                         "%d threads" % (n // 2, cores)},
             "python_oracle": {"value": vpy, "cells": cells_py, "seconds": spy,
                               "sample": "oracle/fld.py (numpy/scipy, PCG, long-double "
-                                        "exchange) at 64^3, one core"}}
+                                        "exchange) at 64^3, one core"},
+            "configs": configs}
 
 
 def aggregate(ms_local, units_local, steps, dist=None, device="cpu"):

@@ -25,11 +25,11 @@ _lib = None
 
 
 def build(force=False):
-    """gcc -O2 with OpenMP when the compiler has it, else without."""
+    """gcc -O3 with OpenMP when the compiler has it, else without."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    base = ["gcc", "-O2", "-fPIC", "-shared", "-o", LIB, SRC, "-lm"]
+    base = ["gcc", "-O3", "-fPIC", "-shared", "-o", LIB, SRC, "-lm"]
     if subprocess.run(base[:4] + ["-fopenmp"] + base[4:], capture_output=True).returncode != 0:
         subprocess.run(base, check=True, capture_output=True)
     return LIB

@@ -35,16 +35,17 @@ __device__ __forceinline__ int rz_axis(int g, int n, bool per) {
 
 __device__ __forceinline__ double rz_factor(int bc) { return bc == FLD_BC_DIRICHLET ? 3.0 : -1.0; }
 
-// FP64 value of an FP32 number in integer arithmetic (normal numbers and zeros; the rest
-// through the conversion instruction).
+// FP64 value of an FP32 number in integer arithmetic only (a conversion instruction would
+// occupy the FP64 pipe, this kernel's bound): exact for normal numbers, zeros and
+// infinities; FP32 subnormals flush to zero and NaNs stay NaNs.
 __device__ __forceinline__ double f64_of(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned a = u & 0x7FFFFFFFu;
     const unsigned long long sg = (unsigned long long)(u >> 31) << 63;
-    if (a >= 0x00800000u && a < 0x7F800000u)
-        return __longlong_as_double((long long)(((((unsigned long long)a) + (896ull << 23)) << 29) | sg));
-    if (a == 0) return __longlong_as_double((long long)sg);
-    return (double)f;
+    unsigned long long r = (((unsigned long long)a) + (896ull << 23)) << 29;   // normal
+    if (a < 0x00800000u) r = 0;                                                 // 0, subnormal
+    if (a >= 0x7F800000u) r = (0x7FFull << 52) | ((unsigned long long)(a & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)(r | sg));
 }
 
 // a + b and a - b as FMAs whose multiplier `one` (1.0) arrives at run time, so the compiler
@@ -54,17 +55,18 @@ __device__ __forceinline__ double f64_of(float f) {
 __device__ __forceinline__ double addf(double a, double b, double one) { return fma(a, one, b); }
 __device__ __forceinline__ double subf(double a, double b, double one) { return fma(b, -one, a); }
 
-// FP32 number nearest to v (ties away from zero) in integer arithmetic where the result is
-// a normal number or zero; the rest through the conversion instruction.
+// FP32 number nearest to v (ties away from zero) in integer arithmetic only: normal
+// results exact to that rounding; below the FP32 normal range zero (subnormals flush),
+// above it infinity, NaN stays NaN.
 __device__ __forceinline__ float f32_of(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
     const unsigned e = (unsigned)(a >> 52);
     const unsigned sg = (unsigned)(b >> 63) << 31;
-    if (e >= 897u && e <= 1149u)
-        return __uint_as_float(((unsigned)((a + (1ull << 28)) >> 29) - (896u << 23)) | sg);
-    if (a == 0) return __uint_as_float(sg);
-    return (float)v;
+    unsigned r = (unsigned)((a + (1ull << 28)) >> 29) - (896u << 23);        // normal
+    if (e < 897u) r = 0;
+    if (e > 1149u) r = (e == 2047u && (a << 12)) ? 0x7FC00000u : 0x7F800000u;
+    return __uint_as_float(r | sg);
 }
 
 __global__ void __launch_bounds__(RZ_NT, 5)
@@ -426,7 +428,7 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
         }
     };
 
-    double acc2 = 0.0;
+    float acc2f = 0.f;
     float xm = 0.f, km = 0.f, xc = 0.f, kc = 0.f, xp = 0.f, kp = 0.f;
     if (act) {
         column(z0, 0.f, xc, kc);
@@ -466,7 +468,7 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
             rv = fmaf(-hy, sy, rv);
             rv = fmaf(-hz, sz, rv);
             r32[pk + own] = rv;
-            acc2 = fma((double)rv, (double)rv, acc2);
+            acc2f = fmaf(rv, rv, acc2f);
         }
         __syncthreads();
         xm = xc;
@@ -475,6 +477,9 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
         kc = kp;
         cur = nxt;
     }
+    // the squares of this column summed in FP32 (a chunk's planes at most: the norm only
+    // reports and screens the first residual), then in FP64 across the block
+    const double acc2 = (double)acc2f;
     const double a2 = block_sum(acc2, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = a2;
 }
