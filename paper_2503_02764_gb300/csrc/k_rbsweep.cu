@@ -8,9 +8,9 @@
 // alternate between the two rows; with a shared row pitch of 8 (mod 32) words those 32
 // scalar accesses fall in 32 distinct banks, as do those of every neighbour.
 //
-// Shared memory holds a ring of ZM_R planes of x and K, each with a 2-row halo in y and a
-// 4-column (one 16-byte chunk) halo in x, filled by cp.async ZM_D planes ahead of use; b,
-// read by its own cell only, goes to registers, loaded two steps ahead. Step k evaluates the red cells of plane k in place in the shared copy, on the tile
+// Shared memory holds a ring of ZM_R planes of x, K and b, each with a 2-row halo in y
+// and a 4-column (one 16-byte chunk) halo in x, filled by cp.async ZM_D planes ahead of
+// use. Step k evaluates the red cells of plane k in place in the shared copy, on the tile
 // and on its 1-cell ring (the ring values are recomputed rather than exchanged between
 // blocks), and the black cells of plane k-2, which need the red values of planes k-3 ..
 // k-1 only, so the two share one barrier per step; it stores plane k-2 of xout. Per sweep
@@ -21,7 +21,7 @@
 // The updates are those of the half-sweep kernels: red cells take (b + acc)/(1 + sw) of
 // the input iterate, black cells that of the red-updated one, with the same face weights
 // (K_p + K_q) w_d / 2 summed in the same order. Boundary faces are encoded in the halo
-// instead of branches: x is 0 outside the domain, and K of the ghost next to a wall
+// instead of branches: x and b are 0 outside the domain, and K of the ghost next to a wall
 // is -K of the wall cell (Neumann: the face weight vanishes) or 3 K (Dirichlet: the face
 // weight becomes the half-cell 2 K w_d of the operator; the wall value itself lives in b).
 // Periodic axes wrap. Same-colour cells must never meet across a periodic wrap, so odd
@@ -49,7 +49,7 @@ struct ZmShape {
     static constexpr int NCH = NROW * CPR;      // chunks per plane and field
     static constexpr int WX = TX / 32;          // warps across the tile width
     static constexpr int NT = 32 * WX * (TY / 2);
-    static constexpr size_t SMEM = sizeof(float) * 2 * ZM_R * PL;
+    static constexpr size_t SMEM = sizeof(float) * 3 * ZM_R * PL;
     static_assert(TX % 32 == 0 && TY % 2 == 0, "tile of whole warps and row pairs");
     static_assert(XW % 32 == 8 || XW % 32 == 24, "row pitch giving conflict-free lanes");
     static_assert(NCH <= NT, "one copy chunk per thread");
@@ -85,12 +85,12 @@ __device__ __forceinline__ void zm_wait() {
 }
 
 // (b + acc)/(1 + sw) of one cell: z points at the shared array, o0 is the cell's offset
-// in the slot of its plane (x at +0, K at +PL), om and op the offsets of the same cell in
-// the slots of the planes below and above; XW is the row pitch; h* = w_d / 2; bv the
-// cell's b. Every access is one shared load at an immediate offset from o0, om or op.
+// in the slot of its plane (x at +0, K at +PL, b at +2 PL), om and op the offsets of the
+// same cell in the slots of the planes below and above; XW is the row pitch; h* = w_d / 2.
+// Every access is one shared load at an immediate offset from o0, om or op.
 template <int XW, int PL>
 __device__ __forceinline__ float zm_relax(const float* z, int o0, int om, int op, float hx,
-                                          float hy, float hz, float bv) {
+                                          float hy, float hz) {
     const float kc = z[o0 + PL];
     float f = (kc + z[o0 + PL - 1]) * hx;
     float sw = f;
@@ -110,7 +110,7 @@ __device__ __forceinline__ float zm_relax(const float* z, int o0, int om, int op
     f = (kc + z[op + PL]) * hz;
     sw += f;
     acc = fmaf(f, z[op], acc);
-    return __fdividef(bv + acc, 1.0f + sw);
+    return __fdividef(z[o0 + 2 * PL] + acc, 1.0f + sw);
 }
 
 }  // namespace
@@ -177,14 +177,16 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
         if (cmode < 5 && m <= z1 + 1) {
             float* Sd = zsm + slot + soff;
             float* Kd = Sd + PL;
+            float* Bd = Kd + PL;
             const int gz = zm_axis(m, nz, zper);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gz >= 0 && cmode == 0) {
                 const long long o = gz * plane + goff;
                 zm_cp16(Sd, xin + o);
                 zm_cp16(Kd, K + o);
+                zm_cp16(Bd, b + o);
             } else {
-                // ghosts: x = 0 and K = factor * K of the mirrored wall cell
+                // ghosts: x = b = 0 and K = factor * K of the mirrored wall cell
                 float4 k4 = z4;
                 if (gz >= 0 && cmode == 1) {
                     k4.w = gfac * K[gz * plane + goff];
@@ -201,6 +203,7 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
                 }
                 *reinterpret_cast<float4*>(Sd) = z4;
                 *reinterpret_cast<float4*>(Kd) = k4;
+                *reinterpret_cast<float4*>(Bd) = z4;
             }
         }
         zm_commit();
@@ -220,7 +223,6 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
     const int ax = min(TX, nx - tx0), ay = min(TY, ny - ty0);
     const int nrow = (ax + 2) / 2, ncol = (ay + 1) / 2;
     int rc0 = -1, rc1 = -1;    // shared offsets of the two candidates (-1: not a cell)
-    long long rg0 = 0, rg1 = 0;   // their plane offsets in global memory (wrapped)
     int rpar = 0;              // parity of gx + gy of candidate 0
     {
         int qx0 = 0, qy0 = 0, dx = 0, dy = 0;
@@ -240,46 +242,22 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
             rpar = (tx0 + qx0 + ty0 + qy0) & 1;
             for (int q = 0; q < 2; ++q) {
                 const int qx = qx0 + q * dx, qy = qy0 + q * dy;
-                const int wx = zm_axis(tx0 + qx, nx, xper), wy = zm_axis(ty0 + qy, ny, yper);
-                const bool cell = wx >= 0 && wy >= 0;
+                const bool cell = zm_axis(tx0 + qx, nx, xper) >= 0 &&
+                                  zm_axis(ty0 + qy, ny, yper) >= 0;
                 const int off = (cell && !(colseg && qy >= ay)) ? (qy + 2) * XW + ZM_XL + qx : -1;
-                const long long g = off >= 0 ? (long long)wy * nx + wx : 0;
-                if (q == 0) { rc0 = off; rg0 = g; } else { rc1 = off; rg1 = g; }
+                if (q == 0) rc0 = off; else rc1 = off;
             }
         }
     }
 
-    // Ring slot offsets of planes k-3 .. k+3 at step k (x at +0, K at +PL); each step
-    // rotates them by one, the slot of k-3 coming back as that of k+4.
-    auto slot_of = [&](int m) { return ((m + 2 * ZM_R) % ZM_R) * 2 * PL; };
+    // Ring slot offsets of planes k-3 .. k+3 at step k (x at +0, K at +PL, b at +2 PL);
+    // each step rotates them by one, the slot of k-3 coming back as that of k+4.
+    auto slot_of = [&](int m) { return ((m + 2 * ZM_R) % ZM_R) * 3 * PL; };
     int pm3 = slot_of(z0 - 4), pm2 = slot_of(z0 - 3), pm1 = slot_of(z0 - 2), p00 = slot_of(z0 - 1);
     int pp1 = slot_of(z0), pp2 = slot_of(z0 + 1), pp3 = slot_of(z0 + 2);
     static_assert(ZM_D == 2 && ZM_R == 7, "the rotation below holds planes k-3 .. k+3");
     const bool ring_warp = (tid & ~31) < 2 * nrow + 2 * ncol;   // warp-uniform
     float* xo = xout + (long long)gy0 * nx + gx;
-    const bool ring_thread = rc0 >= 0 || rc1 >= 0;
-
-    // b in registers: step k uses b of its red cell (plane k, row q), of its black cell
-    // (plane k - 2, row 1 - q) and of its ring cell (plane k); step k loads those of step
-    // k + 2 (the red and ring rows keep the parity of k, the black one is row 1 - q of
-    // plane k). Slots [0]: step k, [1]: step k + 1.
-    const float* bc0 = b + (long long)gy0 * nx + gx;
-    float bred[2] = {0.f, 0.f}, bblk[2] = {0.f, 0.f}, bring[2] = {0.f, 0.f};
-    auto bload = [&](int k, float& vr, float& vbk, float& vg) {
-        vr = vbk = vg = 0.f;
-        const int q = (gx + gy0 + k) & 1;        // red row at planes k and k + 2
-        const int mr = k + 2;
-        const int gr = mr <= z1 ? zm_axis(mr, nz, zper) : -1;
-        if (gr >= 0) {
-            if (q ? act1 : act0) vr = bc0[gr * plane + (long long)q * nx];
-            if (ring_thread) {
-                const bool rsel = (rpar + k) & 1;
-                if ((rsel ? rc1 : rc0) >= 0) vg = b[gr * plane + (rsel ? rg1 : rg0)];
-            }
-        }
-        if (k >= z0 && k < z1 && ((1 - q) ? act1 : act0))
-            vbk = bc0[(long long)k * plane + (long long)(1 - q) * nx];
-    };
 
     // ---- the march. Step k: planes <= k + 1 have landed; red(k) on the tile and its ring
     // (in place in the shared copy) and black(k - 2), which reads planes k - 3 .. k - 1
@@ -290,12 +268,7 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
     issue(z0 - 1, p00);
     issue(z0, pp1);
     issue(z0 + 1, pp2);
-    // b of steps z0 - 1 and z0 (their black cells lie before the chunk: none)
-    bload(z0 - 3, bred[0], bblk[0], bring[0]);
-    bload(z0 - 2, bred[1], bblk[1], bring[1]);
     for (int k = z0 - 1; k <= z1 + 1; ++k) {
-        float nr, nb, ng;
-        bload(k, nr, nb, ng);        // for step k + 2
         zm_wait<ZM_D - 1>();
         __syncthreads();
         issue(k + 3, pp3);
@@ -305,16 +278,15 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
         // are even, ghost planes are not updated)
         const int q = (gx + gy0 + k) & 1;
         const int cr = c0 + q * XW, cb = cr + (1 - 2 * q) * XW;
-        const float vr = zm_relax<XW, PL>(zsm, p00 + cr, pm1 + cr, pp1 + cr, hx, hy, hz, bred[0]);
+        const float vr = zm_relax<XW, PL>(zsm, p00 + cr, pm1 + cr, pp1 + cr, hx, hy, hz);
         // black(k - 2): the other row of the pair at plane k - 2 (same parity as k)
-        const float vb = zm_relax<XW, PL>(zsm, pm2 + cb, pm3 + cb, pm1 + cb, hx, hy, hz, bblk[0]);
+        const float vb = zm_relax<XW, PL>(zsm, pm2 + cb, pm3 + cb, pm1 + cb, hx, hy, hz);
         const float vrb = zsm[pm2 + cr];             // its red cell, updated two steps ago
         if (ring_warp) {
             const bool rsel = (rpar + k) & 1;
             const int cg = rsel ? rc1 : rc0;
             const int cq = cg >= 0 ? cg : c0;
-            const float vg = zm_relax<XW, PL>(zsm, p00 + cq, pm1 + cq, pp1 + cq, hx, hy, hz,
-                                              bring[0]);
+            const float vg = zm_relax<XW, PL>(zsm, p00 + cq, pm1 + cq, pp1 + cq, hx, hy, hz);
             if (do_red && cg >= 0) zsm[p00 + cg] = vg;
         }
         if (do_red && (q ? act1 : act0)) zsm[p00 + cr] = vr;
@@ -325,15 +297,13 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
         }
         const int t = pm3;
         pm3 = pm2; pm2 = pm1; pm1 = p00; p00 = pp1; pp1 = pp2; pp2 = pp3; pp3 = t;
-        bred[0] = bred[1]; bblk[0] = bblk[1]; bring[0] = bring[1];
-        bred[1] = nr; bblk[1] = nb; bring[1] = ng;
     }
     zm_wait<0>();
 }
 
 namespace {
 
-constexpr int ZM_TX = 32, ZM_TY = 16, ZM_MINB = 4;
+constexpr int ZM_TX = 32, ZM_TY = 16, ZM_MINB = 3;
 using ZmMain = ZmShape<ZM_TX, ZM_TY>;
 
 constexpr int ZM_MAXDEV = 64;
