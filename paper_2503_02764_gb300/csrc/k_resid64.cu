@@ -35,17 +35,17 @@ __device__ __forceinline__ int rz_axis(int g, int n, bool per) {
 
 __device__ __forceinline__ double rz_factor(int bc) { return bc == FLD_BC_DIRICHLET ? 3.0 : -1.0; }
 
-// FP64 value of an FP32 number in integer arithmetic only (a conversion instruction would
-// occupy the FP64 pipe, this kernel's bound): exact for normal numbers, zeros and
-// infinities; FP32 subnormals flush to zero and NaNs stay NaNs.
+// FP64 value of an FP32 number in integer arithmetic (normal numbers and zeros; the rest
+// through the conversion instruction, a branch the FP64 residual takes only for such
+// values).
 __device__ __forceinline__ double f64_of(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned a = u & 0x7FFFFFFFu;
     const unsigned long long sg = (unsigned long long)(u >> 31) << 63;
-    unsigned long long r = (((unsigned long long)a) + (896ull << 23)) << 29;   // normal
-    if (a < 0x00800000u) r = 0;                                                 // 0, subnormal
-    if (a >= 0x7F800000u) r = (0x7FFull << 52) | ((unsigned long long)(a & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)(r | sg));
+    if (a >= 0x00800000u && a < 0x7F800000u)
+        return __longlong_as_double((long long)(((((unsigned long long)a) + (896ull << 23)) << 29) | sg));
+    if (a == 0) return __longlong_as_double((long long)sg);
+    return (double)f;
 }
 
 // a + b and a - b as FMAs whose multiplier `one` (1.0) arrives at run time, so the compiler
@@ -55,10 +55,23 @@ __device__ __forceinline__ double f64_of(float f) {
 __device__ __forceinline__ double addf(double a, double b, double one) { return fma(a, one, b); }
 __device__ __forceinline__ double subf(double a, double b, double one) { return fma(b, -one, a); }
 
-// FP32 number nearest to v (ties away from zero) in integer arithmetic only: normal
-// results exact to that rounding; below the FP32 normal range zero (subnormals flush),
-// above it infinity, NaN stays NaN.
+// FP32 number nearest to v (ties away from zero) in integer arithmetic where the result is
+// a normal number or zero; the rest through the conversion instruction.
 __device__ __forceinline__ float f32_of(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned e = (unsigned)(a >> 52);
+    const unsigned sg = (unsigned)(b >> 63) << 31;
+    if (e >= 897u && e <= 1149u)
+        return __uint_as_float(((unsigned)((a + (1ull << 28)) >> 29) - (896u << 23)) | sg);
+    if (a == 0) return __uint_as_float(sg);
+    return (float)v;
+}
+
+// The same conversion in integer arithmetic only, for the FP32 residual (no branch to a
+// conversion instruction): below the FP32 normal range zero (subnormals flush), above it
+// infinity, NaN stays NaN.
+__device__ __forceinline__ float f32_of_i(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
     const unsigned e = (unsigned)(a >> 52);
@@ -400,7 +413,7 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
         const int gz = rz_axis(m, nz, zper);
         if (gz >= 0) {
             const long long q = gz * plane + own;
-            xv = f32_of(x[q]);
+            xv = f32_of_i(x[q]);
             kv = K[q];
         } else {
             xv = 0.f;
@@ -442,18 +455,18 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
         float bk = 0.f;
         if (act) {
             if (rz_axis(k + 1, nz, zper) >= 0) {
-                xp = f32_of(cur.x);
+                xp = f32_of_i(cur.x);
                 kp = cur.k;
             } else {
                 xp = 0.f;
                 kp = kc * (float)rz_factor(L.bchi[2]);
             }
-            bk = f32_of(cur.b);
+            bk = f32_of_i(cur.b);
             XS[so] = xc;
             KS[so] = kc;
         }
         if (rso >= 0) {
-            XS[rso] = rghost ? 0.f : f32_of(cur.rx);
+            XS[rso] = rghost ? 0.f : f32_of_i(cur.rx);
             KS[rso] = rghost ? rfac * cur.rk : cur.rk;
         }
         __syncthreads();

@@ -143,6 +143,14 @@ def test_wave_argument_errors():
     Ud = dev(torch, R.Wave(P).initial())
     with pytest.raises(fld.FldError):
         gpu.step(Ud, 0.0, -1.0)
+    # a state with a NaN density, or with a negative gas energy (negative pressure), in one
+    # cell: the signal-speed maximum is +inf and the time-step call reports a domain error
+    for var, cell, value in ((0, 100, np.nan), (6, 50, -1.0)):
+        U = np.array(R.Wave(P).initial(), dtype=np.float64).reshape(8, -1)
+        U[var, cell] = value
+        with pytest.raises(fld.FldError) as ei:
+            gpu.max_dt(dev(torch, U), 0.8)
+        assert ei.value.code == fld.FLD_ERR_DOMAIN
     gpu.close()
     bad = fld.make_wave1d_params(P, **OPTS)
     bad.n_driven = bad.n
