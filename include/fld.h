@@ -217,6 +217,14 @@ fld_status fld_create(fld_handle** h, const fld_grid* g, const fld_opts* o);
 /* Free the handle and its workspace (NULL is accepted). */
 fld_status fld_destroy(fld_handle* h);
 
+/* Bounds flags of the debug build. The library compiled with FLD_DEBUG (the build step's
+   libfld_gb300_debug.so) checks the computed indices of its stencil, gradient, residual,
+   sweep and transfer kernels: an index outside its array raises a flag in a device word
+   and is replaced by 0 (the kernel carries on; nothing traps). Returns the flags raised
+   since the last call (0: none) and clears them, synchronising the device; -1 from the
+   normal build, which carries no checks. */
+int fld_debug_flags(void);
+
 /* Replace the handle's options (the grid and workspace are kept). */
 fld_status fld_set_opts(fld_handle* h, const fld_opts* o);
 

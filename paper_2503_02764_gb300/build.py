@@ -3,6 +3,11 @@
 Each translation unit under csrc/ is compiled by nvcc in parallel, then linked
 into one shared library next to this file. No cmake, no torch extension
 machinery: the library exports a plain C ABI (include/fld.h).
+
+build(debug=True) (or FLD_DEBUG=1 in the environment of `python build.py`) makes the
+bounds-checked variant libfld_gb300_debug.so beside it, compiled with -DFLD_DEBUG: the
+kernels' computed indices are checked and out-of-range ones flagged (fld_debug_flags())
+instead of dereferenced. The binding loads it when FLD_LIBRARY names it.
 """
 from __future__ import annotations
 
@@ -18,6 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfld_gb300.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libfld_gb300_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -43,14 +50,17 @@ def _stale(obj, src):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose=False, force=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, force=False, extra=(), debug=False):
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra = tuple(extra) + ("-DFLD_DEBUG",)
+    os.makedirs(bdir, exist_ok=True)
     nv = nvcc()
     jobs = []
     objs = []
     for f in sources():
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f[:-3] + ".o")
+        obj = os.path.join(bdir, f[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, src):
             jobs.append([nv, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
@@ -67,11 +77,12 @@ def build(verbose=False, force=False, extra=()):
         for err in ex.map(run, jobs):
             if verbose and err:
                 print(err)
-    if force or jobs or not os.path.exists(LIB) or any(
-            os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        run([nv, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
-    return LIB
+    if force or jobs or not os.path.exists(lib) or any(
+            os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        run([nv, *ARCH, "-shared", "-o", lib, *objs, "-lcudart"])
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv,
+                debug=os.environ.get("FLD_DEBUG") == "1"))

@@ -112,6 +112,33 @@ int num_sms() {
 }
 // launches made outside this file's launch wrapper (the wave step's kernels)
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Debug build: every translation unit registers the setter of its copy of the debug
+// word's address when the library loads; the word is allocated and handed to all of them
+// on the first handle creation.
+namespace {
+std::vector<void (*)(unsigned*)>& debug_setters() {
+    static std::vector<void (*)(unsigned*)> v;
+    return v;
+}
+unsigned* g_debug_word = nullptr;
+std::mutex g_debug_mu;
+}  // namespace
+void debug_register(void (*attach)(unsigned*)) { debug_setters().push_back(attach); }
+void debug_attach_all() {
+#ifdef FLD_DEBUG
+    std::lock_guard<std::mutex> lock(g_debug_mu);
+    if (g_debug_word) return;
+    if (cudaMalloc(&g_debug_word, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        g_debug_word = nullptr;
+        return;
+    }
+    cudaMemset(g_debug_word, 0, sizeof(unsigned));
+    for (auto f : debug_setters()) f(g_debug_word);
+    cudaDeviceSynchronize();
+#endif
+}
 }  // namespace fld
 
 struct fld_handle {
@@ -808,6 +835,7 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
     if (!rc) {
         prepare_rb_sweep();
         prepare_vcycle_tail();
+        debug_attach_all();
     }
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = FLD_ERR_CUDA;
     if (rc) {
@@ -817,6 +845,22 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
     }
     *out = h;
     return FLD_OK;
+}
+
+int fld_debug_flags(void) {
+#ifdef FLD_DEBUG
+    std::lock_guard<std::mutex> lock(g_debug_mu);
+    if (!g_debug_word) return 0;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, g_debug_word, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemset(g_debug_word, 0, sizeof(unsigned));
+    return (int)v;
+#else
+    return -1;
+#endif
 }
 
 fld_status fld_destroy(fld_handle* h) {

@@ -26,7 +26,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
     const int fm = FM < 0 ? L.fm : FM;
     // cell indices fit in 32 bits (the handle rejects grids of 2^31 cells or more)
     const int p = (int)p64;
-    const T Kc = K[p];
+    const T Kc = K[fld_at(p, L.ncell)];
     const int c[3] = {i, j, k};
     int stride = 1;
     sw = T(0);
@@ -41,6 +41,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
             if (c[d] > 0) q = p - stride;
             else if (L.bclo[d] == FLD_BC_PERIODIC) q = p + (n - 1) * stride;
             if (q >= 0) {
+                q = (int)fld_at(q, L.ncell);
                 const T w = fmean(Kc, K[q], fm) * wd;
                 sw += w;
                 acc += w * x[q];
@@ -52,6 +53,7 @@ __device__ __forceinline__ void stencil(const Lvl& L, const T* __restrict__ K,
             if (c[d] < n - 1) q = p + stride;
             else if (L.bchi[d] == FLD_BC_PERIODIC) q = p - (n - 1) * stride;
             if (q >= 0) {
+                q = (int)fld_at(q, L.ncell);
                 const T w = fmean(Kc, K[q], fm) * wd;
                 sw += w;
                 acc += w * x[q];
@@ -147,7 +149,7 @@ __device__ __forceinline__ double fetch_E(const Lvl& L, const double* __restrict
     int m = c[d] + o;
     if (m >= 0 && m < n) {
         c[d] = m;
-        return E[lin(L, c[0], c[1], c[2])];
+        return E[fld_at(lin(L, c[0], c[1], c[2]), L.ncell)];
     }
     int kind, side, mirror;
     if (m < 0) {
@@ -163,7 +165,7 @@ __device__ __forceinline__ double fetch_E(const Lvl& L, const double* __restrict
     }
     const long long fi = face_index(L, d, i, j, k);
     c[d] = mirror;
-    const double v = E[lin(L, c[0], c[1], c[2])];
+    const double v = E[fld_at(lin(L, c[0], c[1], c[2]), L.ncell)];
     if (kind == FLD_BC_DIRICHLET) return 2.0 * Ebc[bo.off[2 * d + side] + fi] - v;
     return v;
 }

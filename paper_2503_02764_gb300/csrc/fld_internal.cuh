@@ -10,6 +10,41 @@ namespace fld {
 // Device error bits (OR-ed into the handle's status word).
 enum : unsigned { ERRBIT_DOMAIN = 1u, ERRBIT_TIMEOUT = 2u, ERRBIT_NOTCONV = 4u };
 
+// Bounds-checked indexing for the debug build (FLD_DEBUG defined at compile time; the
+// library's build step makes it with FLD_DEBUG=1 in the environment). fld_at(i, n) is i
+// when 0 <= i < n; otherwise it raises a flag in a device word the host reads with
+// fld_debug_flags() and returns 0, so the access stays inside the array and the kernel
+// carries on (no trap). Without FLD_DEBUG it is i itself. The word's address is held in
+// a constant of each translation unit, set for all of them when a handle is created.
+void debug_register(void (*attach)(unsigned*));
+void debug_attach_all();
+#ifdef FLD_DEBUG
+static __constant__ unsigned* fld_dbg_word;
+// registers, at load time, the setter of this translation unit's copy (internal linkage)
+static void fld_debug_attach_here(unsigned* w) {
+    cudaMemcpyToSymbol(fld_dbg_word, &w, sizeof(w));
+}
+static int fld_debug_register_here() {
+    debug_register(&fld_debug_attach_here);
+    return 0;
+}
+static int fld_debug_registered = fld_debug_register_here();
+__device__ __forceinline__ long long fld_at(long long i, long long n) {
+    if (i >= 0 && i < n) return i;
+    if (fld_dbg_word) atomicOr(fld_dbg_word, 1u);
+    return 0;
+}
+// the same for the span [i, i + len) of one vector access
+__device__ __forceinline__ long long fld_span(long long i, long long len, long long n) {
+    if (i >= 0 && i + len <= n) return i;
+    if (fld_dbg_word) atomicOr(fld_dbg_word, 1u);
+    return 0;
+}
+#else
+__device__ __forceinline__ long long fld_at(long long i, long long) { return i; }
+__device__ __forceinline__ long long fld_span(long long i, long long, long long) { return i; }
+#endif
+
 // One multigrid level of a uniform block. The operator at this level is
 //   (A x)_p = x_p + sum_faces 0.5 (K_p + K_q) w_d (x_p - x_q) + sum_dirichlet 2 K_p w_d x_p
 // with K = dt D / H_x^2 (stored per cell) and w_d = (H_x / H_d)^2.

@@ -159,32 +159,32 @@ __device__ __forceinline__ void rb_cell(const Lvl& L, int i, int j, int k, T* __
                                         const T* __restrict__ b, const T* __restrict__ K) {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int sy = nx, sz = nx * ny;
-    const int p = (k * ny + j) * nx + i;
+    const int p = (int)fld_at((k * ny + j) * nx + i, L.ncell);
     const T kc = K[p];
     T sw = T(0), acc = T(0);
     const T wx = wgt<T>(L, 0);
     int q = i > 0 ? p - 1 : (L.bclo[0] == FLD_BC_PERIODIC ? p + nx - 1 : -1);
-    if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wx; sw += w; acc += w * x[q]; }
+    if (q >= 0) { q = (int)fld_at(q, L.ncell); const T w = fmean(kc, K[q], L.fm) * wx; sw += w; acc += w * x[q]; }
     else if (L.bclo[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
     q = i < nx - 1 ? p + 1 : (L.bchi[0] == FLD_BC_PERIODIC ? p - nx + 1 : -1);
-    if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wx; sw += w; acc += w * x[q]; }
+    if (q >= 0) { q = (int)fld_at(q, L.ncell); const T w = fmean(kc, K[q], L.fm) * wx; sw += w; acc += w * x[q]; }
     else if (L.bchi[0] == FLD_BC_DIRICHLET) sw += T(2) * kc * wx;
     if (L.ndim >= 2) {
         const T wy = wgt<T>(L, 1);
         q = j > 0 ? p - sy : (L.bclo[1] == FLD_BC_PERIODIC ? p + (ny - 1) * sy : -1);
-        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wy; sw += w; acc += w * x[q]; }
+        if (q >= 0) { q = (int)fld_at(q, L.ncell); const T w = fmean(kc, K[q], L.fm) * wy; sw += w; acc += w * x[q]; }
         else if (L.bclo[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
         q = j < ny - 1 ? p + sy : (L.bchi[1] == FLD_BC_PERIODIC ? p - (ny - 1) * sy : -1);
-        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wy; sw += w; acc += w * x[q]; }
+        if (q >= 0) { q = (int)fld_at(q, L.ncell); const T w = fmean(kc, K[q], L.fm) * wy; sw += w; acc += w * x[q]; }
         else if (L.bchi[1] == FLD_BC_DIRICHLET) sw += T(2) * kc * wy;
     }
     if (L.ndim >= 3) {
         const T wz = wgt<T>(L, 2);
         q = k > 0 ? p - sz : (L.bclo[2] == FLD_BC_PERIODIC ? p + (nz - 1) * sz : -1);
-        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wz; sw += w; acc += w * x[q]; }
+        if (q >= 0) { q = (int)fld_at(q, L.ncell); const T w = fmean(kc, K[q], L.fm) * wz; sw += w; acc += w * x[q]; }
         else if (L.bclo[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
         q = k < nz - 1 ? p + sz : (L.bchi[2] == FLD_BC_PERIODIC ? p - (nz - 1) * sz : -1);
-        if (q >= 0) { const T w = fmean(kc, K[q], L.fm) * wz; sw += w; acc += w * x[q]; }
+        if (q >= 0) { q = (int)fld_at(q, L.ncell); const T w = fmean(kc, K[q], L.fm) * wz; sw += w; acc += w * x[q]; }
         else if (L.bchi[2] == FLD_BC_DIRICHLET) sw += T(2) * kc * wz;
     }
     x[p] = div_fast<T>(b[p] + acc, T(1) + sw);
@@ -427,26 +427,26 @@ __global__ void k_resid64(Lvl L, const double* __restrict__ x, const double* __r
             ozp = k < nz - 1 ? sz : (L.bchi[2] == FLD_BC_PERIODIC ? -(nz - 1) * sz : -1);
         }
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const int p = base + i;
+            const int p = (int)fld_at(base + i, L.ncell);
             const double xc = x[p], kc = K[p];
             double ax = 0.0, ay = 0.0, az = 0.0, dir = 0.0;
             // x faces
             int q = i > 0 ? p - 1 : (L.bclo[0] == FLD_BC_PERIODIC ? p + nx - 1 : -1);
-            if (q >= 0) ax = fma(fsum2(kc, K[q], L.fm), xc - x[q], ax);
+            if (q >= 0) { q = (int)fld_at(q, L.ncell); ax = fma(fsum2(kc, K[q], L.fm), xc - x[q], ax); }
             else if (L.bclo[0] == FLD_BC_DIRICHLET) dir += L.w[0];
             q = i < nx - 1 ? p + 1 : (L.bchi[0] == FLD_BC_PERIODIC ? p - nx + 1 : -1);
-            if (q >= 0) ax = fma(fsum2(kc, K[q], L.fm), xc - x[q], ax);
+            if (q >= 0) { q = (int)fld_at(q, L.ncell); ax = fma(fsum2(kc, K[q], L.fm), xc - x[q], ax); }
             else if (L.bchi[0] == FLD_BC_DIRICHLET) dir += L.w[0];
             if (L.ndim >= 2) {
-                if (oym != -1) ay = fma(fsum2(kc, K[p + oym], L.fm), xc - x[p + oym], ay);
+                if (oym != -1) { const int q2 = (int)fld_at(p + oym, L.ncell); ay = fma(fsum2(kc, K[q2], L.fm), xc - x[q2], ay); }
                 else if (L.bclo[1] == FLD_BC_DIRICHLET) dir += L.w[1];
-                if (oyp != -1) ay = fma(fsum2(kc, K[p + oyp], L.fm), xc - x[p + oyp], ay);
+                if (oyp != -1) { const int q2 = (int)fld_at(p + oyp, L.ncell); ay = fma(fsum2(kc, K[q2], L.fm), xc - x[q2], ay); }
                 else if (L.bchi[1] == FLD_BC_DIRICHLET) dir += L.w[1];
             }
             if (L.ndim >= 3) {
-                if (ozm != -1) az = fma(fsum2(kc, K[p + ozm], L.fm), xc - x[p + ozm], az);
+                if (ozm != -1) { const int q2 = (int)fld_at(p + ozm, L.ncell); az = fma(fsum2(kc, K[q2], L.fm), xc - x[q2], az); }
                 else if (L.bclo[2] == FLD_BC_DIRICHLET) dir += L.w[2];
-                if (ozp != -1) az = fma(fsum2(kc, K[p + ozp], L.fm), xc - x[p + ozp], az);
+                if (ozp != -1) { const int q2 = (int)fld_at(p + ozp, L.ncell); az = fma(fsum2(kc, K[q2], L.fm), xc - x[q2], az); }
                 else if (L.bchi[2] == FLD_BC_DIRICHLET) dir += L.w[2];
             }
             double res = fma(-hx, ax, b[p] - xc);

@@ -181,7 +181,7 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
             const int gz = zm_axis(m, nz, zper);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (gz >= 0 && cmode == 0) {
-                const long long o = gz * plane + goff;
+                const long long o = fld_span(gz * plane + goff, 4, L.ncell);
                 zm_cp16(Sd, xin + o);
                 zm_cp16(Kd, K + o);
                 zm_cp16(Bd, b + o);
@@ -189,15 +189,17 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
                 // ghosts: x = b = 0 and K = factor * K of the mirrored wall cell
                 float4 k4 = z4;
                 if (gz >= 0 && cmode == 1) {
-                    k4.w = gfac * K[gz * plane + goff];
+                    k4.w = gfac * K[fld_at(gz * plane + goff, L.ncell)];
                 } else if (gz >= 0 && cmode == 2) {
-                    k4.x = gfac * K[gz * plane + goff];
+                    k4.x = gfac * K[fld_at(gz * plane + goff, L.ncell)];
                 } else if (gz >= 0 && cmode == 3) {
-                    const float4 v = *reinterpret_cast<const float4*>(K + gz * plane + goff);
+                    const float4 v = *reinterpret_cast<const float4*>(
+                        K + fld_span(gz * plane + goff, 4, L.ncell));
                     k4 = make_float4(gfac * v.x, gfac * v.y, gfac * v.z, gfac * v.w);
                 } else if ((gz == -1 || gz == -2) && cmode == 0) {
                     const float f = zm_ghost_factor(gz == -1 ? L.bclo[2] : L.bchi[2]);
-                    const long long o = (long long)(gz == -1 ? 0 : nz - 1) * plane + goff;
+                    const long long o = fld_span((long long)(gz == -1 ? 0 : nz - 1) * plane + goff,
+                                                 4, L.ncell);
                     const float4 v = *reinterpret_cast<const float4*>(K + o);
                     k4 = make_float4(f * v.x, f * v.y, f * v.z, f * v.w);
                 }
@@ -291,7 +293,9 @@ k_rb_zmarch(Lvl L, const float* __restrict__ xin, float* __restrict__ xout,
         }
         if (do_red && (q ? act1 : act0)) zsm[p00 + cr] = vr;
         if (do_black) {
+            // the pair's plane k - 2 (its row span checked in the debug build)
             float* o = xo + (long long)(k - 2) * plane;
+            if (act0) o = xout + fld_span(o - xout, act1 ? nx + 1 : 1, L.ncell);
             if (act0) o[0] = q ? vb : vrb;
             if (act1) o[nx] = q ? vrb : vb;
         }

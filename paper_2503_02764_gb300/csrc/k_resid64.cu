@@ -150,14 +150,14 @@ k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
         if (gz < 0) return;                   // a wall ghost plane: formed from K below
         const long long pk = gz * plane;
         if (act) {
-            const long long q = pk + own;
+            const long long q = fld_at(pk + own, L.ncell);
             R.x = x[q];
             R.k = K[q];
             R.e = e ? e[q] : 0.f;
             if (m < z1) R.b = b[q];
         }
         if (rso >= 0 && m < z1) {
-            const long long q = pk + rsrc;
+            const long long q = fld_at(pk + rsrc, L.ncell);
             R.rk = K[q];
             if (!rghost) {
                 R.rx = x[q];
@@ -194,7 +194,7 @@ k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
             if (act) {
                 XS[so] = xk;
                 KS[so] = kk;
-                if (xo) xo[(long long)k * plane + own] = xk;
+                if (xo) xo[fld_at((long long)k * plane + own, L.ncell)] = xk;
             }
             if (rso >= 0) {
                 XS[rso] = rghost ? 0.0 : xnew(cur.rx, cur.re);
@@ -221,7 +221,7 @@ k_resid64z(Lvl L, const double* __restrict__ x, const float* __restrict__ e,
         // the plane below is complete: its +z face is this plane's -z face
         if (act && k - 1 >= z0) {
             const double r = fma(-hz, subf(gzprev, gz, one), part);
-            if (r32) r32[(long long)(k - 1) * plane + own] = f32_of(r);
+            if (r32) r32[fld_at((long long)(k - 1) * plane + own, L.ncell)] = f32_of(r);
             acc2 = fma(r, r, acc2);
         }
         __syncthreads();
@@ -412,7 +412,7 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
     auto column = [&](int m, float kwall, float& xv, float& kv) {
         const int gz = rz_axis(m, nz, zper);
         if (gz >= 0) {
-            const long long q = gz * plane + own;
+            const long long q = fld_at(gz * plane + own, L.ncell);
             xv = f32_of_i(x[q]);
             kv = K[q];
         } else {
@@ -430,14 +430,16 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
         const int g1 = rz_axis(k + 1, nz, zper);
         if (act) {
             if (g1 >= 0) {
-                R.x = x[g1 * plane + own];
-                R.k = K[g1 * plane + own];
+                const long long q = fld_at(g1 * plane + own, L.ncell);
+                R.x = x[q];
+                R.k = K[q];
             }
-            R.b = b[(long long)k * plane + own];
+            R.b = b[fld_at((long long)k * plane + own, L.ncell)];
         }
         if (rso >= 0) {
-            R.rk = K[(long long)k * plane + rsrc];
-            if (!rghost) R.rx = x[(long long)k * plane + rsrc];
+            const long long q = fld_at((long long)k * plane + rsrc, L.ncell);
+            R.rk = K[q];
+            if (!rghost) R.rx = x[q];
         }
     };
 
@@ -480,7 +482,7 @@ k_resid32z(Lvl L, const double* __restrict__ x, const double* __restrict__ b,
             float rv = fmaf(-hx, sx, bk - xc);
             rv = fmaf(-hy, sy, rv);
             rv = fmaf(-hz, sz, rv);
-            r32[pk + own] = rv;
+            r32[fld_at(pk + own, L.ncell)] = rv;
             acc2f = fmaf(rv, rv, acc2f);
         }
         __syncthreads();

@@ -94,7 +94,7 @@ __global__ void k_resid_restrict3(Lvl F, Lvl C, const T* __restrict__ x, const T
         const long long pz = (long long)(k0 + c) * sz;
 #pragma unroll
         for (int bb = 0; bb < 2; ++bb) {
-            const long long row = pz + (long long)(j0 + bb) * sy;
+            const long long row = fld_span(pz + (long long)(j0 + bb) * sy, nx, F.ncell);
             const Pair<T> xv = ld2(x + row + i0), kv = ld2(K + row + i0), bv = ld2(b + row + i0);
             // x-neighbours of the pair
             const T xlv = xl >= 0 ? x[row + xl] : T(0);
@@ -106,21 +106,22 @@ __global__ void k_resid_restrict3(Lvl F, Lvl C, const T* __restrict__ x, const T
             const T fy = bb ? fyr : fyl;
             Pair<T> xyo, kyo;
             if (jo >= 0) {
-                xyo = ld2(x + pz + (long long)jo * sy + i0);
-                kyo = ld2(K + pz + (long long)jo * sy + i0);
+                const long long ry = fld_span(pz + (long long)jo * sy, nx, F.ncell);
+                xyo = ld2(x + ry + i0);
+                kyo = ld2(K + ry + i0);
             } else {
                 xyo.v[0] = xyo.v[1] = T(0);
                 kyo.v[0] = fy * kv.v[0];
                 kyo.v[1] = fy * kv.v[1];
             }
-            const long long rowi = pz + (long long)(j0 + 1 - bb) * sy;   // the pair's other row
+            const long long rowi = fld_span(pz + (long long)(j0 + 1 - bb) * sy, nx, F.ncell);   // the pair's other row
             const Pair<T> xyi = ld2(x + rowi + i0), kyi = ld2(K + rowi + i0);
             // z-neighbours (plane k0 - 1 for c = 0, k0 + 2 for c = 1; the other is the pair)
             const int ko = c ? zr : zl;
             const T fz = c ? fzr : fzl;
             Pair<T> xzo, kzo;
             if (ko >= 0) {
-                const long long ro = (long long)ko * sz + (long long)(j0 + bb) * sy + i0;
+                const long long ro = fld_span((long long)ko * sz + (long long)(j0 + bb) * sy, nx, F.ncell) + i0;
                 xzo = ld2(x + ro);
                 kzo = ld2(K + ro);
             } else {
@@ -128,7 +129,7 @@ __global__ void k_resid_restrict3(Lvl F, Lvl C, const T* __restrict__ x, const T
                 kzo.v[0] = fz * kv.v[0];
                 kzo.v[1] = fz * kv.v[1];
             }
-            const long long rzi = (long long)(k0 + 1 - c) * sz + (long long)(j0 + bb) * sy + i0;
+            const long long rzi = fld_span((long long)(k0 + 1 - c) * sz + (long long)(j0 + bb) * sy, nx, F.ncell) + i0;
             const Pair<T> xzi = ld2(x + rzi), kzi = ld2(K + rzi);
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
@@ -161,7 +162,7 @@ __global__ void k_resid_restrict3(Lvl F, Lvl C, const T* __restrict__ x, const T
             }
         }
     }
-    bc[((long long)Kc * C.n[1] + J) * C.n[0] + I] = s * T(0.125);
+    bc[fld_at(((long long)Kc * C.n[1] + J) * C.n[0] + I, C.ncell)] = s * T(0.125);
 }
 
 template <typename T>
@@ -210,7 +211,7 @@ __global__ void k_prolong3(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict
     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const T* r = xc + ((long long)iz[dz] * cy + iy[dy]) * cx;
+            const T* r = xc + fld_span(((long long)iz[dz] * cy + iy[dy]) * cx, cx, C.ncell);
             const T s = sz[dz] * sy[dy];
             const T e0 = s * sx[0] * r[ix[0]], e1 = s * r[ix[1]], e2 = s * sx[2] * r[ix[2]];
             vx[dz][dy][0] = T(0.75) * e1 + T(0.25) * e0;
@@ -232,7 +233,7 @@ __global__ void k_prolong3(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict
         for (int bb = 0; bb < 2; ++bb) {
             const T v0 = T(0.75) * vy[1][bb][0] + T(0.25) * vy[c ? 2 : 0][bb][0];
             const T v1 = T(0.75) * vy[1][bb][1] + T(0.25) * vy[c ? 2 : 0][bb][1];
-            T* p = xf + (long long)(2 * Kc + c) * sz2 + (long long)(2 * J + bb) * sy2 + 2 * I;
+            T* p = xf + fld_span((long long)(2 * Kc + c) * sz2 + (long long)(2 * J + bb) * sy2, nx, F.ncell) + 2 * I;
             const Pair<T> old = ld2(p);
             st2(p, old.v[0] + v0, old.v[1] + v1);
         }

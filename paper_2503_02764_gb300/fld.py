@@ -10,7 +10,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIBPATH = os.path.join(HERE, "libfld_gb300.so")
+# the library (FLD_LIBRARY may name another build of it, such as the bounds-checked
+# libfld_gb300_debug.so)
+LIBPATH = os.environ.get("FLD_LIBRARY") or os.path.join(HERE, "libfld_gb300.so")
 
 FLD_OK, FLD_ERR_ARG, FLD_ERR_DOMAIN, FLD_ERR_NOT_CONVERGED, FLD_ERR_TIMEOUT, FLD_ERR_CUDA, \
     FLD_ERR_NOMEM = range(7)
@@ -91,12 +93,13 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIBPATH):
-        raise ImportError("libfld_gb300.so not built: run paper_2503_02764_gb300/build.py")
+        raise ImportError("%s not built: run paper_2503_02764_gb300/build.py" % LIBPATH)
     L = C.CDLL(LIBPATH)
     sig = {
         "fld_default_opts": (None, [C.POINTER(fld_opts)]),
         "fld_create": (C.c_int, [C.POINTER(H), C.POINTER(fld_grid), C.POINTER(fld_opts)]),
         "fld_destroy": (C.c_int, [H]),
+        "fld_debug_flags": (C.c_int, []),
         "fld_set_opts": (C.c_int, [H, C.POINTER(fld_opts)]),
         "fld_num_levels": (C.c_int, [H]),
         "fld_limiter": (C.c_int, [H, C.POINTER(fld_consts), C.POINTER(fld_opacity), P, P, P, P, P,
@@ -313,6 +316,12 @@ def fld_prof_read(h, cap=256):
     n = lib().fld_prof_read(h, buf, cap)
     return [{"name": e.name.decode(), "level": e.level, "launches": e.launches, "cells": e.cells,
              "ms": e.ms} for e in buf[:n]]
+
+
+def fld_debug_flags():
+    """Bounds flags raised since the last call by the debug build of the library (cleared
+    by the call); -1 from the normal build."""
+    return lib().fld_debug_flags()
 
 
 def fld_launch_count():

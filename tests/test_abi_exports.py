@@ -144,3 +144,11 @@ def test_face_mean_and_diag_checks_without_gpu():
     assert L.fld_amr_create(ctypes.byref(a), ctypes.byref(g),
                             ctypes.byref(fld.make_patch((3, 3), (9, 9))),
                             ctypes.byref(o)) == fld.FLD_ERR_ARG
+
+
+def test_normal_build_has_no_bounds_checks():
+    # fld_debug_flags answers -1 from the normal build (no device call is made)
+    from paper_2503_02764_gb300 import fld
+    if os.environ.get("FLD_LIBRARY", "").endswith("_debug.so"):
+        return
+    assert fld.fld_debug_flags() == -1
