@@ -323,12 +323,15 @@ int zm_slots() {
 
 // z-chunk length: about three waves of blocks over the SMs (the tiles times the chunks),
 // chunks of at least 8 planes so the 2-plane overlap stays small (32 planes at 256^3,
-// the fastest measured there).
+// the fastest measured there). Levels of at most 64^3 cells are bound by the march's
+// per-plane latency, not by traffic: their chunks go down to 2 planes, so more blocks
+// march fewer steps each.
 int zm_chunk(const Lvl& L) {
     const int tiles = ((L.n[0] + ZM_TX - 1) / ZM_TX) * ((L.n[1] + ZM_TY - 1) / ZM_TY);
     const int nch = std::max(1, 2 * zm_slots() / std::max(1, tiles));
     const int cz = (L.n[2] + nch - 1) / nch;
-    return std::min(L.n[2], std::max(8, cz));
+    const int minc = L.ncell <= (1LL << 18) ? 2 : 8;
+    return std::min(L.n[2], std::max(minc, cz));
 }
 
 }  // namespace
