@@ -12,8 +12,9 @@
  *   2. diffuse  (the div F term of Eq. mhd_r_e with F = -D grad E, treated
  *        implicitly as Sect. 3 describes): backward Euler
  *        (I - dt div D grad) E^{n+1} = E^n on cell-centred finite volumes,
- *        face D = mean of the two cell values, solved by geometric multigrid
- *        V-cycles to a relative residual ||b - A x||_2 / ||b||_2 <= tol;
+ *        face D = mean of the two cell values (arithmetic, or harmonic as an
+ *        option), solved by geometric multigrid V-cycles (1D grids: a direct
+ *        tridiagonal solve) to a relative residual ||b - A x||_2 / ||b||_2 <= tol;
  *   3. exchange (Eqs. heating, qdot; implicit quartic of Sect. 3): backward
  *        Euler on de/dt = +qdot, dE/dt = -qdot, qdot = c kappa rho (E - a_r T^4),
  *        e = rho R_gas T / (gamma - 1) (Eqs. energy_density, ideal_gas_law).
@@ -21,8 +22,10 @@
  * Around the substep: its explicit coupling terms (fld_coupling), a batched
  * substep over many independent grids in one launch (fld_step_batched), an
  * allocation-free solve (fld_diffuse_static), a 1D radiation-MHD step that
- * runs the substep inside a hyperbolic update (fld_wave1d_*) and the diffusion
- * solve on a coarse block with a refined box (fld_amr_*).
+ * runs the substep inside a hyperbolic update (fld_wave1d_*), the implicit stage
+ * of the ARS3 IMEX scheme (fld_ars3_*), the diffusion solve on a coarse block
+ * with a refined box (fld_amr_*), and the bounds flags of the debug build
+ * (fld_debug_flags).
  *
  * Layout: every field is a contiguous float64 array of n[0]*n[1]*n[2] cells,
  * x fastest: index = (k * n[1] + j) * n[0] + i. Absent axes have n = 1.
