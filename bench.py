@@ -384,9 +384,13 @@ DTYPE = {
                    "f64 exchange), with the double-f32 (48-bit) limiter: gradient from f32 "
                    "pairs of E, R, lambda, D",
 }
-BATCH_DTYPE = ("f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
-               "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
-               "exponent window)")
+BATCH_DTYPE = {
+    "mixed": "f32 V-cycles inside f64 iterative refinement (f64 residuals and corrections); "
+             "f64 coarsest solve; f64 limiter; f64 exchange (f32 Newton seed, f64 Newton polish)",
+    "mixed_df": "f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
+                "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
+                "exponent window)",
+}
 PREC = {"mixed_df": 2, "mixed": 1, "fp64": 0}
 
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per SM per
@@ -418,14 +422,16 @@ def run_batch(args):
     # each rank advances its own independent batch (weak scaling, no collective)
     seed = I.SEED_BASE + 4 + 100000 * rank
     res = batch_workload(fld, I, torch, args.nprob, seed, args.steps, args.warmup, args.block,
-                         args.cluster, dist=dist, local=local)
+                         args.cluster, dist=dist, local=local,
+                         precision=args.precision if args.precision != "fp64" else "mixed")
     ms, cells_all, value = aggregate(res["ms_per_step"] * args.steps, res["cells"], args.steps,
                                      dist, "cuda")
     line = {"metric": METRIC + " [batched]", "value": value,
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": BATCH_DTYPE, "data": "synthetic",
+            "vs_baseline": None, "dtype": res["dtype"], "data": "synthetic",
             "config": {"workload": res["workload"], "cells": res["cells"],
+                       "precision": res["precision"],
                        "block": res["options"]["block"], "cluster": res["options"]["cluster"],
                        "nu1": res["options"]["nu1"], "nu2": res["options"]["nu2"],
                        "inner": res["options"]["inner"], "autotuned": res["autotuned"]},
@@ -438,15 +444,17 @@ def run_batch(args):
 
 
 def batch_workload(fld, I, torch, nprob, seed, steps, warmup, block=0, cluster=0, dist=None,
-                   local=0):
-    """Time `steps` batched substeps (after `warmup`) of the nprob-member batch."""
+                   local=0, precision="mixed"):
+    """Time `steps` batched substeps (after `warmup`) of the nprob-member batch in the given
+    precision mode (mixed: FP64 refinement, limiter and exchange; mixed_df: double-FP32)."""
     ps = I.batch(nprob, seed_base=seed)
     from paper_2503_02764_gb300 import autotune
     tuned = autotune.batch_options(ps)
     kw = dict(block=block, cluster=cluster, nu1=2, nu2=2, inner=1)
     if tuned and not (block or cluster):
         kw = tuned
-    b = fld.Batch([(p.shape, p.h, p.bc) for p in ps], tol=1e-10, max_cycles=50, graph=1, **kw)
+    b = fld.Batch([(p.shape, p.h, p.bc) for p in ps], tol=1e-10, max_cycles=50, graph=1,
+                  precision=PREC[precision], **kw)
     cat = lambda xs: torch.from_numpy(np.concatenate([x.ravel() for x in xs])).cuda()
     rho, T, E = cat([p.rho for p in ps]), cat([p.T for p in ps]), cat([p.E for p in ps])
     consts = fld.make_consts(1.0, 1.0, 5.0 / 3.0, 1.0)
@@ -480,8 +488,8 @@ def batch_workload(fld, I, torch, nprob, seed, steps, warmup, block=0, cluster=0
             "options": {"block": kw["block"] or 512, "cluster": kw["cluster"] or "auto",
                         "nu1": kw["nu1"], "nu2": kw["nu2"], "inner": kw.get("inner", 1)},
             "autotuned": bool(tuned and not (block or cluster)),
-            "max_cycles_per_step": cyc, "clocks": clocks, "precision": "mixed_df",
-            "dtype": BATCH_DTYPE, "gpu_launches": fld.fld_launch_count() - n0}
+            "max_cycles_per_step": cyc, "clocks": clocks, "precision": precision,
+            "dtype": BATCH_DTYPE[precision], "gpu_launches": fld.fld_launch_count() - n0}
 
 
 def step_series(hd, consts, op, P, rho, T, E, ebc, steps, warmup, torch):
@@ -640,6 +648,10 @@ def config_workloads(fld, I, torch, peak_hbm, nprob=512, big=512):
         hd.close()
     # 4: the 512-member batch, one launch per step
     out["batch_%d" % nprob] = batch_workload(fld, I, torch, nprob, I.SEED_BASE + 4, 5, 2)
+    out["batch_%d" % nprob]["mixed_df"] = {
+        k: v for k, v in batch_workload(fld, I, torch, nprob, I.SEED_BASE + 4, 5, 2,
+                                        precision="mixed_df").items()
+        if k in ("ms_per_step", "cell_updates_per_s", "max_cycles_per_step", "dtype")}
     # 5: linear mode at big^3, mixed, 100 steps, for both pressure ratios, seeded with the
     # fast magnetosonic eigenmode (B at 45 degrees to k); the complex amplitudes of the
     # k = 2 pi mode before and after are reported (the GPU tests compare them with the

@@ -305,9 +305,10 @@ fld_status fld_step(fld_handle* h, const fld_consts* k, const fld_opacity* op, d
    persistent kernel launch (512 uneven 2D problems is the intended scale):
    every block takes the next problem from a queue ordered by decreasing cell count
    and runs limiter -> multigrid solve -> exchange on it, so no block ever waits on
-   another. The solve is the MIXED_DF scheme (FP32 V-cycles inside double-FP32
-   iterative refinement) whatever o->precision says; o->block (256, 512 or 1024; 0 =
-   512) is the block size and o->cluster the number of blocks that share one problem
+   another. The solve runs FP32 V-cycles inside iterative refinement whose residual,
+   correction, limiter and exchange are FP64 (o->precision FLD_PREC_MIXED, or
+   FLD_PREC_FP64, which keeps the FP32 V-cycles) or double-FP32 (FLD_PREC_MIXED_DF);
+   o->block (256, 512 or 1024; 0 = 512) is the block size and o->cluster the number of blocks that share one problem
    (a thread-block cluster synchronised by the hardware cluster barrier);
    o->nu1/nu2/coarse_sweeps/tol/max_cycles/limiter apply.
    Layout: the fields of all problems are concatenated in problem order (problem p

@@ -17,7 +17,8 @@ struct BProb {
     long long cell_off;     // first cell of the problem in the concatenated fields
     long long ebc_off;      // first Dirichlet face value in the concatenated faces (-1: none)
     long long bc_off[6];    // Dirichlet face blocks within the problem's faces (-1: none)
-    long long ws_d;         // offset (doubles) of the problem's D in the FP64 workspace
+    long long ws_d;         // offset (doubles) of the problem's FP64 workspace: D, then
+                            // the FP64 refinement's x, b and K (4 n doubles)
     long long ws_f;         // offset (floats) of the problem's FP32 workspace
 };
 
@@ -31,6 +32,7 @@ struct BatchParams {
     double c, a_r, cv;      // speed of light, radiation constant, R_gas/(gamma - 1)
     double tol;
     int max_cycles, nu1, nu2, coarse_sweeps, limiter, inner;
+    int fp64;               // 1: FP64 refinement, limiter and exchange; 0: double-FP32
 };
 
 struct BatchStat {

@@ -140,7 +140,7 @@ fld_status fld_batch_create(fld_batch** out, int nprob, const fld_grid* grids, c
         P.ebc_off = nf ? b->nface : -1;
         b->nface += nf;
         P.ws_d = b->wsd_n;
-        b->wsd_n += n0;
+        b->wsd_n += 4 * n0;                   // D, and the FP64 refinement's x, b, K
         long long f = 6 * n0;                 // double-FP32 x, b, K (hi and lo)
         for (int l = 0; l < P.nlev; ++l) {
             P.o32[l] = f;
@@ -239,6 +239,7 @@ fld_status fld_step_batched(fld_batch* b, const fld_consts* k, const fld_opacity
     prm.coarse_sweeps = b->o.coarse_sweeps;
     prm.limiter = b->o.limiter;
     prm.inner = b->o.inner > 0 ? b->o.inner : 1;
+    prm.fp64 = b->o.precision == FLD_PREC_MIXED_DF ? 0 : 1;
     const int nt = block_threads(b->o);
     const int cl = cluster_size(b, nt);
     const int maxg = batch_max_groups(nt, cl);

@@ -1,8 +1,9 @@
 // Batched FLD substep: many independent problems of uneven sizes in ONE persistent
 // launch. A group of CS blocks (a thread-block cluster when CS > 1, one block when
 // CS == 1) takes the next problem from a queue ordered by decreasing size and runs the
-// whole substep on it: limiter -> multigrid solve (FP32 V-cycles inside double-FP32
-// iterative refinement, to the relative-residual tolerance) -> exchange.
+// whole substep on it: limiter -> multigrid solve (FP32 V-cycles inside FP64 or
+// double-FP32 iterative refinement, to the relative-residual tolerance) -> exchange, the
+// limiter and the exchange in the refinement's arithmetic.
 //
 // The group's threads split every phase's cells; phases are separated by the hardware
 // cluster barrier (or __syncthreads), reductions go through distributed shared memory
@@ -332,6 +333,25 @@ __device__ double grp_df_resid(const Grp<CS>& g, const Lvl& L, const DfW& wd, co
     return grp_sum(a2, sh, g);
 }
 
+// Level-0 residual in FP64: r = b - A x with the level operator's stencil, r32 = r rounded
+// to FP32; returns the group's sum of r^2.
+template <int CS>
+__device__ double grp_resid64(const Grp<CS>& g, const Lvl& L, const double* x, const double* b,
+                              const double* K, float* r32, GroupShared& sh) {
+    double a2 = 0.0;
+    for (int p = g.tid; p < (int)L.ncell; p += g.nthr) {
+        int i, j, k;
+        decode(L, p, i, j, k);
+        double sw, acc;
+        stencil<double>(L, K, x, i, j, k, p, sw, acc);
+        const double r = b[p] - fma(1.0 + sw, x[p], -acc);
+        r32[p] = (float)r;
+        a2 = fma(r, r, a2);
+    }
+    g.sync();
+    return grp_sum(a2, sh, g);
+}
+
 template <int NT, int CS>
 __global__ void __launch_bounds__(NT)
 k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
@@ -362,6 +382,9 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
         double* E_ = E + P.cell_off;
         const double* eb = P.ebc_off >= 0 ? Ebc + P.ebc_off : nullptr;
         double* D = wsd + P.ws_d;
+        double* x64 = D + n0;              // FP64 refinement (prm.fp64): iterate, rhs, K
+        double* b64 = D + 2 * n0;
+        double* K64 = D + 3 * n0;
         float* F = wsf + P.ws_f;
         float* xh = F;
         float* xl = F + n0;
@@ -390,8 +413,8 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
             int i, j, k;
             decode(L0, p, i, j, k);
             double Dv = 0.0, lm;
-            if (!limiter_cell_df(L0, ih, E_, r_, T_, eb, bo, op, KC, prm.limiter, i, j, k, p, Dv,
-                                 lm) &&
+            if (!(!prm.fp64 && limiter_cell_df(L0, ih, E_, r_, T_, eb, bo, op, KC, prm.limiter, i,
+                                               j, k, p, Dv, lm)) &&
                 !limiter_cell<false>(L0, ih, E_, r_, T_, eb, bo, op, prm.c, prm.limiter, i, j, k,
                                      p, Dv, lm))
                 bad += 1.0;
@@ -426,6 +449,43 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
                 b2 = fma(bp, bp, b2);
             }
             b2 = grp_sum(b2, sh, g);
+            if (prm.fp64) {
+                // ---- FP64 refinement: x = E^n, b and K in FP64, FP32 V-cycles on A e = r
+                for (int p = g.tid; p < n0; p += g.nthr) {
+                    const double Kp = kscale * D[p];
+                    x64[p] = E_[p];
+                    b64[p] = bval(p, Kp);
+                    K64[p] = Kp;
+                    K32[p] = (float)Kp;
+                }
+                g.sync();
+                for (int l = 0; l + 1 < P.nlev; ++l) {
+                    const long long nf = P.lv[l].ncell, nc = P.lv[l + 1].ncell;
+                    grp_restrict_K(g, P.lv[l], P.lv[l + 1], (float)P.kdown[l],
+                                   F + P.o32[l] + 2 * nf, F + P.o32[l + 1] + 2 * nc);
+                }
+                const double bnorm = sqrt(b2);
+                rel = bnorm > 0.0 ? sqrt(grp_resid64(g, L0, x64, b64, K64, b32, sh)) / bnorm : 0.0;
+                rel0 = rel;
+                while (rel > prm.tol && cyc < prm.max_cycles && isfinite(rel)) {
+                    for (int p = g.tid; p < n0; p += g.nthr) x32[p] = 0.f;
+                    g.sync();
+                    for (int ic = 0; ic < prm.inner; ++ic)
+                        grp_vcycle(g, P, F, prm.nu1, prm.nu2, prm.coarse_sweeps, sh);
+                    for (int p = g.tid; p < n0; p += g.nthr) x64[p] += (double)x32[p];
+                    g.sync();
+                    rel = sqrt(grp_resid64(g, L0, x64, b64, K64, b32, sh)) / bnorm;
+                    ++cyc;
+                }
+                // ---- the exchange in FP64 with kappa(rho, T^n)
+                const double dtc = dt * prm.c;
+                for (int p = g.tid; p < n0; p += g.nthr) {
+                    double t = T_[p], e_new = x64[p];
+                    exchange_cell<false>(r_[p], t, e_new, op, dtc, prm.a_r, prm.cv);
+                    T_[p] = t;
+                    E_[p] = e_new;
+                }
+            } else {
             int ex = 0;
             frexp(b2 > 0.0 ? sqrt(b2 / n0) : 1.0, &ex);
             const double S = ldexp(1.0, -ex);
@@ -487,6 +547,7 @@ k_batch_step(const BProb* __restrict__ probs, const BDyn* __restrict__ dyn,
                 }
                 T_[p] = t;
                 E_[p] = e_new;
+            }
             }
         }
         if (g.rank == 0 && threadIdx.x == 0) {

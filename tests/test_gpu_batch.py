@@ -44,15 +44,17 @@ def _split(ps, v):
     return out
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("block,cluster", [(256, 1), (512, 1), (1024, 1), (256, 8), (512, 2),
                                            (512, 4), (1024, 8)])
-def test_batch_matches_oracle(block, cluster):
-    # cluster > 1: a thread-block cluster shares each problem
+def test_batch_matches_oracle(block, cluster, precision):
+    # cluster > 1: a thread-block cluster shares each problem; precision 1 (MIXED): FP64
+    # refinement, limiter and exchange, 2 (MIXED_DF): double-FP32
     torch = torch_cuda()
     fld = library()
     ps = _problems()
     b, rc, st, _, T, E = _run(fld, torch, ps, tol=1e-13, max_cycles=60, block=block,
-                              cluster=cluster)
+                              cluster=cluster, precision=precision)
     assert rc in (0, 3), st
     for p, Tp, Ep, s in zip(ps, _split(ps, T), _split(ps, E), st):
         assert s["rel_resid"] < 1e-10, s
