@@ -449,7 +449,7 @@ def batch_workload(fld, I, torch, nprob, seed, steps, warmup, block=0, cluster=0
     precision mode (mixed: FP64 refinement, limiter and exchange; mixed_df: double-FP32)."""
     ps = I.batch(nprob, seed_base=seed)
     from paper_2503_02764_gb300 import autotune
-    tuned = autotune.batch_options(ps)
+    tuned = autotune.batch_options(ps, PREC[precision])
     kw = dict(block=block, cluster=cluster, nu1=2, nu2=2, inner=1)
     if tuned and not (block or cluster):
         kw = tuned

@@ -69,11 +69,14 @@ def grid_options(problem, precision, gpu=None):
             "inner": b.get("inner", 1), "prolong": b.get("prolong", 0)}, True
 
 
-def batch_options(problems, gpu=None):
-    """Options of the batched substep in the benchmark: the cached best for this GPU and
-    batch (block, cluster, nu1, nu2, inner), else None."""
+def batch_options(problems, precision=None, gpu=None):
+    """Options of the batched substep in the benchmark: the cached best for this GPU, batch
+    and precision mode (else the entry cached without a precision) as (block, cluster,
+    nu1, nu2, inner), else None."""
     try:
-        c = cached("batch", signature("batch", problems), gpu)
+        c = ((precision is not None and cached("batch", signature("batch", problems, precision),
+                                                gpu))
+             or cached("batch", signature("batch", problems), gpu))
     except Exception:
         c = None
     if not c:
@@ -130,8 +133,10 @@ def _time_batch(fld, torch, problems, opts, reps=3):
 
 
 def tune_batch(problems, blocks=(256, 512, 1024), clusters=(1, 2, 4, 8),
-               sweeps=((2, 2), (1, 1), (2, 1), (3, 3)), inners=(1, 2), tol=1e-10, store=True):
-    """Time every (block, cluster, nu1, nu2, inner) candidate on the batch; return the best."""
+               sweeps=((2, 2), (1, 1), (2, 1), (3, 3)), inners=(1, 2), tol=1e-10, store=True,
+               precision=None):
+    """Time every (block, cluster, nu1, nu2, inner) candidate on the batch in the given
+    precision mode (the library's default when None); return the best."""
     import torch
     from . import fld
     results = []
@@ -141,6 +146,8 @@ def tune_batch(problems, blocks=(256, 512, 1024), clusters=(1, 2, 4, 8),
                 for inner in inners:
                     opts = dict(tol=tol, max_cycles=60, block=nb, cluster=cl, nu1=nu1, nu2=nu2,
                                 inner=inner, graph=0)
+                    if precision is not None:
+                        opts["precision"] = int(precision)
                     try:
                         t, ok = _time_batch(fld, torch, problems, opts)
                     except fld.FldError:
@@ -151,7 +158,7 @@ def tune_batch(problems, blocks=(256, 512, 1024), clusters=(1, 2, 4, 8),
     best = min(good, key=lambda r: r["seconds"]) if good else None
     if store and best:
         gpu = gpu_name()
-        _store(signature("batch", problems), {"best": best, "candidates": results,
+        _store(signature("batch", problems, precision), {"best": best, "candidates": results,
                                               "when": time.strftime("%Y-%m-%dT%H:%M:%SZ",
                                                                     time.gmtime())}, gpu)
     return best, results
