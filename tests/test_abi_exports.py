@@ -152,3 +152,30 @@ def test_normal_build_has_no_bounds_checks():
     if os.environ.get("FLD_LIBRARY", "").endswith("_debug.so"):
         return
     assert fld.fld_debug_flags() == -1
+
+
+def test_size_limits_and_degenerate_grids_without_gpu():
+    # the host rejects, before any device work: a grid of 2^31 cells (32-bit indices), a
+    # batch member above 2^27 cells, an axis of one cell, a negative or NaN spacing, and
+    # a composite box of 2^31 or more fine cells (here the whole box refined: 2^33)
+    from paper_2503_02764_gb300 import fld
+    L = fld.lib()
+    o = fld.make_opts()
+    for shape, h in ((((1 << 11), (1 << 10), (1 << 10)), (1.0, 1.0, 1.0)),     # 2^31 cells
+                     ((1, 8), (1.0, 1.0)),                                      # n = 1
+                     ((8, 8), (1.0, -1.0)),
+                     ((8, 8), (float("nan"), 1.0))):
+        g = fld.make_grid(shape, h, ((0, 0),) * len(shape))
+        hh = fld.H()
+        assert L.fld_create(ctypes.byref(hh), ctypes.byref(g), ctypes.byref(o)) == \
+            fld.FLD_ERR_ARG, shape
+    big = fld.make_grid(((1 << 10), (1 << 9), (1 << 9)), (1.0, 1.0, 1.0), ((0, 0),) * 3)
+    arr = (fld.fld_grid * 1)(big)                                               # 2^28 cells
+    b = fld.H()
+    assert L.fld_batch_create(ctypes.byref(b), 1, arr, ctypes.byref(o)) == fld.FLD_ERR_ARG
+    assert L.fld_batch_create(ctypes.byref(b), 0, arr, ctypes.byref(o)) == fld.FLD_ERR_ARG
+    g = fld.make_grid(((1 << 10), (1 << 10), (1 << 10)), (1.0, 1.0, 1.0), ((0, 0),) * 3)
+    a = fld.H()
+    assert L.fld_amr_create(ctypes.byref(a), ctypes.byref(g),
+                            ctypes.byref(fld.make_patch((0, 0, 0), (1024, 1024, 1024))),
+                            None) == fld.FLD_ERR_ARG                           # 2^33 fine cells
