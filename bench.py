@@ -47,6 +47,7 @@ BYTES_PER_CELL = {
     "resid64": 28.0,          # x, b, K read; r32 written (mixed) / 24 (fp64)
     "resid64x": 40.0,         # x, e32, b, K read; x + e, r32 written
     "resid32": 24.0,          # x, b (FP64), K32 read; r32 written (FP32 arithmetic)
+    "resid_upd": 32.0,        # x, e32, K32, r32 read; x + e, r32 written (r - A e in FP32)
     "resid_df": 40.0,         # x (hi, lo), e32, b (hi, lo), K (hi, lo) read; x (hi, lo), r32 written
     "rbhalf32": 10.0,         # one colour: the other colour's x and every K read (faces),
     "rbhalf64": 20.0,         #   this colour's b read and x written
@@ -372,9 +373,12 @@ def run_reference(args):
 
 DTYPE = {
     "mixed": "f32 V-cycles (smoothing, restriction, prolongation) inside f64 iterative "
-             "refinement (f64 residuals and corrections; the first correction from the f32 "
-             "residual of E^n, an f32 initial solve); f64 coarsest solve; f64 limiter; f64 "
-             "exchange (f32 Newton seed, f64 Newton polish)",
+             "refinement (f64 corrections x + e; the first correction from the f32 residual "
+             "of E^n, the residual after it in f64, later ones updated as r - A e in f32 with "
+             "a rigorous rounding bound added to the reported residual); f64 coarsest "
+             "solve; f64 limiter; f64 exchange (f32 Newton seed, f64 Newton polish)",
+    "mixed_fp64res": "as mixed, with every refinement residual after the first correction "
+                     "formed in f64 (b - A x)",
     "mixed_df": "f32 V-cycles inside double-f32 (48-bit) iterative refinement; f64 coarsest "
                 "solve; double-f32 limiter and exchange polish (f64 for cells outside the f32 "
                 "exponent window)",
@@ -912,12 +916,13 @@ def main():
     # tuned options, from the same state (rank 0)
     variants = {}
     if rank == 0 and not args.no_variants:
-        for name in ("mixed_df", "fp64", "mixed", "mixed_dflim"):
+        for name in ("mixed_df", "fp64", "mixed", "mixed_dflim", "mixed_fp64res"):
             if name == args.precision:
                 continue
-            base = "mixed" if name == "mixed_dflim" else name
+            base = "mixed" if name in ("mixed_dflim", "mixed_fp64res") else name
             o, t = options(PREC[base])
             o = dict(o, limiter_df=1) if name == "mixed_dflim" else o
+            o = dict(o, resid_update=0) if name == "mixed_fp64res" else o
             hv = fld.Handle(P.shape, P.h, P.bc, precision=PREC[base], tol=1e-10, max_cycles=50, **o)
             Tv, Ev = T_start.clone(), E_start.clone()
             nst = max(5, args.steps // 4) if name == "fp64" else args.steps
@@ -934,9 +939,11 @@ def main():
     if rank == 0 and not args.no_ttt:
         D = torch.empty_like(E)
         hd.limiter(consts, op, E_start, rho, T_start, ebc, D)
-        for name, pr in (("mixed_df", fld.PREC_MIXED_DF), ("mixed", fld.PREC_MIXED),
-                         ("fp64", fld.PREC_FP64)):
+        for name, pr, extra in (("mixed_df", fld.PREC_MIXED_DF, {}), ("mixed", fld.PREC_MIXED, {}),
+                                ("mixed_fp64res", fld.PREC_MIXED, {"resid_update": 0}),
+                                ("fp64", fld.PREC_FP64, {})):
             o, _ = options(pr)
+            o = dict(o, **extra)
             hd.set_opts(precision=pr, tol=1e-10, max_cycles=50, **o)
             times, cyc = [], 0
             for rep in range(4):

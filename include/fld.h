@@ -180,6 +180,17 @@ typedef struct {
                            R, lambda, D; relative error ~1e-14) whatever the precision
                            mode, the solve and the exchange keeping theirs; 0 (default):
                            the limiter of the precision mode                           */
+    int resid_update;   /* MIXED on 3D grids with the arithmetic face mean: 1 (default)
+                           forms the first refinement residual after the FP32 solve of
+                           E^n in FP64 and the later ones as r - A e, A e evaluated in FP32
+                           on the level's FP32 coefficients (x + e stays FP64), with a
+                           per-cell bound on that update's rounding accumulated beside it;
+                           the solve stops when ||r|| plus the accumulated bound is below
+                           tol ||b|| (rel_resid reports that sum, an upper bound on the
+                           true relative residual), and takes a full FP64 residual
+                           whenever the bound alone passes tol/2 or the recursive residual
+                           is below tol while the sum is not. 0: every refinement residual
+                           in FP64. Ignored by the other modes and grids                */
 } fld_opts;
 
 enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };

@@ -35,6 +35,8 @@ struct DevScalars {       // read back together after each cycle
     unsigned err;
     unsigned pad;
     double energy[2];     // diagnostics: total energy before and after a call
+    double drift;         // recursive residual: sum of the squared scaled rounding bound
+    double amax;          //   and the largest absolute row sum of the level-0 operator
 };
 
 std::atomic<long long> g_launches{0};
@@ -233,7 +235,8 @@ bool fld::opts_valid(const fld_opts* o) {
            (o->face_mean == FLD_FACE_ARITH ||
             (o->face_mean == FLD_FACE_HARM && o->precision != FLD_PREC_MIXED_DF)) &&
            (o->prolong == FLD_PROLONG_LINEAR || o->prolong == FLD_PROLONG_CONSTANT) &&
-           (o->limiter_df == 0 || o->limiter_df == 1);
+           (o->limiter_df == 0 || o->limiter_df == 1) &&
+           (o->resid_update == 0 || o->resid_update == 1);
 }
 
 namespace {
@@ -478,6 +481,34 @@ fld_status residual(fld_handle* h, const double* x, const float* e, double* xo, 
     return read_scalars(h, s, rr, err);
 }
 
+// The recursive refinement residual at level 0 (3D, MIXED): xo = x + e (e the FP32 V-cycles'
+// correction), r32 <- r32 - A e in FP32; *rr = ||r||^2, *dd = ||beta||^2 (beta the per-cell
+// bound on the update's rounding) and *amax the largest absolute row sum of A. The kernel
+// forms beta' = 2^20 beta and squares rs r and bs beta' = 2^-20 rs beta' = rs beta, rs a power
+// of two.
+fld_status residual_update(fld_handle* h, const double* x, double* xo, double rs, double bs,
+                           cudaStream_t s, double* rr, double* dd, double* amax,
+                           unsigned* err) {
+    const Lvl& L = h->lv[0];
+    int nparts = 0;
+    run(h, "resid_upd", 0, L.ncell, s, [&] {
+        nparts = launch_resid_update(L, x, h->d32[0].x, xo, h->d32[0].K, h->d32[0].b,
+                                     h->partials, h->norm_blocks, (float)rs, (float)bs, s);
+    });
+    run(h, "finish_sum", 0, nparts, s, [&] {
+        launch_finish_update(h->partials, nparts, &h->scal->sum, &h->scal->drift,
+                             &h->scal->amax, s);
+    });
+    FLD_CK(cudaGetLastError());
+    double sum;
+    const fld_status rc = read_scalars(h, s, &sum, err);
+    if (rc != FLD_OK) return rc;
+    *rr = sum / (rs * rs);
+    *dd = h->hscal->drift / (rs * rs);     // (bs beta')^2 / rs^2 = (2^-20 beta')^2
+    *amax = h->hscal->amax;
+    return FLD_OK;
+}
+
 void graph_free(fld_handle* h) {
     if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
     if (h->gev_in) cudaEventDestroy(h->gev_in);
@@ -704,6 +735,17 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     // out of place, the iterate alternating between E and the level-0 FP64 scratch (free
     // in this mode); it ends in E
     const bool fused = mixed && resid64z_ok(L0, h->norm_blocks);
+    // after the first FP64 residual, the later ones may be updated recursively (r - A e in
+    // FP32) while the accumulated rounding bound `drift` stays below tol/2 ||b||; the scale
+    // of the squared sums is 2^-k with 2^k near the RMS of b
+    const bool upd = fused && h->o.resid_update && resid_update_ok(L0, h->norm_blocks);
+    const int sk = bnorm > 0 ? std::max(-100, std::min(100, -std::ilogb(bnorm /
+                                                                        std::sqrt((double)L0.ncell))))
+                             : 0;
+    const double rs = std::ldexp(1.0, sk), bs = std::ldexp(1.0, sk - 20);
+    const double tolb = h->o.tol * bnorm;
+    bool have64 = false;
+    double drift = 0.0;
     double* cur = E;
     double* oth = h->d64[0].tmp;
     int cyc = 0;
@@ -712,8 +754,26 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         if (fused) {
             rc = vcycle32(h, s);
             if (rc != FLD_OK) break;
-            rc = residual(h, cur, h->d32[0].x, oth, h->d32[0].b, s, &r2, &err);
-            std::swap(cur, oth);
+            if (upd && have64 && drift <= 0.5 * tolb) {
+                double d2 = 0.0, amax = 0.0;
+                rc = residual_update(h, cur, oth, rs, bs, s, &r2, &d2, &amax, &err);
+                std::swap(cur, oth);
+                if (rc != FLD_OK) break;
+                // the update's FP32 rounding, and that of x + e in FP64 moved through A
+                // (||A||_2 <= its largest row sum, FP32-rounded: 1.01; ||x + e||_2 <= ||b||_2)
+                drift += std::sqrt(d2) + 1.01 * std::ldexp(amax, -53) * bnorm;
+                // the recursive residual passes and its bound does not: the FP64 residual
+                // of the same iterate decides
+                if (std::sqrt(r2) <= tolb && std::sqrt(r2) + drift > tolb) {
+                    rc = residual(h, cur, nullptr, nullptr, h->d32[0].b, s, &r2, &err);
+                    drift = 0.0;
+                }
+            } else {
+                rc = residual(h, cur, h->d32[0].x, oth, h->d32[0].b, s, &r2, &err);
+                std::swap(cur, oth);
+                have64 = true;
+                drift = 0.0;
+            }
         } else if (mixed) {
             rc = vcycle32(h, s);
             if (rc != FLD_OK) break;
@@ -725,7 +785,7 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
             rc = residual(h, E, nullptr, nullptr, nullptr, s, &r2, &err);
         }
         if (rc != FLD_OK) break;
-        rel = std::sqrt(r2) / bnorm;
+        rel = (std::sqrt(r2) + drift) / bnorm;
         ++cyc;
         if (st && cyc < 64) st->resid_hist[cyc] = rel;
     }
@@ -763,6 +823,7 @@ void fld_default_opts(fld_opts* o) {
     o->cluster = 0;
     o->inner = 1;
     o->direct1d = 1;
+    o->resid_update = 1;
 }
 
 fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
@@ -820,7 +881,7 @@ fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {
     rc = rc ? rc : dalloc(h, &h->krscratch, n0);
     if (g->ndim == 1) rc = rc ? rc : dalloc(h, &h->triw, 12 * n0 + 1);
     h->norm_blocks = NORM_BLOCKS_PER_SM * num_sms();
-    rc = rc ? rc : dalloc(h, &h->partials, h->norm_blocks);
+    rc = rc ? rc : dalloc(h, &h->partials, 3LL * h->norm_blocks);
     rc = rc ? rc : dalloc(h, &h->scal, 1);
     if (!rc && cudaMallocHost(&h->hscal, sizeof(DevScalars)) != cudaSuccess) {
         cudaGetLastError();
@@ -1234,7 +1295,7 @@ extern "C" fld_status fld_diffuse_static(const fld_grid* g, const fld_opts* o, d
         h.dfK[q] = (float*)take(4 * n0);
     }
     h.norm_blocks = NORM_BLOCKS_PER_SM * num_sms();
-    h.partials = (double*)take(8 * (size_t)h.norm_blocks);
+    h.partials = (double*)take(24 * (size_t)h.norm_blocks);
     h.scal = (DevScalars*)take(sizeof(DevScalars));
     if (!fits) return FLD_ERR_ARG;
     h.Dscratch = nullptr;

@@ -325,6 +325,18 @@ int launch_resid32_init(const Lvl& L, const double* x, const double* b, const fl
                         float* r32, double* partials, int nblocks, cudaStream_t s);
 int launch_resid64z(const Lvl& L, const double* x, const float* e, double* xo, const double* b,
                     const double* K, float* r32, double* partials, int nblocks, cudaStream_t s);
+// Recursive refinement residual (k_resupd.cu): xo = x + e, r32 <- r32 - A e in FP32 on the
+// level's FP32 coefficients, sums of (rs r)^2 in partials[0, n) and of (bs beta)^2 in
+// partials[n, 2n), beta the per-cell rounding bound of the update, the largest absolute
+// row sum of A in partials[2n, 3n); returns n (<= nblocks).
+// resid_update_ok: the level is 3D, arithmetic face mean, its tiles fit the slots.
+bool resid_update_ok(const Lvl& L, int nblocks);
+int launch_resid_update(const Lvl& L, const double* x, const float* e, double* xo,
+                        const float* K, float* r32, double* partials, int nblocks, float rs,
+                        float bs, cudaStream_t s);
+// its reductions in one launch: the two sums and the largest row sum (partials[2n, 3n))
+void launch_finish_update(const double* partials, int nparts, double* out0, double* out1,
+                          double* out2, cudaStream_t s);
 
 // double-FP32 refinement (k_df.cu): half axis weights w_d/2 as (hi, lo) pairs
 struct DfW {
