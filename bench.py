@@ -725,6 +725,8 @@ def main():
     ap.add_argument("--nu2", type=int, default=-1, help="post-smoothing sweeps (-1: tuned)")
     ap.add_argument("--prolong", type=int, default=-1,
                     help="prolongation: -1 the tuned choice (else linear); 0 linear, 1 constant")
+    ap.add_argument("--truncate", type=int, default=-1,
+                    help="V-cycle depth from the operator: 1 on (the default), 0 full depth")
     ap.add_argument("--inner", type=int, default=-1,
                     help="FP32 V-cycles per refinement step (-1: tuned)")
     ap.add_argument("--no-ttt", action="store_true", help="skip the mixed-vs-FP64 solve timing")
@@ -763,7 +765,7 @@ def main():
 
     def options(pr):
         o, t = autotune.grid_options(P, pr)
-        for k in ("smoother", "nu1", "nu2", "inner", "prolong"):   # explicit choices override the tuner
+        for k in ("smoother", "nu1", "nu2", "inner", "prolong", "truncate"):   # explicit choices override the tuner
             if getattr(args, k) >= 0:
                 o[k] = getattr(args, k)
                 t = False

@@ -191,6 +191,17 @@ typedef struct {
                            whenever the bound alone passes tol/2 or the recursive residual
                            is below tol while the sum is not. 0: every refinement residual
                            in FP64. Ignored by the other modes and grids                */
+    int truncate;       /* V-cycle depth from the operator (every precision, 2D and 3D):
+                           1 (default) ends the V-cycle at the first level below the finest
+                           on which at most 4 red-black sweeps from zero reduce the error to
+                           1e-2, and solves that level by them. The bound comes from the
+                           call's largest K = dt D / h_x^2: on level l the off-diagonal row
+                           sums are at most s_l = 2 K_l sum_d w_d (K_l the largest K rescaled
+                           to the level's spacing), a sweep contracts by about
+                           (s_l/(1 + s_l))^2. Diffusion steps of a few explicit time steps
+                           then skip the coarse levels whose operator is close to the
+                           identity. 0: every level down to the coarsest (the single-block
+                           tail and its dense solve)                                    */
 } fld_opts;
 
 enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };
@@ -198,7 +209,9 @@ enum { FLD_FACE_ARITH = 0, FLD_FACE_HARM = 1 };
 enum { FLD_PROLONG_LINEAR = 0, FLD_PROLONG_CONSTANT = 1 };
 
 /* Per-solve statistics (optional output). resid_hist[i] is the relative
-   residual after i cycles (resid_hist[0] before the first), for i < 64.
+   residual after i cycles (resid_hist[0] before the first), for i < 64. levels: the
+   levels the solve's V-cycles used (fewer than the pyramid's with the truncate option;
+   1 for a direct 1D solve).
    With FLD_DIAG_ENERGY in the handle's diag option: energy_before / energy_after are the
    sums over the block of the energy per cell times the cell volume (prod h[d], d < ndim),
    before the call and after it: E for fld_diffuse, rho c_v T + E (c_v = R_gas/(gamma-1),

@@ -33,7 +33,7 @@ struct LevelBufs {
 struct DevScalars {       // read back together after each cycle
     double sum;
     unsigned err;
-    unsigned pad;
+    unsigned kmax;        // FP32 bits of the largest level-0 K of the solve
     double energy[2];     // diagnostics: total energy before and after a call
     double drift;         // recursive residual: sum of the squared scaled rounding bound
     double amax;          //   and the largest absolute row sum of the level-0 operator
@@ -169,10 +169,14 @@ struct fld_handle {
     cudaStream_t gs = nullptr;
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
     cudaGraphExec_t vgraph = nullptr;
-    int vgraph_key[6] = {0, 0, 0, 0, 0, 0};
+    int vgraph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long vgraph_nodes = 0;
     // first level of the single-launch V-cycle tail (-1: none); set when the levels are built
     int tail_start = -1;
+    // levels the V-cycles of the current solve use (the last one solved by vsweeps
+    // red-black sweeps when vdepth < nlev); set per solve from the largest K
+    int vdepth = 0;
+    int vsweeps = 0;
     cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};   // per-phase times (diag)
 };
 
@@ -236,7 +240,8 @@ bool fld::opts_valid(const fld_opts* o) {
             (o->face_mean == FLD_FACE_HARM && o->precision != FLD_PREC_MIXED_DF)) &&
            (o->prolong == FLD_PROLONG_LINEAR || o->prolong == FLD_PROLONG_CONSTANT) &&
            (o->limiter_df == 0 || o->limiter_df == 1) &&
-           (o->resid_update == 0 || o->resid_update == 1);
+           (o->resid_update == 0 || o->resid_update == 1) &&
+           (o->truncate == 0 || o->truncate == 1);
 }
 
 namespace {
@@ -307,6 +312,38 @@ void build_levels(fld_handle* h) {
             h->tail_start = l;
             break;
         }
+}
+
+// Depth of the V-cycles of one solve. On level l the operator is I plus a part whose
+// off-diagonal row sums are at most s_l = 2 Kmax_l sum_d w_d (Kmax_l <= Kmax times the
+// K rescalings down to l: restriction averages K), so the Jacobi iteration contracts by
+// at most rho_l = s_l / (1 + s_l) and a red-black sweep by about rho_l^2. The V-cycle
+// stops at the first level below the finest where TRUNC_MAX_SWEEPS such sweeps or fewer
+// reduce the error to TRUNC_EPS, and solves that level by them; with no such level above
+// the single-block tail (or the coarsest level) it runs to the coarsest level.
+constexpr double TRUNC_EPS = 0.01;
+constexpr int TRUNC_MAX_SWEEPS = 4;
+
+void choose_depth(fld_handle* h, double kmax) {
+    h->vdepth = h->nlev;
+    h->vsweeps = 0;
+    if (!h->o.truncate || !(kmax >= 0.0) || !std::isfinite(kmax)) return;
+    const int stop = h->tail_start >= 0 ? h->tail_start : h->nlev - 1;
+    double kl = kmax * (1.0 + 1e-6);        // the maximum was taken in FP32
+    for (int c = 1; c < stop; ++c) {
+        kl *= h->kscale_down[c - 1];
+        double ws = 0.0;
+        for (int d = 0; d < h->lv[c].ndim; ++d) ws += h->lv[c].w[d];
+        const double sw = 2.0 * kl * ws;
+        const double rho = sw / (1.0 + sw);
+        const int n = rho > 0.0 ? (int)std::ceil(std::log(TRUNC_EPS) / (2.0 * std::log(rho)))
+                                : 1;
+        if (n >= 1 && n <= TRUNC_MAX_SWEEPS) {
+            h->vdepth = c + 1;
+            h->vsweeps = n;
+            return;
+        }
+    }
 }
 
 template <typename T>
@@ -400,6 +437,16 @@ void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
     if (l == h->nlev - 1) {
         run(h, f32 ? "coarse32" : "coarse64", l, L.ncell, s,
             [&] { launch_coarse_solve<T>(L, B.x, B.b, B.K, h->o.coarse_sweeps, s); });
+        return;
+    }
+    if (l == h->vdepth - 1) {
+        // the truncated coarsest level: vsweeps red-black sweeps from x = 0 (an even
+        // number of them single-pass, so the iterate ends in B.x)
+        T* cur = B.x;
+        T* oth = B.tmp;
+        const int n = h->vsweeps;
+        const int f = (h->o.smoother == 2 && rb_sweep_supported<T>(L)) ? (n & ~1) : 0;
+        smooth<T>(h, B, l, n, f, cur, oth, s);
         return;
     }
     if (l == h->tail_start) {
@@ -531,7 +578,8 @@ fld_status vcycle32(fld_handle* h, cudaStream_t s) {
         for (int c = 0; c < inner; ++c) vcycle<float>(h, h->d32, 0, s);
         return FLD_OK;
     }
-    const int key[6] = {h->o.nu1, h->o.nu2, h->o.smoother, h->o.block, h->o.coarse_sweeps, inner};
+    const int key[8] = {h->o.nu1, h->o.nu2, h->o.smoother, h->o.block, h->o.coarse_sweeps,
+                        inner, h->vdepth, h->vsweeps};
     if (!h->gs) {
         FLD_CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
         FLD_CK(cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
@@ -610,7 +658,7 @@ fld_status diffuse_df(fld_handle* h, double* E, double bsum, fld_stats* st, cuda
     if (st) {
         memset(st, 0, sizeof(*st));
         st->resid_hist[0] = rel;
-        st->levels = h->nlev;
+        st->levels = h->vdepth;
     }
     int cyc = 0;
     while (rel > h->o.tol && cyc < h->o.max_cycles && std::isfinite(rel)) {
@@ -640,12 +688,16 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     const bool dfmode = h->o.precision == FLD_PREC_MIXED_DF;
     const bool mixed = h->o.precision == FLD_PREC_MIXED || dfmode;
     const double kscale = dt / (h->g.h[0] * h->g.h[0]);
-    run(h, "prep", 0, L0.ncell, s, [&] {
-        launch_prep_level0(L0, kscale, D, E, E_bc, h->bc_off, h->d64[0].K,
-                           mixed ? h->d32[0].K : nullptr, h->d64[0].b, &h->scal->err, s);
-    });
     // 1D grids with direct1d: the tridiagonal system solved directly (no pyramid needed)
     const bool direct = h->g.ndim == 1 && h->o.direct1d && h->triw;
+    // the largest K decides the V-cycle depth (read back with the norm of b)
+    const bool want_kmax = !direct && h->o.truncate;
+    if (want_kmax) FLD_CK(cudaMemsetAsync(&h->scal->kmax, 0, sizeof(unsigned), s));
+    run(h, "prep", 0, L0.ncell, s, [&] {
+        launch_prep_level0(L0, kscale, D, E, E_bc, h->bc_off, h->d64[0].K,
+                           mixed ? h->d32[0].K : nullptr, h->d64[0].b, &h->scal->err,
+                           want_kmax ? &h->scal->kmax : nullptr, s);
+    });
     if (!direct) {
         if (mixed) restrict_pyramid<float>(h, h->d32, s);
         else restrict_pyramid<double>(h, h->d64, s);
@@ -664,6 +716,14 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
         return FLD_ERR_DOMAIN;
     }
     const double bnorm = std::sqrt(bsum);
+    if (want_kmax) {
+        unsigned kb = h->hscal->kmax;
+        float kf;
+        memcpy(&kf, &kb, sizeof(kf));
+        choose_depth(h, (double)kf);
+    } else {
+        choose_depth(h, -1.0);
+    }
     if (direct) {
         // the reduction, then refinement steps with it while the FP64 residual is above
         // tol (each one a cycle; rounding of the reduction grows with dt D / h^2)
@@ -729,7 +789,7 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     if (st) {
         memset(st, 0, sizeof(*st));
         st->resid_hist[0] = rel;
-        st->levels = h->nlev;
+        st->levels = h->vdepth;
     }
     // mixed refinement on 3D levels: the correction is added inside the residual kernel,
     // out of place, the iterate alternating between E and the level-0 FP64 scratch (free
@@ -824,6 +884,7 @@ void fld_default_opts(fld_opts* o) {
     o->inner = 1;
     o->direct1d = 1;
     o->resid_update = 1;
+    o->truncate = 1;
 }
 
 fld_status fld_create(fld_handle** out, const fld_grid* g, const fld_opts* o) {

@@ -245,9 +245,10 @@ void launch_coupling(const Lvl& L, const double* h, const double* E, const doubl
 void launch_split_df(long long n, const double* v, float* hi, float* lo, cudaStream_t s);
 
 // multigrid (k_mg.cu)
+// kmax (nullable): the FP32 bits of the largest K, folded in by atomicMax (zero it first)
 void launch_prep_level0(const Lvl& L, double kscale, const double* D, const double* E,
                         const double* E_bc, const long long* bc_off, double* K64, float* K32,
-                        double* b, unsigned* err, cudaStream_t s);
+                        double* b, unsigned* err, unsigned* kmax, cudaStream_t s);
 template <typename T>
 void launch_restrict_K(const Lvl& F, const Lvl& C, double scale, const T* Kf, T* Kc,
                        cudaStream_t s);

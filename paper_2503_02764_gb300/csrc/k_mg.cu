@@ -33,20 +33,25 @@ static inline int rows_grid(const Lvl& L, int cap = 0) {
 
 // ----------------------------------------------------------------- level-0 set-up
 // K = kscale D (kscale = dt / h_x^2), its FP32 copy, and b = E + Dirichlet face terms
-// 2 K w_d E_b.
+// 2 K w_d E_b. With kmax, the largest K (its FP32 value, K >= 0) is folded into *kmax by
+// an integer atomicMax of its bits (non-negative FP32 numbers order as their bit patterns).
 struct BcOffM {
     long long off[6];
 };
 
-__global__ void k_prep_level0(Lvl L, double kscale, const double* __restrict__ D,
-                              const double* __restrict__ E, const double* __restrict__ Ebc,
-                              BcOffM bo, double* __restrict__ K64, float* __restrict__ K32,
-                              double* __restrict__ b, unsigned* err) {
+__global__ void __launch_bounds__(256)
+k_prep_level0(Lvl L, double kscale, const double* __restrict__ D,
+              const double* __restrict__ E, const double* __restrict__ Ebc, BcOffM bo,
+              double* __restrict__ K64, float* __restrict__ K32, double* __restrict__ b,
+              unsigned* err, unsigned* kmax) {
+    __shared__ float wmax[8];
+    float km = 0.f;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.ncell;
          p += (long long)gridDim.x * blockDim.x) {
         const double Dp = D[p];
         if (!pos_finite(Dp)) atomicOr(err, ERRBIT_DOMAIN);
         const double Kp = kscale * Dp;
+        km = fmaxf(km, (float)Kp);
         K64[p] = Kp;
         if (K32) K32[p] = (float)Kp;
         double bp = E[p];
@@ -66,15 +71,23 @@ __global__ void k_prep_level0(Lvl L, double kscale, const double* __restrict__ D
         }
         b[p] = bp;
     }
+    if (!kmax) return;
+    for (int o = 16; o > 0; o >>= 1) km = fmaxf(km, __shfl_down_sync(0xffffffffu, km, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = km;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) km = fmaxf(km, wmax[q]);
+        if (km > 0.f) atomicMax(kmax, __float_as_uint(km));
+    }
 }
 
 void launch_prep_level0(const Lvl& L, double kscale, const double* D, const double* E,
                         const double* E_bc, const long long* bc_off, double* K64, float* K32,
-                        double* b, unsigned* err, cudaStream_t s) {
+                        double* b, unsigned* err, unsigned* kmax, cudaStream_t s) {
     BcOffM bo;
     for (int q = 0; q < 6; ++q) bo.off[q] = bc_off[q];
     k_prep_level0<<<grid_for(L.ncell, 256), 256, 0, s>>>(L, kscale, D, E, E_bc, bo, K64, K32, b,
-                                                         err);
+                                                         err, kmax);
 }
 
 // ----------------------------------------------------------------- transfers

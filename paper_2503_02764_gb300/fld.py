@@ -52,7 +52,8 @@ class fld_opts(C.Structure):
                 ("limiter", C.c_int), ("block", C.c_int), ("smoother", C.c_int),
                 ("graph", C.c_int), ("cluster", C.c_int), ("inner", C.c_int),
                 ("direct1d", C.c_int), ("diag", C.c_int), ("face_mean", C.c_int),
-                ("prolong", C.c_int), ("limiter_df", C.c_int), ("resid_update", C.c_int)]
+                ("prolong", C.c_int), ("limiter_df", C.c_int), ("resid_update", C.c_int),
+                ("truncate", C.c_int)]
 
 
 class fld_stats(C.Structure):
@@ -191,7 +192,7 @@ def make_grid(shape, h, bc):
 def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_sweeps=32,
               limiter=LIMITER_LP, block=0, smoother=0, graph=1, cluster=0, inner=1, direct1d=1,
               diag=0, face_mean=FACE_ARITH, prolong=PROLONG_LINEAR, limiter_df=0,
-              resid_update=1):
+              resid_update=1, truncate=1):
     o = fld_opts()
     lib().fld_default_opts(C.byref(o))
     o.precision, o.tol, o.max_cycles = precision, tol, max_cycles
@@ -206,6 +207,7 @@ def make_opts(precision=PREC_FP64, tol=1e-10, max_cycles=50, nu1=2, nu2=2, coars
     o.prolong = prolong
     o.limiter_df = limiter_df
     o.resid_update = resid_update
+    o.truncate = truncate
     return o
 
 
