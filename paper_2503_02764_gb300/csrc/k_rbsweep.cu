@@ -321,18 +321,31 @@ int zm_slots() {
     return std::max(1, g_zm_slots[dev].load(std::memory_order_relaxed));
 }
 
-// z-chunk length: about three waves of blocks over the SMs (the tiles times the chunks),
-// chunks of at least 8 planes so the 2-plane overlap stays small (32 planes at 256^3,
-// the fastest measured there). Levels of at most 64^3 cells are bound by the march's
-// per-plane latency, not by traffic: their chunks go down to 2 planes, so more blocks
-// march fewer steps each (64^3 to 16^3: 12-13 to 10-11 us per sweep; at 128^3 it gained
-// nothing).
+// z-chunk length. A block of a chunk of cz planes marches cz + 3 steps, and the blocks
+// (tiles times chunks) run in waves of the resident slots, so the sweep takes about
+// waves x (cz + 3) step times: the chunk length minimises that, from chunks of at least 8
+// planes (2 on levels of at most 64^3 cells, which are bound by the march's per-plane
+// latency, not by traffic) up to the whole extent. At 256^3 it picks 37 planes (7 chunks,
+// two full waves); at 128^3 10 planes (one wave of 416 blocks, where 8 planes made 512
+// blocks, a second wave of 56).
 int zm_chunk(const Lvl& L) {
-    const int tiles = ((L.n[0] + ZM_TX - 1) / ZM_TX) * ((L.n[1] + ZM_TY - 1) / ZM_TY);
-    const int nch = std::max(1, 2 * zm_slots() / std::max(1, tiles));
-    const int cz = (L.n[2] + nch - 1) / nch;
-    const int minc = L.ncell <= (1LL << 18) ? 2 : 8;
-    return std::min(L.n[2], std::max(minc, cz));
+    const long long tiles = ((L.n[0] + ZM_TX - 1) / ZM_TX) * ((L.n[1] + ZM_TY - 1) / ZM_TY);
+    const long long slots = zm_slots();
+    const int nz = L.n[2];
+    const int minc = std::min(nz, L.ncell <= (1LL << 18) ? 2 : 8);
+    int best = nz;
+    long long best_cost = -1;
+    for (int cz = minc; cz <= nz; ++cz) {
+        const long long nch = (nz + cz - 1) / cz;
+        if (cz > minc && (nz + cz - 2) / (cz - 1) == nch) continue;   // same chunk count
+        const long long waves = (tiles * nch + slots - 1) / slots;
+        const long long cost = waves * (cz + 3);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = cz;
+        }
+    }
+    return best;
 }
 
 }  // namespace
