@@ -11,14 +11,18 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-# z-marching sweeps and transfers (3D, tuned and untuned shapes), the FP64 and mixed
-# residuals, 1D/2D levels, the limiter's gradient with every wall kind, the whole step
+# z-marching sweeps and transfers (3D, tuned and untuned shapes), the FP64, mixed and
+# recursive residuals, 1D/2D levels, truncated V-cycles, the limiter's gradient with every
+# wall kind, the whole step
 TESTS = [
     "tests/test_gpu_step.py",
     "tests/test_gpu_limiter.py",
     "tests/test_gpu_diffuse.py::test_fused_sweep_matches_half_sweeps_and_oracle",
     "tests/test_gpu_tuned.py::test_inner_cycles_zmarch_graph_box",
     "tests/test_gpu_face_mean.py::test_diffuse_harmonic_matches_oracle",
+    # the recursive refinement residual and the truncated V-cycle's coarse sweeps
+    "tests/test_gpu_resid_update.py::test_recursive_residual_bounds_the_true_residual",
+    "tests/test_gpu_truncate.py::test_truncated_vcycle_solves_the_same_system",
 ]
 
 
