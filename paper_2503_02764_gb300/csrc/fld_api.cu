@@ -480,7 +480,7 @@ void vcycle(fld_handle* h, LevelBufs<T>* P, int l, cudaStream_t s) {
     smooth<T>(h, B, l, nu1, f1, cur, oth, s);
     const Lvl& C = h->lv[l + 1];
     run(h, f32 ? "resid_restrict32" : "resid_restrict64", l, L.ncell, s,
-        [&] { launch_resid_restrict<T>(L, C, cur, B.b, B.K, P[l + 1].b, bs, s); });
+        [&] { launch_resid_restrict<T>(L, C, cur, B.b, B.K, P[l + 1].b, bs, nu1 > 0, s); });
     if (l + 1 < h->nlev - 1) cudaMemsetAsync(P[l + 1].x, 0, sizeof(T) * C.ncell, s);
     vcycle<T>(h, P, l + 1, s);
     run(h, f32 ? "prolong32" : "prolong64", l, L.ncell, s,

@@ -292,14 +292,16 @@ void prepare_vcycle_tail();
 
 // 3D transfers when every axis halves exactly (one thread per coarse cell).
 bool transfer3_ok(const Lvl& F, const Lvl& C);
+// red_only: the level was just smoothed by a red-black sweep (black last), so only the
+// red children's residuals are summed (the black ones vanish up to rounding)
 template <typename T>
 void launch_resid_restrict3(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
-                            cudaStream_t s);
+                            bool red_only, cudaStream_t s);
 template <typename T>
 void launch_prolong3(const Lvl& F, const Lvl& C, T* xf, const T* xc, cudaStream_t s);
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K,
-                           T* bc, int block, cudaStream_t s);
+                           T* bc, int block, bool red_only, cudaStream_t s);
 template <typename T>
 void launch_prolong(const Lvl& F, const Lvl& C, T* xf, const T* xc, int block, cudaStream_t s);
 template <typename T>

@@ -273,8 +273,9 @@ __global__ void k_resid_restrict(Lvl F, Lvl C, const T* __restrict__ x, const T*
 
 template <typename T>
 void launch_resid_restrict(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
-                           int block, cudaStream_t s) {
-    if (transfer3_ok(F, C) && !F.fm) return launch_resid_restrict3<T>(F, C, x, b, K, bc, s);
+                           int block, bool red_only, cudaStream_t s) {
+    if (transfer3_ok(F, C) && !F.fm)
+        return launch_resid_restrict3<T>(F, C, x, b, K, bc, red_only, s);
     k_resid_restrict<T><<<grid_for(C.ncell, block), block, 0, s>>>(F, C, x, b, K, bc);
 }
 
@@ -541,7 +542,7 @@ void launch_energy_sum(long long n, const double* rho, const double* T, const do
     template void launch_smooth<T>(const Lvl&, int, const T*, T*, const T*, const T*, int,         \
                                    cudaStream_t);                                                \
     template void launch_resid_restrict<T>(const Lvl&, const Lvl&, const T*, const T*, const T*,  \
-                                           T*, int, cudaStream_t);                               \
+                                           T*, int, bool, cudaStream_t);                         \
     template void launch_prolong<T>(const Lvl&, const Lvl&, T*, const T*, int, cudaStream_t);     \
     template void launch_coarse_solve<T>(const Lvl&, T*, const T*, const T*, int, cudaStream_t); \
     template bool rb_half_supported<T>(const Lvl&);                                              \

@@ -165,6 +165,115 @@ __global__ void k_resid_restrict3(Lvl F, Lvl C, const T* __restrict__ x, const T
     bc[fld_at(((long long)Kc * C.n[1] + J) * C.n[0] + I, C.ncell)] = s * T(0.125);
 }
 
+// The same restriction right after a red-black smoothing sweep, which ends with the black
+// cells (x + y + z odd) relaxed against their updated red neighbours: their residual is
+// zero up to the rounding of that relaxation, so only the four red children of a coarse
+// cell, (0,0,0), (1,1,0), (1,0,1) and (0,1,1) in (x, y, z) offsets, enter the mean. Each
+// red child's six neighbours are three black siblings and three cells outside the block
+// (one per axis, on its side), read as single values.
+template <typename T>
+__global__ void k_restrict_red3(Lvl F, Lvl C, const T* __restrict__ x, const T* __restrict__ b,
+                                const T* __restrict__ K, T* __restrict__ bc) {
+    const int I = blockIdx.x * 32 + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Kc = blockIdx.z;
+    if (I >= C.n[0] || J >= C.n[1]) return;
+    const int nx = F.n[0], ny = F.n[1], nz = F.n[2];
+    const long long sy = nx, sz = (long long)nx * ny;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * Kc;
+    const T hx = T(0.5) * wgt<T>(F, 0), hy = T(0.5) * wgt<T>(F, 1), hz = T(0.5) * wgt<T>(F, 2);
+    const int xo[2] = {tr_nb(i0, -1, nx, F.bclo[0] == FLD_BC_PERIODIC),
+                       tr_nb(i0 + 1, 1, nx, F.bclo[0] == FLD_BC_PERIODIC)};
+    const int yo[2] = {tr_nb(j0, -1, ny, F.bclo[1] == FLD_BC_PERIODIC),
+                       tr_nb(j0 + 1, 1, ny, F.bclo[1] == FLD_BC_PERIODIC)};
+    const int zo[2] = {tr_nb(k0, -1, nz, F.bclo[2] == FLD_BC_PERIODIC),
+                       tr_nb(k0 + 1, 1, nz, F.bclo[2] == FLD_BC_PERIODIC)};
+    const T fx[2] = {(T)tr_factor(F.bclo[0]), (T)tr_factor(F.bchi[0])};
+    const T fy[2] = {(T)tr_factor(F.bclo[1]), (T)tr_factor(F.bchi[1])};
+    const T fz[2] = {(T)tr_factor(F.bclo[2]), (T)tr_factor(F.bchi[2])};
+
+    // x and K of the eight children, rows (bb, c) read as pairs
+    Pair<T> xv[2][2], kv[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+            const long long row =
+                fld_span((long long)(k0 + c) * sz + (long long)(j0 + bb) * sy, nx, F.ncell) + i0;
+            xv[c][bb] = ld2(x + row);
+            kv[c][bb] = ld2(K + row);
+        }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+            const int a = bb ^ c;                       // the red child of row (bb, c)
+            const long long row =
+                fld_span((long long)(k0 + c) * sz + (long long)(j0 + bb) * sy, nx, F.ncell);
+            const T kc = kv[c][bb].v[a], xc = xv[c][bb].v[a];
+            const T bv = b[row + i0 + a];
+            // outside neighbours: x on side a, y on side bb, z on side c
+            T xxo, kxo, xyo, kyo, xzo, kzo;
+            if (xo[a] >= 0) {
+                xxo = x[row + xo[a]];
+                kxo = K[row + xo[a]];
+            } else {
+                xxo = T(0);
+                kxo = fx[a] * kc;
+            }
+            if (yo[bb] >= 0) {
+                const long long r = fld_span((long long)(k0 + c) * sz + (long long)yo[bb] * sy, nx,
+                                             F.ncell) + i0 + a;
+                xyo = x[r];
+                kyo = K[r];
+            } else {
+                xyo = T(0);
+                kyo = fy[bb] * kc;
+            }
+            if (zo[c] >= 0) {
+                const long long r = fld_span((long long)zo[c] * sz + (long long)(j0 + bb) * sy, nx,
+                                             F.ncell) + i0 + a;
+                xzo = x[r];
+                kzo = K[r];
+            } else {
+                xzo = T(0);
+                kzo = fz[c] * kc;
+            }
+            // black siblings: across x in the same row, across y in row (1 - bb, c), across z
+            // in row (bb, 1 - c), each at offset 1 - a, a, a of its pair
+            const T xxi = xv[c][bb].v[1 - a], kxi = kv[c][bb].v[1 - a];
+            const T xyi = xv[c][1 - bb].v[a], kyi = kv[c][1 - bb].v[a];
+            const T xzi = xv[1 - c][bb].v[a], kzi = kv[1 - c][bb].v[a];
+            // faces in the order x-, x+, y-, y+, z-, z+ (the side-0 neighbour is the lower)
+            const T kxm = a ? kxi : kxo, xxm = a ? xxi : xxo;
+            const T kxp = a ? kxo : kxi, xxp = a ? xxo : xxi;
+            const T kym = bb ? kyi : kyo, xym = bb ? xyi : xyo;
+            const T kyp = bb ? kyo : kyi, xyp = bb ? xyo : xyi;
+            const T kzm = c ? kzi : kzo, xzm = c ? xzi : xzo;
+            const T kzp = c ? kzo : kzi, xzp = c ? xzo : xzi;
+            T f = (kc + kxm) * hx;
+            T sw = f, acc = f * xxm;
+            f = (kc + kxp) * hx;
+            sw += f;
+            acc += f * xxp;
+            f = (kc + kym) * hy;
+            sw += f;
+            acc += f * xym;
+            f = (kc + kyp) * hy;
+            sw += f;
+            acc += f * xyp;
+            f = (kc + kzm) * hz;
+            sw += f;
+            acc += f * xzm;
+            f = (kc + kzp) * hz;
+            sw += f;
+            acc += f * xzp;
+            s += bv - (T(1) + sw) * xc + acc;
+        }
+    bc[fld_at(((long long)Kc * C.n[1] + J) * C.n[0] + I, C.ncell)] = s * T(0.125);
+}
+
 template <typename T>
 __global__ void k_prolong3(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict__ xc) {
     const int I = blockIdx.x * 32 + threadIdx.x;
@@ -241,10 +350,13 @@ __global__ void k_prolong3(Lvl F, Lvl C, T* __restrict__ xf, const T* __restrict
 
 template <typename T>
 void launch_resid_restrict3(const Lvl& F, const Lvl& C, const T* x, const T* b, const T* K, T* bc,
-                            cudaStream_t s) {
+                            bool red_only, cudaStream_t s) {
     dim3 block(32, 4);
     dim3 grid((C.n[0] + 31) / 32, (C.n[1] + 3) / 4, C.n[2]);
-    k_resid_restrict3<T><<<grid, block, 0, s>>>(F, C, x, b, K, bc);
+    if (red_only)
+        k_restrict_red3<T><<<grid, block, 0, s>>>(F, C, x, b, K, bc);
+    else
+        k_resid_restrict3<T><<<grid, block, 0, s>>>(F, C, x, b, K, bc);
 }
 
 template <typename T>
@@ -255,9 +367,9 @@ void launch_prolong3(const Lvl& F, const Lvl& C, T* xf, const T* xc, cudaStream_
 }
 
 template void launch_resid_restrict3<float>(const Lvl&, const Lvl&, const float*, const float*,
-                                            const float*, float*, cudaStream_t);
+                                            const float*, float*, bool, cudaStream_t);
 template void launch_resid_restrict3<double>(const Lvl&, const Lvl&, const double*, const double*,
-                                             const double*, double*, cudaStream_t);
+                                             const double*, double*, bool, cudaStream_t);
 template void launch_prolong3<float>(const Lvl&, const Lvl&, float*, const float*, cudaStream_t);
 template void launch_prolong3<double>(const Lvl&, const Lvl&, double*, const double*, cudaStream_t);
 
