@@ -201,7 +201,7 @@ typedef struct {
                            (s_l/(1 + s_l))^2. Diffusion steps of a few explicit time steps
                            then skip the coarse levels whose operator is close to the
                            identity. 0: every level down to the coarsest (the single-block
-                           tail and its dense solve)                                    */
+                           tail and its dense solve). The batched step keeps every level */
 } fld_opts;
 
 enum { FLD_DIAG_ENERGY = 1, FLD_DIAG_TIMES = 2 };
