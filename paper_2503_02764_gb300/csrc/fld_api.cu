@@ -799,9 +799,9 @@ fld_status diffuse_impl(fld_handle* h, double dt, const double* D, const double*
     // FP32) while the accumulated rounding bound `drift` stays below tol/2 ||b||; the scale
     // of the squared sums is 2^-k with 2^k near the RMS of b
     const bool upd = fused && h->o.resid_update && resid_update_ok(L0, h->norm_blocks);
-    const int sk = bnorm > 0 ? std::max(-100, std::min(100, -std::ilogb(bnorm /
-                                                                        std::sqrt((double)L0.ncell))))
-                             : 0;
+    int sk = 0;
+    if (bnorm > 0 && std::isfinite(bnorm))
+        sk = std::max(-100, std::min(100, -std::ilogb(bnorm / std::sqrt((double)L0.ncell))));
     const double rs = std::ldexp(1.0, sk), bs = std::ldexp(1.0, sk - 20);
     const double tolb = h->o.tol * bnorm;
     bool have64 = false;
